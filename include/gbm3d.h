@@ -1,0 +1,170 @@
+/*
+ * gbm3d.h -- C ABI of the GB300 (sm_103a) G-BM3D denoising hot path.
+ *
+ * Method: T. Sanders and S. Larkin, "New Computational Techniques for a Faster
+ * Variation of BM3D Image Denoising", arXiv 2103.10765.  Stage 1 is fast block
+ * matching (Sec. 2) followed by global 3-D wavelet hard thresholding of the
+ * volume of matched blocks with cycle spinning and aggregation (Sec. 3,
+ * Sec. 3.1); stage 2 matches again on the stage-1 estimate and applies the
+ * per-group 2-D DCT + 1-D Haar empirical Wiener filter (Sec. 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Images are float32, row-major, H rows by W columns, with a row pitch in
+ *    ELEMENTS (pitch >= W).  Internal images (pilots, outputs of
+ *    gbm3d_denoise) use the caller's pitch for `out`.
+ *  - Every pointer argument except `params` is a DEVICE pointer owned by the
+ *    caller, unless stated otherwise.  `params` is a host pointer.
+ *  - Block indices are int32 linear top-left positions k*W + l (never use the
+ *    pitch for these).
+ *  - Reference blocks sit on the grid G_y x G_x, G = {0, s, 2s, ...} with the
+ *    last position clamped to M - N (covers the image without padding;
+ *    Sec. 3.1 tiling, generalised to a stride s).  Reference g = p*Bx + q sits
+ *    at (G_y[p], G_x[q]).
+ *  - All calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  They validate every argument on the host before any
+ *    launch and return a status code; on failure nothing has been launched
+ *    unless the code is GBM3D_ECUDA.  gbm3d_last_error_string() describes the
+ *    last failure of the calling host thread.
+ *  - `ws` is caller-owned device scratch of at least gbm3d_workspace_bytes()
+ *    bytes, 256-byte aligned.  The library allocates no device memory.  Calls
+ *    that share one `ws` must be ordered on one stream.
+ *  - Supported now: patch N = 8, K1, K2 in {8, 16, 32}, levels in 1..3,
+ *    cycle_spins in 1..4, translations in 1..3.  Other values return
+ *    GBM3D_EUNSUPPORTED.
+ */
+#ifndef GBM3D_H
+#define GBM3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gbm3d_stream_t; /* same type as cudaStream_t */
+
+enum {
+    GBM3D_OK = 0,
+    GBM3D_EINVAL = 1,       /* bad argument (null pointer, size, parameter) */
+    GBM3D_ENOMEM = 2,       /* workspace too small */
+    GBM3D_ECUDA = 3,        /* a CUDA launch or runtime call failed */
+    GBM3D_ETIMEOUT = 4,     /* reserved: a bounded device-side wait gave up */
+    GBM3D_EUNSUPPORTED = 5  /* valid but not implemented for this build */
+};
+
+/* Method parameters (Sec. 5 parameter list; see gbm3d_params_default). */
+typedef struct {
+    int patch;          /* N: block side, both stages                         */
+    int step;           /* s: reference-grid stride                           */
+    int search_radius;  /* R: candidates with |k-i| <= R and |l-j| <= R       */
+    int k1;             /* K: blocks per group, stage 1 (Sec. 3: K = 16)      */
+    int k2;             /* K: blocks per group, stage 2                       */
+    int levels;         /* wavelet levels of the 3-D transform (3)            */
+    int cycle_spins;    /* number of cycle spins h = 0..C-1 (2)               */
+    int translations;   /* image translations h in {0, N/4, N/2}[:T]          */
+    int stages;         /* 1 = stage 1 only (BM3D1), 2 = both (BM3D2)         */
+    float tau_a;        /* tau_l = sigma (tau_a - tau_b l), l = 1 finest (3.6) */
+    float tau_b;        /* (0.3)                                              */
+    float kaiser_beta;  /* stage-2 aggregation window, 0 = no window (2.0)    */
+    float eps_w;        /* lower guard on TV and Wiener weight denominators   */
+} gbm3d_params;
+
+/* Fill *p with a preset.  preset 0: N=8, s=3, R=19 (39x39 candidate offsets),
+ * K1=16, K2=32, 3 levels, 2 cycle spins, 1 translation, 2 stages,
+ * tau = sigma (3.6 - 0.3 l), Kaiser beta 2, eps_w 1e-8.  preset 1 (the
+ * paper's Sec. 5 list where this build supports it): N=8, s=8, R=16, K1=K2=16,
+ * 3 levels, 2 cycle spins, 2 translations.  Returns GBM3D_EINVAL for other
+ * presets or p == NULL. */
+int gbm3d_params_default(gbm3d_params *p, int preset);
+
+/* Reference-grid size for an H x W image: By = |G_y|, Bx = |G_x|.  Host-only,
+ * launches nothing. */
+int gbm3d_grid_dims(int H, int W, const gbm3d_params *p, int *By, int *Bx);
+
+/* Bytes of device scratch `ws` needed by any call below for an H x W image
+ * with these parameters (the maximum over the calls; gbm3d_denoise needs the
+ * most).  Host-only. */
+int gbm3d_workspace_bytes(int H, int W, const gbm3d_params *p, size_t *bytes);
+
+/* Block matching (Sec. 2 eq. dfg, Theorem 1, Algorithm 1; Sec. 3.1 S^K_pq).
+ * For every reference block (i,j) of the grid: exact squared distances
+ * ||z^{ij} - z^{kl}||^2 (FP32, direct sum of squared differences) to every
+ * candidate top-left (k,l) with |k-i| <= R, |l-j| <= R inside [0,H-N]x[0,W-N];
+ * slot 0 = the reference itself, slots 1..K-1 = the K-1 nearest other blocks
+ * ordered by (distance, k, l).
+ *   img  : H x W image, pitch elements per row.
+ *   idx  : out, int32 [By*Bx][K].
+ *   dist : out, float [By*Bx][K] (nullable); slot 0 holds 0.
+ *   ws   : unused (may be NULL).
+ * EINVAL if the smallest search window holds fewer than K blocks. */
+int gbm3d_match(const float *img, int H, int W, int pitch, const gbm3d_params *p, int K,
+                int32_t *idx, float *dist, void *ws, gbm3d_stream_t stream);
+
+/* Stage-1 global hard thresholding (Sec. 3.1 eq. BM3DHT with cycle spinning,
+ * TV weights).  The volume V[pN+a, qN+b, r] = Z[k_r+a, l_r+b] (mosaic of all
+ * groups, (By N) x (Bx N) x K1) is transformed as a whole by a `levels`-level
+ * 3-D wavelet (bior1.5 along rows and columns, Haar along the group axis,
+ * periodic, Mallat), every detail coefficient of level l is hard-thresholded
+ * at sigma (tau_a - tau_b l), the transform is inverted; this is repeated for
+ * cycle spins h = 0..C-1 (circular shift by h along all three axes) and
+ * averaged.
+ *   noisy  : H x W noisy image Z, pitch elements per row.
+ *   idx    : int32 [By*Bx][K1] from gbm3d_match with K = k1.
+ *   groups : out, float [By*Bx][K1][N][N] = filtered blocks U.
+ *   w      : out, float [By*Bx]: 1 / max(TV(u^{pq}), eps_w).
+ *   ws     : scratch, gbm3d_workspace_bytes. */
+int gbm3d_filter_ht(const float *noisy, int H, int W, int pitch, const int32_t *idx, float sigma,
+                    const gbm3d_params *p, float *groups, float *w, void *ws, gbm3d_stream_t stream);
+
+/* Stage-2 empirical Wiener filtering (Sec. 4).  Per group: G_z (noisy) and
+ * G_y (pilot) blocks, transform T = orthonormal 8x8 DCT-II per block then
+ * full-depth orthonormal Haar along the K2 blocks; omega = P^2/(P^2+sigma^2)
+ * with P = T(G_y); filtered group T^-1(omega . T(G_z)); weight
+ * 1 / max(sigma^2 sum omega^2, eps_w).
+ *   noisy, pilot : H x W images sharing `pitch`.
+ *   idx    : int32 [By*Bx][K2] (matching done on the pilot).
+ *   groups : out, float [By*Bx][K2][N][N];  w : out, float [By*Bx].
+ *   ws     : unused (may be NULL). */
+int gbm3d_filter_wiener(const float *noisy, const float *pilot, int H, int W, int pitch,
+                        const int32_t *idx, float sigma, const gbm3d_params *p, float *groups, float *w,
+                        void *ws, gbm3d_stream_t stream);
+
+/* Aggregation (Sec. 3.1 weighted average Y = sum w U / sum w chi).  Every
+ * block of every group goes back to its own position k*W + l with weight
+ * w[g] (times kappa[a] kappa[b], the Kaiser window of parameter window_beta,
+ * when window_beta > 0).  Each output pixel sums its contributions in a fixed
+ * order with Kahan-compensated FP32 numerator and denominator, so the result
+ * is deterministic.
+ *   groups : float [G][K][N][N];  w : float [G];  idx : int32 [G][K], with
+ *            G = By*Bx of the grid for H x W.
+ *   out    : out, H x W, pitch elements per row.
+ *   ws     : scratch, gbm3d_workspace_bytes.
+ * Every pixel must be covered by some block (true for grid-reference slot 0). */
+int gbm3d_aggregate(const float *groups, const float *w, const int32_t *idx, int K, int H, int W,
+                    int pitch, const gbm3d_params *p, float window_beta, float *out, void *ws,
+                    gbm3d_stream_t stream);
+
+/* Whole method (Sec. 1.1 BM3D1/BM3D2 with translation averaging, eq.
+ * firstEst): input the noisy image and the noise standard deviation, get the
+ * denoised image (Sec. 1: "only ... the noisy image and an estimate of the
+ * noise level").  Stage 1 with k1, then (stages == 2) stage 2 matching on the
+ * stage-1 estimate with k2 and Wiener filtering, each stage averaged over
+ * `translations` circular image shifts.
+ *   noisy : H x W, pitch;  out : H x W, same pitch (must not alias noisy).
+ *   ws    : scratch, gbm3d_workspace_bytes. */
+int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, const gbm3d_params *p,
+                  float *out, void *ws, gbm3d_stream_t stream);
+
+/* Description of the last failure on this host thread ("" if none). */
+const char *gbm3d_last_error_string(void);
+
+/* Library version string. */
+const char *gbm3d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBM3D_H */

@@ -1,0 +1,218 @@
+// aggregate.cu -- weighted aggregation of filtered blocks (Sec. 3.1:
+// Y = sum w U / sum w chi; stage 2 adds a Kaiser window).
+//
+// Deterministic owner-computes design: the match lists are inverted into a
+// CSR index (block top-left position -> the (group, slot) entries placed
+// there; counting sort, then each bucket sorted), and one thread per output
+// pixel walks the N x N top-left positions that cover it, in a fixed order,
+// summing numerator and denominator with Kahan compensation.  No floating-
+// point atomics: the result does not depend on scheduling.
+#include "internal.cuh"
+
+namespace gbm3d {
+namespace {
+
+constexpr int kScanBlock = 1024; // elements per scan block (256 threads x 4)
+
+// Entries that are not valid block positions are skipped (never counted,
+// never placed), so a bad caller-supplied list cannot write out of bounds.
+__global__ void k_count(const int32_t *__restrict__ idx, int n, int H, int W, int *__restrict__ cnt)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int pos = idx[e];
+    if (block_ok(pos, H, W)) atomicAdd(cnt + pos, 1);
+}
+
+// Exclusive scan, phase 1: per-block scan of 1024 elements, block totals out.
+__global__ void __launch_bounds__(256) k_scan_local(const int *__restrict__ in, int n, int *__restrict__ out,
+                                                    int *__restrict__ bsum)
+{
+    __shared__ int warp_tot[8];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 4;
+    int v[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) v[i] = base + i < n ? in[base + i] : 0;
+    const int tsum = v[0] + v[1] + v[2] + v[3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    int woff = 0;
+    for (int i = 0; i < wid; i++) woff += warp_tot[i];
+    int run = woff + incl - tsum;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 255) bsum[blockIdx.x] = woff + incl;
+}
+
+// Phase 2: exclusive scan of the block totals (one CTA, sequential chunks).
+__global__ void __launch_bounds__(1024) k_scan_bsum(int *__restrict__ bsum, int nb)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < nb; c0 += 1024) {
+        const int e = c0 + threadIdx.x;
+        const int v = e < nb ? bsum[e] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        int woff = 0;
+        for (int i = 0; i < wid; i++) woff += warp_tot[i];
+        const int c = carry;
+        if (e < nb) bsum[e] = c + woff + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c + woff + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ bsum)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] += bsum[e / kScanBlock];
+}
+
+__global__ void k_fill(const int32_t *__restrict__ idx, int n, int H, int W, const int *__restrict__ off,
+                       int *__restrict__ cursor, int *__restrict__ list)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int pos = idx[e];
+    if (!block_ok(pos, H, W)) return;
+    const int slot = atomicAdd(cursor + pos, 1);
+    list[off[pos] + slot] = e;
+}
+
+// Sort each bucket ascending (fixes the summation order).
+__global__ void k_sort(const int *__restrict__ off, int npos, int *__restrict__ list)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npos) return;
+    const int b0 = off[p], b1 = off[p + 1];
+    for (int i = b0 + 1; i < b1; i++) {
+        const int v = list[i];
+        int j = i - 1;
+        while (j >= b0 && list[j] > v) {
+            list[j + 1] = list[j];
+            j--;
+        }
+        list[j + 1] = v;
+    }
+}
+
+struct Win8 {
+    float v[8];
+};
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+__global__ void __launch_bounds__(256)
+k_gather(const float *__restrict__ groups, const float *__restrict__ w, const int *__restrict__ off,
+         const int *__restrict__ list, int log2K, int H, int W, int pitch, Win8 win, float *__restrict__ out)
+{
+    __shared__ float sw[8];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) sw[i] = win.v[i];
+    }
+    __syncthreads();
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= W || y >= H) return;
+    float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
+    const int ka = max(0, y - 7), kb = min(y, H - 8);
+    const int la = max(0, x - 7), lb = min(x, W - 8);
+    for (int k = ka; k <= kb; k++) {
+        const int a = y - k;
+        const float wa = sw[a];
+        for (int l = la; l <= lb; l++) {
+            const int b = x - l;
+            const float wab = wa * sw[b];
+            const int pos = k * W + l;
+            const int e0 = __ldg(off + pos), e1 = __ldg(off + pos + 1);
+            for (int e = e0; e < e1; e++) {
+                const int ent = __ldg(list + e);
+                const float wt = __ldg(w + (ent >> log2K)) * wab;
+                const float v = __ldg(groups + (size_t)ent * 64 + a * 8 + b);
+                kahan_add(num, cn, wt * v);
+                kahan_add(den, cd, wt);
+            }
+        }
+    }
+    out[(size_t)y * pitch + x] = num / den;
+}
+
+} // namespace
+
+AggLayout agg_layout(int H, int W, int G, int K)
+{
+    AggLayout L{};
+    L.npos = H * W;
+    const int nscan = L.npos + 1;
+    L.nblk = (nscan + kScanBlock - 1) / kScanBlock;
+    size_t o = 0;
+    L.cnt = o;
+    o += align_up((size_t)nscan * sizeof(int));
+    L.off = o;
+    o += align_up((size_t)nscan * sizeof(int));
+    L.cursor = o;
+    o += align_up((size_t)nscan * sizeof(int));
+    L.list = o;
+    o += align_up((size_t)G * K * sizeof(int));
+    L.bsum = o;
+    o += align_up((size_t)L.nblk * sizeof(int));
+    L.bytes = o;
+    return L;
+}
+
+cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t *idx, int G, int K, int H, int W,
+                             int pitch, const float *window8, float *out, void *agg_ws, cudaStream_t st)
+{
+    const AggLayout L = agg_layout(H, W, G, K);
+    char *base = (char *)agg_ws;
+    int *cnt = (int *)(base + L.cnt), *off = (int *)(base + L.off), *cursor = (int *)(base + L.cursor);
+    int *list = (int *)(base + L.list), *bsum = (int *)(base + L.bsum);
+    const int n = G * K, nscan = L.npos + 1;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)nscan * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(cursor, 0, (size_t)nscan * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_count<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, cnt);
+    k_scan_local<<<L.nblk, 256, 0, st>>>(cnt, nscan, off, bsum);
+    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, L.nblk);
+    k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(off, nscan, bsum);
+    k_fill<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, off, cursor, list);
+    k_sort<<<(L.npos + 255) / 256, 256, 0, st>>>(off, L.npos, list);
+    Win8 win;
+    for (int i = 0; i < 8; i++) win.v[i] = window8[i];
+    int log2K = 0;
+    while ((1 << log2K) < K) log2K++;
+    dim3 grid((W + 31) / 32, (H + 7) / 8);
+    k_gather<<<grid, 256, 0, st>>>(groups, w, off, list, log2K, H, W, pitch, win, out);
+    return cudaGetLastError();
+}
+
+} // namespace gbm3d

@@ -1,0 +1,372 @@
+// api.cu -- the extern "C" entry points of libgbm3d: argument validation
+// (host only, before any launch), workspace layout and the two-stage driver
+// (Sec. 1.1 BM3D1 / BM3D2, translation averaging of eq. firstEst).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace gbm3d {
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(GBM3D_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int check_params(const gbm3d_params *p)
+{
+    if (!p) return fail(GBM3D_EINVAL, "params is NULL");
+    if (p->patch != kPatch) return fail(GBM3D_EUNSUPPORTED, "patch %d: this build supports N = 8", p->patch);
+    if (p->step < 1) return fail(GBM3D_EINVAL, "step %d < 1", p->step);
+    if (p->search_radius < 0) return fail(GBM3D_EINVAL, "search_radius %d < 0", p->search_radius);
+    if (p->levels < 1 || p->levels > 3) return fail(GBM3D_EUNSUPPORTED, "levels %d: supported 1..3", p->levels);
+    for (int k : {p->k1, p->k2})
+        if (!pow2(k) || k < 8 || k > kMaxK) return fail(GBM3D_EUNSUPPORTED, "group size %d: supported 8, 16, 32", k);
+    if (p->k1 % (1 << p->levels)) return fail(GBM3D_EINVAL, "k1 %d not divisible by 2^levels", p->k1);
+    if (p->cycle_spins < 1 || p->cycle_spins > 4)
+        return fail(GBM3D_EUNSUPPORTED, "cycle_spins %d: supported 1..4", p->cycle_spins);
+    if (p->translations < 1 || p->translations > 3)
+        return fail(GBM3D_EUNSUPPORTED, "translations %d: supported 1..3", p->translations);
+    if (p->stages < 1 || p->stages > 2) return fail(GBM3D_EINVAL, "stages %d: 1 or 2", p->stages);
+    if (!(p->eps_w > 0.f) || !isfinite(p->eps_w)) return fail(GBM3D_EINVAL, "eps_w must be positive");
+    if (!isfinite(p->tau_a) || !isfinite(p->tau_b) || !isfinite(p->kaiser_beta) || p->kaiser_beta < 0.f)
+        return fail(GBM3D_EINVAL, "tau_a, tau_b, kaiser_beta must be finite (beta >= 0)");
+    if (match_smem_bytes(p->step, p->search_radius) > 227 * 1024)
+        return fail(GBM3D_EUNSUPPORTED, "search region of R=%d, s=%d exceeds shared memory", p->search_radius,
+                    p->step);
+    return GBM3D_OK;
+}
+
+static int check_image(int H, int W, int pitch)
+{
+    if (H < kPatch || W < kPatch) return fail(GBM3D_EINVAL, "image %dx%d smaller than the %d-pixel block", H, W, kPatch);
+    if (pitch < W) return fail(GBM3D_EINVAL, "pitch %d < W %d", pitch, W);
+    if ((long long)H * W >= (1ll << 31) - 1 || (long long)H * pitch >= (1ll << 40))
+        return fail(GBM3D_EINVAL, "image %dx%d too large for int32 block indices", H, W);
+    return GBM3D_OK;
+}
+
+static int check_window(int H, int W, int R, int K)
+{
+    const long long wy = (H - kPatch < R ? H - kPatch : R) + 1, wx = (W - kPatch < R ? W - kPatch : R) + 1;
+    if (wy * wx < K)
+        return fail(GBM3D_EINVAL, "search window holds %lld blocks, fewer than K = %d", wy * wx, K);
+    return GBM3D_OK;
+}
+
+// Kaiser window kappa[n] = I0(beta sqrt(1 - (2n/(N-1) - 1)^2)) / I0(beta), with
+// I0 summed from its power series in double precision.
+static double bessel_i0(double x)
+{
+    double s = 1.0, t = 1.0;
+    for (int k = 1; k < 100; k++) {
+        t *= 0.5 * x / k;
+        s += t * t;
+    }
+    return s;
+}
+
+static void kaiser8(float beta, float *out)
+{
+    for (int n = 0; n < kPatch; n++) {
+        if (beta <= 0.f) {
+            out[n] = 1.f;
+            continue;
+        }
+        const double r = 2.0 * n / (kPatch - 1) - 1.0;
+        out[n] = (float)(bessel_i0(beta * sqrt(fmax(0.0, 1.0 - r * r))) / bessel_i0(beta));
+    }
+}
+
+struct Sizes {
+    int By, Bx, G, Kmax;
+    HtGeom ht;
+    AggLayout agg1, agg2;
+    size_t sub;                                 // shared scratch for HT / aggregation
+    size_t idx, groups, w, y1, zs, ys, y1s, total; // byte offsets of the denoise layout
+};
+
+static Sizes sizes(int H, int W, const gbm3d_params *p)
+{
+    Sizes z{};
+    z.By = grid_count(H, kPatch, p->step);
+    z.Bx = grid_count(W, kPatch, p->step);
+    z.G = z.By * z.Bx;
+    z.Kmax = p->k1 > p->k2 ? p->k1 : p->k2;
+    z.ht = ht_geom(z.By, z.Bx, p->k1, p->levels);
+    z.agg1 = agg_layout(H, W, z.G, p->k1);
+    z.agg2 = agg_layout(H, W, z.G, p->k2);
+    z.sub = z.ht.bytes;
+    if (z.agg1.bytes > z.sub) z.sub = z.agg1.bytes;
+    if (z.agg2.bytes > z.sub) z.sub = z.agg2.bytes;
+    const size_t img = align_up((size_t)H * W * sizeof(float));
+    size_t o = align_up(z.sub);
+    z.idx = o;
+    o += align_up((size_t)z.G * z.Kmax * sizeof(int32_t));
+    z.groups = o;
+    o += align_up((size_t)z.G * z.Kmax * kPatch * kPatch * sizeof(float));
+    z.w = o;
+    o += align_up((size_t)z.G * sizeof(float));
+    z.y1 = o;
+    o += img;
+    if (p->translations > 1) {
+        z.zs = o;
+        o += img;
+        z.ys = o;
+        o += img;
+        z.y1s = o;
+        o += img;
+    }
+    z.total = o;
+    return z;
+}
+
+static bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// ---- one stage on (possibly shifted) images ------------------------------
+static int run_stage1(const float *z, int zp, int H, int W, float sigma, const gbm3d_params *p, const Sizes &S,
+                      char *ws, float *out, int op, cudaStream_t st)
+{
+    int32_t *idx = (int32_t *)(ws + S.idx);
+    float *groups = (float *)(ws + S.groups), *w = (float *)(ws + S.w);
+    cudaError_t e = launch_match(z, H, W, zp, S.By, S.Bx, p->step, p->search_radius, p->k1, idx, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "match (stage 1)");
+    e = launch_filter_ht(z, H, W, zp, idx, S.ht, sigma, p->tau_a, p->tau_b, p->cycle_spins, p->eps_w, groups, w, ws,
+                         st);
+    if (e != cudaSuccess) return cuda_fail(e, "filter_ht");
+    float win[8];
+    kaiser8(0.f, win);
+    e = launch_aggregate(groups, w, idx, S.G, p->k1, H, W, op, win, out, ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "aggregate (stage 1)");
+    return GBM3D_OK;
+}
+
+static int run_stage2(const float *z, int zp, const float *y1, int yp, int H, int W, float sigma,
+                      const gbm3d_params *p, const Sizes &S, char *ws, float *out, int op, cudaStream_t st)
+{
+    int32_t *idx = (int32_t *)(ws + S.idx);
+    float *groups = (float *)(ws + S.groups), *w = (float *)(ws + S.w);
+    cudaError_t e = launch_match(y1, H, W, yp, S.By, S.Bx, p->step, p->search_radius, p->k2, idx, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "match (stage 2)");
+    e = launch_filter_wiener(z, zp, y1, yp, H, W, idx, S.G, p->k2, sigma, p->eps_w, groups, w, st);
+    if (e != cudaSuccess) return cuda_fail(e, "filter_wiener");
+    float win[8];
+    kaiser8(p->kaiser_beta, win);
+    e = launch_aggregate(groups, w, idx, S.G, p->k2, H, W, op, win, out, ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "aggregate (stage 2)");
+    return GBM3D_OK;
+}
+
+// Circular 2-D shift: dst[y][x] (+)= scale * src[y - h][x - h] (periodic).
+__global__ void k_shift(const float *__restrict__ src, int sp, float *__restrict__ dst, int dp, int H, int W, int h,
+                        float scale, int acc)
+{
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= W || y >= H) return;
+    int ys = (y - h) % H, xs = (x - h) % W;
+    if (ys < 0) ys += H;
+    if (xs < 0) xs += W;
+    const float v = scale * src[(size_t)ys * sp + xs];
+    float *o = dst + (size_t)y * dp + x;
+    *o = acc ? *o + v : v;
+}
+
+cudaError_t launch_shift(const float *src, int spitch, float *dst, int dpitch, int H, int W, int h, float scale,
+                         int accumulate, cudaStream_t st)
+{
+    dim3 grid((W + 31) / 32, (H + 7) / 8);
+    k_shift<<<grid, 256, 0, st>>>(src, spitch, dst, dpitch, H, W, h, scale, accumulate);
+    return cudaGetLastError();
+}
+
+} // namespace gbm3d
+
+using namespace gbm3d;
+
+extern "C" {
+
+const char *gbm3d_last_error_string(void) { return g_err; }
+
+const char *gbm3d_version(void) { return "gbm3d 0.1 (sm_103a)"; }
+
+int gbm3d_params_default(gbm3d_params *p, int preset)
+{
+    if (!p) return fail(GBM3D_EINVAL, "params is NULL");
+    if (preset != 0 && preset != 1) return fail(GBM3D_EINVAL, "unknown preset %d", preset);
+    p->patch = 8;
+    p->levels = 3;
+    p->cycle_spins = 2;
+    p->stages = 2;
+    p->tau_a = 3.6f;
+    p->tau_b = 0.3f;
+    p->kaiser_beta = 2.0f;
+    p->eps_w = 1e-8f;
+    if (preset == 0) {
+        p->step = 3;
+        p->search_radius = 19;
+        p->k1 = 16;
+        p->k2 = 32;
+        p->translations = 1;
+    } else {
+        p->step = 8;
+        p->search_radius = 16;
+        p->k1 = 16;
+        p->k2 = 16;
+        p->translations = 2;
+    }
+    g_err[0] = 0;
+    return GBM3D_OK;
+}
+
+int gbm3d_grid_dims(int H, int W, const gbm3d_params *p, int *By, int *Bx)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if (!By || !Bx) return fail(GBM3D_EINVAL, "By/Bx is NULL");
+    if ((st = check_image(H, W, W))) return st;
+    *By = grid_count(H, kPatch, p->step);
+    *Bx = grid_count(W, kPatch, p->step);
+    return GBM3D_OK;
+}
+
+int gbm3d_workspace_bytes(int H, int W, const gbm3d_params *p, size_t *bytes)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if (!bytes) return fail(GBM3D_EINVAL, "bytes is NULL");
+    if ((st = check_image(H, W, W))) return st;
+    *bytes = sizes(H, W, p).total;
+    return GBM3D_OK;
+}
+
+int gbm3d_match(const float *img, int H, int W, int pitch, const gbm3d_params *p, int K, int32_t *idx, float *dist,
+                void *ws, gbm3d_stream_t stream)
+{
+    (void)ws;
+    int st = check_params(p);
+    if (st) return st;
+    if ((st = check_image(H, W, pitch))) return st;
+    if (!img || !idx) return fail(GBM3D_EINVAL, "img/idx is NULL");
+    if (K < 2 || K > kMaxK) return fail(GBM3D_EUNSUPPORTED, "K = %d: supported 2..32", K);
+    if ((st = check_window(H, W, p->search_radius, K))) return st;
+    const int By = grid_count(H, kPatch, p->step), Bx = grid_count(W, kPatch, p->step);
+    cudaError_t e = launch_match(img, H, W, pitch, By, Bx, p->step, p->search_radius, K, idx, dist,
+                                 (cudaStream_t)stream);
+    return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "match");
+}
+
+int gbm3d_filter_ht(const float *noisy, int H, int W, int pitch, const int32_t *idx, float sigma,
+                    const gbm3d_params *p, float *groups, float *w, void *ws, gbm3d_stream_t stream)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if ((st = check_image(H, W, pitch))) return st;
+    if (!noisy || !idx || !groups || !w || !ws) return fail(GBM3D_EINVAL, "null pointer argument");
+    if (!(sigma >= 0.f) || !isfinite(sigma)) return fail(GBM3D_EINVAL, "sigma must be finite and >= 0");
+    if (!aligned(ws, kAlign) || !aligned(groups, 16)) return fail(GBM3D_EINVAL, "ws must be 256-byte aligned");
+    const Sizes S = sizes(H, W, p);
+    cudaError_t e = launch_filter_ht(noisy, H, W, pitch, idx, S.ht, sigma, p->tau_a, p->tau_b, p->cycle_spins,
+                                     p->eps_w, groups, w, ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "filter_ht");
+}
+
+int gbm3d_filter_wiener(const float *noisy, const float *pilot, int H, int W, int pitch, const int32_t *idx,
+                        float sigma, const gbm3d_params *p, float *groups, float *w, void *ws, gbm3d_stream_t stream)
+{
+    (void)ws;
+    int st = check_params(p);
+    if (st) return st;
+    if ((st = check_image(H, W, pitch))) return st;
+    if (!noisy || !pilot || !idx || !groups || !w) return fail(GBM3D_EINVAL, "null pointer argument");
+    if (!(sigma >= 0.f) || !isfinite(sigma)) return fail(GBM3D_EINVAL, "sigma must be finite and >= 0");
+    if (!aligned(groups, 16)) return fail(GBM3D_EINVAL, "groups must be 16-byte aligned");
+    const int G = grid_count(H, kPatch, p->step) * grid_count(W, kPatch, p->step);
+    cudaError_t e = launch_filter_wiener(noisy, pitch, pilot, pitch, H, W, idx, G, p->k2, sigma, p->eps_w, groups, w,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "filter_wiener");
+}
+
+int gbm3d_aggregate(const float *groups, const float *w, const int32_t *idx, int K, int H, int W, int pitch,
+                    const gbm3d_params *p, float window_beta, float *out, void *ws, gbm3d_stream_t stream)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if ((st = check_image(H, W, pitch))) return st;
+    if (!groups || !w || !idx || !out || !ws) return fail(GBM3D_EINVAL, "null pointer argument");
+    if (!pow2(K) || K > kMaxK) return fail(GBM3D_EUNSUPPORTED, "K = %d: supported powers of two up to 32", K);
+    if (K > (p->k1 > p->k2 ? p->k1 : p->k2))
+        return fail(GBM3D_EINVAL, "K = %d exceeds max(k1, k2): the workspace is sized by the params", K);
+    if (!(window_beta >= 0.f) || !isfinite(window_beta)) return fail(GBM3D_EINVAL, "window_beta must be >= 0");
+    if (!aligned(ws, kAlign)) return fail(GBM3D_EINVAL, "ws must be 256-byte aligned");
+    const int G = grid_count(H, kPatch, p->step) * grid_count(W, kPatch, p->step);
+    float win[8];
+    kaiser8(window_beta, win);
+    cudaError_t e = launch_aggregate(groups, w, idx, G, K, H, W, pitch, win, out, ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "aggregate");
+}
+
+int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, const gbm3d_params *p, float *out,
+                  void *ws, gbm3d_stream_t stream)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if ((st = check_image(H, W, pitch))) return st;
+    if (!noisy || !out || !ws) return fail(GBM3D_EINVAL, "null pointer argument");
+    if (noisy == out) return fail(GBM3D_EINVAL, "out must not alias noisy");
+    if (!(sigma >= 0.f) || !isfinite(sigma)) return fail(GBM3D_EINVAL, "sigma must be finite and >= 0");
+    if (!aligned(ws, kAlign)) return fail(GBM3D_EINVAL, "ws must be 256-byte aligned");
+    if ((st = check_window(H, W, p->search_radius, p->k1 > p->k2 ? p->k1 : p->k2))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Sizes S = sizes(H, W, p);
+    char *base = (char *)ws;
+    float *y1 = (float *)(base + S.y1);
+    const int T = p->translations;
+    const int hs[3] = {0, kPatch / 4, kPatch / 2};
+    float *final_out = p->stages == 1 ? out : nullptr;
+    // stage 1: Y1 = (1/T) sum_h S_{-h} phi1(S_h Z)
+    if (T == 1) {
+        st = run_stage1(noisy, pitch, H, W, sigma, p, S, base, final_out ? out : y1, final_out ? pitch : W, s);
+        if (st) return st;
+    } else {
+        float *zs = (float *)(base + S.zs), *ys = (float *)(base + S.ys);
+        float *acc = final_out ? out : y1;
+        const int ap = final_out ? pitch : W;
+        for (int t = 0; t < T; t++) {
+            cudaError_t e = launch_shift(noisy, pitch, zs, W, H, W, hs[t], 1.f, 0, s);
+            if (e != cudaSuccess) return cuda_fail(e, "shift");
+            if ((st = run_stage1(zs, W, H, W, sigma, p, S, base, ys, W, s))) return st;
+            e = launch_shift(ys, W, acc, ap, H, W, -hs[t], 1.f / T, t > 0, s);
+            if (e != cudaSuccess) return cuda_fail(e, "shift");
+        }
+    }
+    if (p->stages == 1) return GBM3D_OK;
+    // stage 2: Y2 = (1/T) sum_h S_{-h} phi2(S_h Z, S_h Y1)
+    if (T == 1) return run_stage2(noisy, pitch, y1, W, H, W, sigma, p, S, base, out, pitch, s);
+    float *zs = (float *)(base + S.zs), *ys = (float *)(base + S.ys), *y1s = (float *)(base + S.y1s);
+    for (int t = 0; t < T; t++) {
+        cudaError_t e = launch_shift(noisy, pitch, zs, W, H, W, hs[t], 1.f, 0, s);
+        if (e == cudaSuccess) e = launch_shift(y1, W, y1s, W, H, W, hs[t], 1.f, 0, s);
+        if (e != cudaSuccess) return cuda_fail(e, "shift");
+        if ((st = run_stage2(zs, W, y1s, W, H, W, sigma, p, S, base, ys, W, s))) return st;
+        e = launch_shift(ys, W, out, pitch, H, W, -hs[t], 1.f / T, t > 0, s);
+        if (e != cudaSuccess) return cuda_fail(e, "shift");
+    }
+    return GBM3D_OK;
+}
+
+} // extern "C"

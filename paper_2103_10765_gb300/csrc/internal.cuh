@@ -1,0 +1,91 @@
+// internal.cuh -- declarations shared by the CUDA translation units of
+// libgbm3d (launch wrappers, workspace layout helpers).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "gbm3d.h"
+
+namespace gbm3d {
+
+constexpr int kPatch = 8;      // the block side this build is specialised for
+constexpr int kMaxK = 32;      // largest group size (one warp lane per list slot)
+constexpr size_t kAlign = 256; // workspace sub-buffer alignment
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Reference-grid count: positions 0, s, 2s, ... <= M-N plus M-N itself.
+inline int grid_count(int M, int N, int s)
+{
+    if (M < N || N <= 0 || s <= 0) return 0;
+    int n = (M - N) / s + 1;
+    return ((M - N) % s) ? n + 1 : n;
+}
+
+// Position of reference p on a grid of stride s (the last one clamps to M-N).
+__host__ __device__ inline int grid_pos(int p, int s, int M, int N)
+{
+    int v = p * s;
+    return v < M - N ? v : M - N;
+}
+
+// Top-left (k, l) of block position pos = k*W + l, clamped so that an
+// out-of-range entry in a caller-supplied match list can never address
+// memory outside the image (such entries yield garbage, not a fault).
+__device__ __forceinline__ void block_kl(int pos, int H, int W, int &k, int &l)
+{
+    if (pos < 0 || pos >= H * W) pos = 0;
+    k = pos / W;
+    l = pos - k * W;
+    k = k < H - kPatch ? k : H - kPatch;
+    l = l < W - kPatch ? l : W - kPatch;
+}
+
+// True when pos is a valid block top-left for an H x W image.
+__device__ __forceinline__ bool block_ok(int pos, int H, int W)
+{
+    if (pos < 0 || pos >= H * W) return false;
+    const int k = pos / W, l = pos - k * W;
+    return k <= H - kPatch && l <= W - kPatch;
+}
+
+// Geometry of the stage-1 mosaic volume and of its wavelet pyramid.
+struct HtGeom {
+    int By, Bx, K;          // groups along y, x; blocks per group
+    int Yd, Xd;             // mosaic dims (By*N, Bx*N)
+    int levels;
+    size_t level_elems[4];  // elements of the coefficient buffer of level l (1-based)
+    size_t level_off[4];    // byte offset of each level buffer in the HT scratch
+    size_t bytes;           // total HT scratch
+};
+HtGeom ht_geom(int By, int Bx, int K, int levels);
+
+struct AggLayout {
+    size_t cnt, off, cursor, list, bsum, bytes; // byte offsets and total
+    int npos, nblk;
+};
+AggLayout agg_layout(int H, int W, int G, int K);
+
+size_t match_smem_bytes(int s, int R);
+
+// ---- launch wrappers (each returns cudaGetLastError()) -------------------
+cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+                         int32_t *idx, float *dist, cudaStream_t st);
+
+cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
+                             float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, float *groups,
+                             float *w, void *ht_ws, cudaStream_t st);
+
+cudaError_t launch_filter_wiener(const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
+                                 const int32_t *idx, int G, int K, float sigma, float eps_w, float *groups, float *w,
+                                 cudaStream_t st);
+
+cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t *idx, int G, int K, int H, int W,
+                             int pitch, const float *window8, float *out, void *agg_ws, cudaStream_t st);
+
+cudaError_t launch_shift(const float *src, int spitch, float *dst, int dpitch, int H, int W, int h, float scale,
+                         int accumulate, cudaStream_t st);
+
+} // namespace gbm3d

@@ -1,0 +1,213 @@
+"""Thin Python binding of libgbm3d (the C ABI in include/gbm3d.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors (torch provides device memory
+and the current stream); outputs are allocated here with torch.  There is no
+CPU fallback: if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+_lib = None
+
+
+class Gbm3dError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gbm3d status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of gbm3d_params."""
+    _fields_ = [(n, ctypes.c_int) for n in
+                ("patch", "step", "search_radius", "k1", "k2", "levels", "cycle_spins", "translations", "stages")] + \
+               [(n, ctypes.c_float) for n in ("tau_a", "tau_b", "kaiser_beta", "eps_w")]
+
+    def replace(self, **kw) -> "Params":
+        q = Params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(self), ctypes.sizeof(Params))
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return q
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgbm3d.so (building it first if it is missing and allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libgbm3d not built: {path} is missing (run __graft_entry__.build())")
+        _build.build_library()
+    lib = ctypes.CDLL(path)
+    vp, ci, cf, P = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.POINTER(Params)
+    lib.gbm3d_params_default.argtypes = [P, ci]
+    lib.gbm3d_grid_dims.argtypes = [ci, ci, P, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    lib.gbm3d_workspace_bytes.argtypes = [ci, ci, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.gbm3d_match.argtypes = [vp, ci, ci, ci, P, ci, vp, vp, vp, vp]
+    lib.gbm3d_filter_ht.argtypes = [vp, ci, ci, ci, vp, cf, P, vp, vp, vp, vp]
+    lib.gbm3d_filter_wiener.argtypes = [vp, vp, ci, ci, ci, vp, cf, P, vp, vp, vp, vp]
+    lib.gbm3d_aggregate.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp, vp]
+    lib.gbm3d_denoise.argtypes = [vp, ci, ci, ci, cf, P, vp, vp, vp]
+    lib.gbm3d_last_error_string.restype = ctypes.c_char_p
+    lib.gbm3d_version.restype = ctypes.c_char_p
+    for name in ("gbm3d_params_default", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
+                 "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise"):
+        getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise Gbm3dError(status, load().gbm3d_last_error_string().decode())
+
+
+def params_default(preset: int = 0) -> Params:
+    p = Params()
+    _check(load().gbm3d_params_default(ctypes.byref(p), preset))
+    return p
+
+
+def grid_dims(H: int, W: int, p: Params | None = None):
+    p = p or params_default()
+    by, bx = ctypes.c_int(), ctypes.c_int()
+    _check(load().gbm3d_grid_dims(H, W, ctypes.byref(p), ctypes.byref(by), ctypes.byref(bx)))
+    return by.value, bx.value
+
+
+def workspace_bytes(H: int, W: int, p: Params | None = None) -> int:
+    p = p or params_default()
+    n = ctypes.c_size_t()
+    _check(load().gbm3d_workspace_bytes(H, W, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def workspace(H: int, W: int, p: Params | None = None, device=None) -> torch.Tensor:
+    """Device scratch for any call on an H x W image (torch allocations are 256-byte aligned)."""
+    return torch.empty(max(workspace_bytes(H, W, p), 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def _stream(t: torch.Tensor):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _img(t: torch.Tensor, name: str):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.stride(1) == 1):
+        raise ValueError(f"{name} must be a 2-D float32 CUDA tensor with unit column stride")
+    return t.shape[0], t.shape[1], t.stride(0)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def match(img: torch.Tensor, K: int, p: Params | None = None, with_dist: bool = False):
+    """Block matching: (idx int32 [G, K], dist float32 [G, K] or None)."""
+    p = p or params_default()
+    H, W, pitch = _img(img, "img")
+    by, bx = grid_dims(H, W, p)
+    idx = torch.empty((by * bx, K), dtype=torch.int32, device=img.device)
+    dist = torch.empty((by * bx, K), dtype=torch.float32, device=img.device) if with_dist else None
+    _check(load().gbm3d_match(_ptr(img), H, W, pitch, ctypes.byref(p), K, _ptr(idx), _ptr(dist), None,
+                              _stream(img)))
+    return idx, dist
+
+
+def filter_ht(noisy: torch.Tensor, idx: torch.Tensor, sigma: float, p: Params | None = None,
+              ws: torch.Tensor | None = None):
+    """Stage-1 global hard thresholding: (groups [G, K1, 8, 8], w [G])."""
+    p = p or params_default()
+    H, W, pitch = _img(noisy, "noisy")
+    G = idx.shape[0]
+    ws = ws if ws is not None else workspace(H, W, p, noisy.device)
+    groups = torch.empty((G, p.k1, 8, 8), dtype=torch.float32, device=noisy.device)
+    w = torch.empty(G, dtype=torch.float32, device=noisy.device)
+    _check(load().gbm3d_filter_ht(_ptr(noisy), H, W, pitch, _ptr(idx.contiguous()), float(sigma), ctypes.byref(p),
+                                  _ptr(groups), _ptr(w), _ptr(ws), _stream(noisy)))
+    return groups, w
+
+
+def filter_wiener(noisy: torch.Tensor, pilot: torch.Tensor, idx: torch.Tensor, sigma: float,
+                  p: Params | None = None):
+    """Stage-2 empirical Wiener filter: (groups [G, K2, 8, 8], w [G])."""
+    p = p or params_default()
+    H, W, pitch = _img(noisy, "noisy")
+    if _img(pilot, "pilot") != (H, W, pitch):
+        raise ValueError("noisy and pilot must share shape and pitch")
+    G = idx.shape[0]
+    groups = torch.empty((G, p.k2, 8, 8), dtype=torch.float32, device=noisy.device)
+    w = torch.empty(G, dtype=torch.float32, device=noisy.device)
+    _check(load().gbm3d_filter_wiener(_ptr(noisy), _ptr(pilot), H, W, pitch, _ptr(idx.contiguous()), float(sigma),
+                                      ctypes.byref(p), _ptr(groups), _ptr(w), None, _stream(noisy)))
+    return groups, w
+
+
+def aggregate(groups: torch.Tensor, w: torch.Tensor, idx: torch.Tensor, H: int, W: int,
+              p: Params | None = None, window_beta: float = 0.0, ws: torch.Tensor | None = None,
+              out: torch.Tensor | None = None) -> torch.Tensor:
+    """Weighted aggregation of filtered blocks into an H x W image."""
+    p = p or params_default()
+    K = idx.shape[1]
+    out = out if out is not None else torch.empty((H, W), dtype=torch.float32, device=groups.device)
+    _, _, pitch = _img(out, "out")
+    ws = ws if ws is not None else workspace(H, W, p, groups.device)
+    _check(load().gbm3d_aggregate(_ptr(groups.contiguous()), _ptr(w.contiguous()), _ptr(idx.contiguous()), K, H, W,
+                                  pitch, ctypes.byref(p), float(window_beta), _ptr(out), _ptr(ws), _stream(groups)))
+    return out
+
+
+def denoise(noisy: torch.Tensor, sigma: float, p: Params | None = None, ws: torch.Tensor | None = None,
+            out: torch.Tensor | None = None) -> torch.Tensor:
+    """Two-stage (or stage-1-only) G-BM3D of a device image."""
+    p = p or params_default()
+    H, W, pitch = _img(noisy, "noisy")
+    out = out if out is not None else torch.empty_like(noisy)
+    if _img(out, "out")[2] != pitch:
+        raise ValueError("out must have the same pitch as noisy")
+    ws = ws if ws is not None else workspace(H, W, p, noisy.device)
+    _check(load().gbm3d_denoise(_ptr(noisy), H, W, pitch, float(sigma), ctypes.byref(p), _ptr(out), _ptr(ws),
+                                _stream(noisy)))
+    return out
+
+
+class HostDenoiser:
+    """End-to-end use from host memory: pinned host -> device copy, denoise,
+    device -> host copy, on one stream.  Buffers are allocated once per shape."""
+
+    def __init__(self, H: int, W: int, p: Params | None = None, device="cuda"):
+        self.p = p or params_default()
+        self.H, self.W = H, W
+        self.dev_in = torch.empty((H, W), dtype=torch.float32, device=device)
+        self.dev_out = torch.empty((H, W), dtype=torch.float32, device=device)
+        self.host_out = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+        self.ws = workspace(H, W, self.p, device)
+
+    @property
+    def h2d_bytes(self) -> int:
+        return self.H * self.W * 4
+
+    d2h_bytes = h2d_bytes
+
+    def __call__(self, host_noisy: torch.Tensor, sigma: float) -> torch.Tensor:
+        self.dev_in.copy_(host_noisy, non_blocking=True)
+        denoise(self.dev_in, sigma, self.p, self.ws, self.dev_out)
+        self.host_out.copy_(self.dev_out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return self.host_out

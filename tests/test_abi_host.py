@@ -1,0 +1,119 @@
+"""The C-ABI library loads, exports every symbol include/gbm3d.h declares, and
+its host-side logic (presets, grid sizes, workspace sizes, argument
+validation) behaves as documented.  No call here reaches the GPU: every
+validation failure returns before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_2103_10765_gb300 import build, gbm3d
+    build.build_library()
+    return gbm3d
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gbm3d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbm3d_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(g):
+    lib = g.load()
+    names = declared_functions()
+    assert "gbm3d_denoise" in names and len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version(g):
+    assert b"gbm3d" in g.load().gbm3d_version()
+
+
+def test_presets(g):
+    p = g.params_default(0)
+    assert (p.patch, p.step, p.search_radius, p.k1, p.k2, p.levels, p.cycle_spins, p.translations, p.stages) == \
+        (8, 3, 19, 16, 32, 3, 2, 1, 2)
+    assert abs(p.tau_a - 3.6) < 1e-6 and abs(p.tau_b - 0.3) < 1e-6 and p.kaiser_beta == 2.0
+    q = g.params_default(1)
+    assert (q.step, q.search_radius, q.k1, q.translations) == (8, 16, 16, 2)
+    with pytest.raises(g.Gbm3dError):
+        g.params_default(7)
+
+
+def test_grid_dims_closed_form(g, orc):
+    for H, W in ((256, 256), (512, 512), (1024, 1024), (37, 101), (8, 8)):
+        assert g.grid_dims(H, W) == (len(orc.grid(H, 8, 3)), len(orc.grid(W, 8, 3)))
+    assert g.grid_dims(1024, 1024) == (340, 340)
+
+
+def test_workspace_monotone(g):
+    a = g.workspace_bytes(256, 256)
+    b = g.workspace_bytes(512, 512)
+    c = g.workspace_bytes(1024, 1024)
+    assert 0 < a < b < c
+    # groups buffer alone: G * K2 * 64 floats
+    assert c >= 340 * 340 * 32 * 64 * 4
+    assert g.workspace_bytes(256, 256, g.params_default().replace(translations=3)) > a
+
+
+def _status(fn, *args):
+    return fn(*args)
+
+
+def test_validation_errors(g):
+    lib = g.load()
+    p = g.params_default()
+    P = ctypes.byref(p)
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
+    # image smaller than a block
+    assert lib.gbm3d_match(fake, 7, 64, 64, P, 16, fake, None, None, None) == g.EINVAL
+    # pitch < W
+    assert lib.gbm3d_match(fake, 64, 64, 32, P, 16, fake, None, None, None) == g.EINVAL
+    # null pointers
+    assert lib.gbm3d_match(None, 64, 64, 64, P, 16, fake, None, None, None) == g.EINVAL
+    assert lib.gbm3d_denoise(fake, 64, 64, 64, ctypes.c_float(0.1), P, None, fake, None) == g.EINVAL
+    # out aliasing noisy
+    assert lib.gbm3d_denoise(fake, 64, 64, 64, ctypes.c_float(0.1), P, fake, fake, None) == g.EINVAL
+    # negative or non-finite sigma
+    assert lib.gbm3d_denoise(fake, 64, 64, 64, ctypes.c_float(-1.0), P, ctypes.c_void_p(0x2000), fake,
+                             None) == g.EINVAL
+    assert lib.gbm3d_denoise(fake, 64, 64, 64, ctypes.c_float(float("nan")), P, ctypes.c_void_p(0x2000), fake,
+                             None) == g.EINVAL
+    # search window too small for K: 9 x 9 image has 2 x 2 block positions
+    assert lib.gbm3d_match(fake, 9, 9, 9, P, 16, fake, None, None, None) == g.EINVAL
+    # unsupported parameters
+    for bad in (dict(patch=16), dict(k1=64), dict(levels=4), dict(k2=12), dict(translations=4)):
+        q = p.replace(**bad)
+        st = lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None)
+        assert st in (g.EINVAL, g.EUNSUPPORTED), bad
+    assert b"" != lib.gbm3d_last_error_string()
+    # misaligned workspace
+    assert lib.gbm3d_filter_ht(fake, 64, 64, 64, fake, ctypes.c_float(0.1), P, ctypes.c_void_p(0x3000), fake,
+                               ctypes.c_void_p(0x1004), None) == g.EINVAL
+    # unsupported group size for aggregation
+    assert lib.gbm3d_aggregate(fake, fake, fake, 12, 64, 64, 64, P, ctypes.c_float(0.0), fake, fake,
+                               None) == g.EUNSUPPORTED
+
+
+def test_empty_image_rejected(g):
+    lib = g.load()
+    p = g.params_default()
+    by, bx = ctypes.c_int(), ctypes.c_int()
+    assert lib.gbm3d_grid_dims(0, 0, ctypes.byref(p), ctypes.byref(by), ctypes.byref(bx)) == g.EINVAL
+    n = ctypes.c_size_t()
+    assert lib.gbm3d_workspace_bytes(0, 64, ctypes.byref(p), ctypes.byref(n)) == g.EINVAL
+
+
+def test_binding_fails_loudly_without_library(g, monkeypatch, tmp_path):
+    from paper_2103_10765_gb300 import build
+    monkeypatch.setattr(g, "_lib", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        g.load(build_if_missing=False)
