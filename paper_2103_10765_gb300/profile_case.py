@@ -1,0 +1,53 @@
+"""Runs one G-BM3D entry point on a seeded synthetic image, for profilers.
+
+  python -m paper_2103_10765_gb300.profile_case --op match --size 1024 --reps 2
+
+Every op first runs one whole denoise (warm-up, and to make the stage-1
+estimate for stage-2 ops), then `reps` launches of the chosen entry point:
+  match1 / match2   gbm3d_match on the noisy image (K1) / stage-1 estimate (K2)
+  ht                gbm3d_filter_ht        wiener   gbm3d_filter_wiener
+  agg1 / agg2       gbm3d_aggregate of the stage-1 / stage-2 groups
+  denoise           gbm3d_denoise
+"""
+import argparse
+
+import torch
+
+from paper_2103_10765_gb300 import gbm3d, synth
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="match2")
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--sigma", type=float, default=25 / 255)
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    H = W = a.size
+    p = gbm3d.params_default()
+    _, noisy = synth.make_pair(H, W, a.sigma, 1)
+    z = torch.from_numpy(noisy).cuda()
+    ws = gbm3d.workspace(H, W, p)
+    y1 = gbm3d.denoise(z, a.sigma, p.replace(stages=1), ws)
+    idx1, _ = gbm3d.match(z, p.k1, p)
+    idx2, _ = gbm3d.match(y1, p.k2, p)
+    g1, w1 = gbm3d.filter_ht(z, idx1, a.sigma, p, ws)
+    g2, w2 = gbm3d.filter_wiener(z, y1, idx2, a.sigma, p)
+    torch.cuda.synchronize()
+    ops = {
+        "match1": lambda: gbm3d.match(z, p.k1, p),
+        "match2": lambda: gbm3d.match(y1, p.k2, p),
+        "ht": lambda: gbm3d.filter_ht(z, idx1, a.sigma, p, ws),
+        "wiener": lambda: gbm3d.filter_wiener(z, y1, idx2, a.sigma, p),
+        "agg1": lambda: gbm3d.aggregate(g1, w1, idx1, H, W, p, 0.0, ws),
+        "agg2": lambda: gbm3d.aggregate(g2, w2, idx2, H, W, p, p.kaiser_beta, ws),
+        "denoise": lambda: gbm3d.denoise(z, a.sigma, p, ws),
+    }
+    for _ in range(a.reps):
+        ops[a.op]()
+    torch.cuda.synchronize()
+    print(f"profile_case {a.op} {H}x{W} reps={a.reps} ok")
+
+
+if __name__ == "__main__":
+    main()
