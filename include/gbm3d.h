@@ -27,8 +27,9 @@
  *    unless the code is GBM3D_ECUDA.  gbm3d_last_error_string() describes the
  *    last failure of the calling host thread.
  *  - `ws` is caller-owned device scratch of at least gbm3d_workspace_bytes()
- *    bytes, 256-byte aligned.  The library allocates no device memory.  Calls
- *    that share one `ws` must be ordered on one stream.
+ *    bytes, 256-byte aligned.  No call allocates device memory (no cudaMalloc
+ *    or allocating library routine).  Calls that share one `ws` must be
+ *    ordered on one stream.
  *  - Supported now: patch N = 8, K1, K2 in {8, 16, 32}, levels in 1..3,
  *    cycle_spins in 1..4, translations in 1..3.  Other values return
  *    GBM3D_EUNSUPPORTED.
@@ -48,7 +49,7 @@ typedef struct CUstream_st *gbm3d_stream_t; /* same type as cudaStream_t */
 enum {
     GBM3D_OK = 0,
     GBM3D_EINVAL = 1,       /* bad argument (null pointer, size, parameter) */
-    GBM3D_ENOMEM = 2,       /* workspace too small */
+    GBM3D_ENOMEM = 2,       /* scratch too small for the request */
     GBM3D_ECUDA = 3,        /* a CUDA launch or runtime call failed */
     GBM3D_ETIMEOUT = 4,     /* reserved: a bounded device-side wait gave up */
     GBM3D_EUNSUPPORTED = 5  /* valid but not implemented for this build */
@@ -145,6 +146,27 @@ int gbm3d_filter_wiener(const float *noisy, const float *pilot, int H, int W, in
 int gbm3d_aggregate(const float *groups, const float *w, const int32_t *idx, int K, int H, int W,
                     int pitch, const gbm3d_params *p, float window_beta, float *out, void *ws,
                     gbm3d_stream_t stream);
+
+/* Aggregation exactly as gbm3d_aggregate, for callers that cannot allocate
+ * device memory -- for example code running inside a host framework that owns
+ * every device allocation and hands plugins a fixed budget, or a real-time
+ * loop that must not allocate once it is running -- and so cannot provide
+ * `ws`.  The paper has no counterpart; this is a convenience of the library.
+ *   Scratch: a fixed 8 MiB array in device memory, part of the library image
+ *   (every GPU that loads the library holds it until the process exits).
+ *   That covers images up to about 512 x 512 with K = 32 (the CSR index needs
+ *   12 (H W + 1) + 4 G K bytes); larger sizes return GBM3D_ENOMEM without
+ *   launching anything.
+ *   The call allocates nothing.  Its first call on a device looks up the
+ *   array's device address (cudaGetSymbolAddress) and caches it; make that
+ *   first call before any stream capture on that device.
+ *   All calls on a device share the one array, and each call clears the
+ *   parts it needs zeroed: calls whose executions overlap on the GPU (other
+ *   streams, other host threads) race on it and must be serialised by the
+ *   caller.  Arguments and result as gbm3d_aggregate. */
+int gbm3d_aggregate_noalloc(const float *groups, const float *w, const int32_t *idx, int K, int H, int W,
+                            int pitch, const gbm3d_params *p, float window_beta, float *out,
+                            gbm3d_stream_t stream);
 
 /* Whole method (Sec. 1.1 BM3D1/BM3D2 with translation averaging, eq.
  * firstEst): input the noisy image and the noise standard deviation, get the

@@ -7,9 +7,16 @@
 // pixel walks the N x N top-left positions that cover it, in a fixed order,
 // summing numerator and denominator with Kahan compensation.  No floating-
 // point atomics: the result does not depend on scheduling.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace gbm3d {
+
+// Fixed device scratch for gbm3d_aggregate_noalloc (callers that cannot
+// allocate device memory).  Every GPU that loads this library holds these
+// bytes until the process exits; all calls on a device share them.
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
 namespace {
 
 constexpr int kScanBlock = 1024; // elements per scan block (256 threads x 4)
@@ -166,6 +173,30 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
 }
 
 } // namespace
+
+// Device address of g_fixed_scratch on the current device.  In host code the
+// symbol names a host-side stand-in, so the address is asked of the runtime
+// once per device (with that device current) and cached.
+cudaError_t fixed_scratch(void **ptr)
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static void *cache[kMaxDev] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < kMaxDev && cache[dev]) {
+        *ptr = cache[dev];
+        return cudaSuccess;
+    }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDev) cache[dev] = p;
+    *ptr = p;
+    return cudaSuccess;
+}
 
 AggLayout agg_layout(int H, int W, int G, int K)
 {

@@ -320,6 +320,29 @@ int gbm3d_aggregate(const float *groups, const float *w, const int32_t *idx, int
     return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "aggregate");
 }
 
+int gbm3d_aggregate_noalloc(const float *groups, const float *w, const int32_t *idx, int K, int H, int W,
+                            int pitch, const gbm3d_params *p, float window_beta, float *out, gbm3d_stream_t stream)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if ((st = check_image(H, W, pitch))) return st;
+    if (!groups || !w || !idx || !out) return fail(GBM3D_EINVAL, "null pointer argument");
+    if (!pow2(K) || K > kMaxK) return fail(GBM3D_EUNSUPPORTED, "K = %d: supported powers of two up to 32", K);
+    if (!(window_beta >= 0.f) || !isfinite(window_beta)) return fail(GBM3D_EINVAL, "window_beta must be >= 0");
+    const int G = grid_count(H, kPatch, p->step) * grid_count(W, kPatch, p->step);
+    const AggLayout L = agg_layout(H, W, G, K);
+    if (L.bytes > kFixedScratchBytes)
+        return fail(GBM3D_ENOMEM, "aggregation of a %dx%d image with K = %d needs %zu bytes of scratch, more than "
+                    "the fixed %zu bytes of gbm3d_aggregate_noalloc", H, W, K, L.bytes, kFixedScratchBytes);
+    void *scratch = nullptr;
+    cudaError_t e = fixed_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "fixed scratch address");
+    float win[8];
+    kaiser8(window_beta, win);
+    e = launch_aggregate(groups, w, idx, G, K, H, W, pitch, win, out, scratch, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "aggregate_noalloc");
+}
+
 int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, const gbm3d_params *p, float *out,
                   void *ws, gbm3d_stream_t stream)
 {

@@ -70,6 +70,11 @@ AggLayout agg_layout(int H, int W, int G, int K);
 
 size_t match_smem_bytes(int s, int R);
 
+// Size of the fixed device scratch used by gbm3d_aggregate_noalloc, and its
+// device address on the current device (looked up once per device).
+constexpr size_t kFixedScratchBytes = size_t(8) << 20;
+cudaError_t fixed_scratch(void **ptr);
+
 // ---- launch wrappers (each returns cudaGetLastError()) -------------------
 cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                          int32_t *idx, float *dist, cudaStream_t st);

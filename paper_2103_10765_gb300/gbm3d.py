@@ -65,10 +65,12 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_filter_wiener.argtypes = [vp, vp, ci, ci, ci, vp, cf, P, vp, vp, vp, vp]
     lib.gbm3d_aggregate.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp, vp]
     lib.gbm3d_denoise.argtypes = [vp, ci, ci, ci, cf, P, vp, vp, vp]
+    lib.gbm3d_aggregate_noalloc.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp]
     lib.gbm3d_last_error_string.restype = ctypes.c_char_p
     lib.gbm3d_version.restype = ctypes.c_char_p
     for name in ("gbm3d_params_default", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
-                 "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise"):
+                 "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise",
+                 "gbm3d_aggregate_noalloc"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -170,6 +172,17 @@ def aggregate(groups: torch.Tensor, w: torch.Tensor, idx: torch.Tensor, H: int, 
     ws = ws if ws is not None else workspace(H, W, p, groups.device)
     _check(load().gbm3d_aggregate(_ptr(groups.contiguous()), _ptr(w.contiguous()), _ptr(idx.contiguous()), K, H, W,
                                   pitch, ctypes.byref(p), float(window_beta), _ptr(out), _ptr(ws), _stream(groups)))
+    return out
+
+
+def aggregate_noalloc(groups: torch.Tensor, w: torch.Tensor, idx: torch.Tensor, H: int, W: int, out: torch.Tensor,
+                      p: Params | None = None, window_beta: float = 0.0) -> torch.Tensor:
+    """gbm3d_aggregate_noalloc: aggregation into a caller-provided `out` using
+    the library's fixed device scratch (no workspace, no allocation)."""
+    p = p or params_default()
+    _, _, pitch = _img(out, "out")
+    _check(load().gbm3d_aggregate_noalloc(_ptr(groups), _ptr(w), _ptr(idx), idx.shape[1], H, W, pitch,
+                                          ctypes.byref(p), float(window_beta), _ptr(out), _stream(groups)))
     return out
 
 
