@@ -124,6 +124,13 @@ __global__ void k_sort(const int *__restrict__ off, int npos, int *__restrict__ 
     }
 }
 
+// slot_of[entry] = its index in the position-sorted entry list.
+__global__ void k_slots(const int *__restrict__ list, const int *__restrict__ total, int *__restrict__ slot_of)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < *total) slot_of[list[j]] = j;
+}
+
 struct Win8 {
     float v[8];
 };
@@ -136,6 +143,14 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     s = t;
 }
 
+// One thread per output pixel, eight lanes per 8-pixel row segment: the lanes
+// of a segment walk the same block positions and entries together, so each
+// patch-row read is one 32-byte sector shared by the 8 lanes (lanes the block
+// does not cover sit the entry out).  Per pixel the order is fixed -- block
+// rows k ascending, columns l ascending, entries ascending -- and numerator
+// and denominator are Kahan-compensated FP32 sums.
+constexpr int kSegX = 8, kSegRows = 4; // CTA: 8 segments (64 px) x 4 rows
+
 __global__ void __launch_bounds__(256)
 k_gather(const float *__restrict__ groups, const float *__restrict__ w, const int *__restrict__ off,
          const int *__restrict__ list, int log2K, int H, int W, int pitch, Win8 win, float *__restrict__ out)
@@ -146,30 +161,82 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
         for (int i = 0; i < 8; i++) sw[i] = win.v[i];
     }
     __syncthreads();
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (x >= W || y >= H) return;
+    const int j = threadIdx.x & 7;
+    const int x0 = blockIdx.x * (8 * kSegX) + ((threadIdx.x >> 3) & (kSegX - 1)) * 8;
+    const int y = blockIdx.y * kSegRows + (threadIdx.x >> 6);
+    if (x0 >= W || y >= H) return; // whole segment
+    const int x = x0 + j;
     float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
     const int ka = max(0, y - 7), kb = min(y, H - 8);
-    const int la = max(0, x - 7), lb = min(x, W - 8);
+    const int la = max(0, x0 - 7), lb = min(x0 + 7, W - 8);
     for (int k = ka; k <= kb; k++) {
         const int a = y - k;
         const float wa = sw[a];
+        const float *grow = groups + a * 8;
         for (int l = la; l <= lb; l++) {
             const int b = x - l;
-            const float wab = wa * sw[b];
+            const bool inb = b >= 0 && b < 8 && x < W;
+            const float wab = inb ? wa * sw[b] : 0.f;
             const int pos = k * W + l;
             const int e0 = __ldg(off + pos), e1 = __ldg(off + pos + 1);
             for (int e = e0; e < e1; e++) {
                 const int ent = __ldg(list + e);
-                const float wt = __ldg(w + (ent >> log2K)) * wab;
-                const float v = __ldg(groups + (size_t)ent * 64 + a * 8 + b);
-                kahan_add(num, cn, wt * v);
-                kahan_add(den, cd, wt);
+                if (inb) {
+                    const float wt = __ldg(w + (ent >> log2K)) * wab;
+                    const float v = __ldg(grow + (size_t)ent * 64 + b);
+                    kahan_add(num, cn, wt * v);
+                    kahan_add(den, cd, wt);
+                }
             }
         }
     }
-    out[(size_t)y * pitch + x] = num / den;
+    if (x < W) out[(size_t)y * pitch + x] = num / den;
+}
+
+// The same walk over the planar, position-sorted layout: the entries of
+// position pos are slots off[pos] .. off[pos+1]-1, row a of slot j is the 8
+// floats at planes + a * n_entries * 8 + j * 8, its weight w_slot[j].  For a
+// fixed block row k the slots of consecutive positions are consecutive, so
+// the reads stream through memory.  Same per-pixel order as k_gather.
+__global__ void __launch_bounds__(256)
+k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_slot, const int *__restrict__ off,
+                long long plane_stride, int H, int W, int pitch, Win8 win, float *__restrict__ out)
+{
+    __shared__ float sw[8];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) sw[i] = win.v[i];
+    }
+    __syncthreads();
+    const int j = threadIdx.x & 7;
+    const int x0 = blockIdx.x * (8 * kSegX) + ((threadIdx.x >> 3) & (kSegX - 1)) * 8;
+    const int y = blockIdx.y * kSegRows + (threadIdx.x >> 6);
+    if (x0 >= W || y >= H) return;
+    const int x = x0 + j;
+    float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
+    const int ka = max(0, y - 7), kb = min(y, H - 8);
+    const int la = max(0, x0 - 7), lb = min(x0 + 7, W - 8);
+    for (int k = ka; k <= kb; k++) {
+        const int a = y - k;
+        const float wa = sw[a];
+        const float *plane = planes + a * plane_stride;
+        for (int l = la; l <= lb; l++) {
+            const int b = x - l;
+            const bool inb = b >= 0 && b < 8 && x < W;
+            const int pos = k * W + l;
+            const int e0 = __ldg(off + pos), e1 = __ldg(off + pos + 1);
+            if (inb) {
+                const float wab = wa * sw[b];
+                for (int e = e0; e < e1; e++) {
+                    const float wt = __ldg(w_slot + e) * wab;
+                    const float v = __ldg(plane + (size_t)e * 8 + b);
+                    kahan_add(num, cn, wt * v);
+                    kahan_add(den, cd, wt);
+                }
+            }
+        }
+    }
+    if (x < W) out[(size_t)y * pitch + x] = num / den;
 }
 
 } // namespace
@@ -198,7 +265,7 @@ cudaError_t fixed_scratch(void **ptr)
     return cudaSuccess;
 }
 
-AggLayout agg_layout(int H, int W, int G, int K)
+AggLayout agg_layout(int H, int W, int G, int K, bool with_slots)
 {
     AggLayout L{};
     L.npos = H * W;
@@ -213,19 +280,20 @@ AggLayout agg_layout(int H, int W, int G, int K)
     o += align_up((size_t)nscan * sizeof(int));
     L.list = o;
     o += align_up((size_t)G * K * sizeof(int));
+    L.slot_of = o;
+    if (with_slots) o += align_up((size_t)G * K * sizeof(int));
     L.bsum = o;
     o += align_up((size_t)L.nblk * sizeof(int));
     L.bytes = o;
     return L;
 }
 
-cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t *idx, int G, int K, int H, int W,
-                             int pitch, const float *window8, float *out, void *agg_ws, cudaStream_t st)
+cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, void *agg_ws, bool with_slots, cudaStream_t st)
 {
-    const AggLayout L = agg_layout(H, W, G, K);
+    const AggLayout L = agg_layout(H, W, G, K, with_slots);
     char *base = (char *)agg_ws;
     int *cnt = (int *)(base + L.cnt), *off = (int *)(base + L.off), *cursor = (int *)(base + L.cursor);
-    int *list = (int *)(base + L.list), *bsum = (int *)(base + L.bsum);
+    int *list = (int *)(base + L.list), *bsum = (int *)(base + L.bsum), *slot_of = (int *)(base + L.slot_of);
     const int n = G * K, nscan = L.npos + 1;
     cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)nscan * sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -237,12 +305,40 @@ cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t 
     k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(off, nscan, bsum);
     k_fill<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, off, cursor, list);
     k_sort<<<(L.npos + 255) / 256, 256, 0, st>>>(off, L.npos, list);
+    if (with_slots) k_slots<<<(n + 255) / 256, 256, 0, st>>>(list, off + L.npos, slot_of);
+    return cudaGetLastError();
+}
+
+static Win8 make_win(const float *window8)
+{
     Win8 win;
     for (int i = 0; i < 8; i++) win.v[i] = window8[i];
+    return win;
+}
+
+cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t *idx, int G, int K, int H, int W,
+                             int pitch, const float *window8, float *out, void *agg_ws, cudaStream_t st)
+{
+    cudaError_t e = build_csr(idx, G, K, H, W, agg_ws, false, st);
+    if (e != cudaSuccess) return e;
+    const AggLayout L = agg_layout(H, W, G, K, false);
+    const char *base = (const char *)agg_ws;
     int log2K = 0;
     while ((1 << log2K) < K) log2K++;
-    dim3 grid((W + 31) / 32, (H + 7) / 8);
-    k_gather<<<grid, 256, 0, st>>>(groups, w, off, list, log2K, H, W, pitch, win, out);
+    dim3 grid((W + 8 * kSegX - 1) / (8 * kSegX), (H + kSegRows - 1) / kSegRows);
+    k_gather<<<grid, 256, 0, st>>>(groups, w, (const int *)(base + L.off), (const int *)(base + L.list), log2K, H, W,
+                                   pitch, make_win(window8), out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, int n_entries, int H, int W,
+                                    int pitch, const float *window8, float *out, const void *agg_ws, cudaStream_t st)
+{
+    const AggLayout L = agg_layout(H, W, 1, 1, false);
+    const int *off = (const int *)((const char *)agg_ws + L.off);
+    dim3 grid((W + 8 * kSegX - 1) / (8 * kSegX), (H + kSegRows - 1) / kSegRows);
+    k_gather_planar<<<grid, 256, 0, st>>>(planes, w_slot, off, (long long)n_entries * 8, H, W, pitch,
+                                          make_win(window8), out);
     return cudaGetLastError();
 }
 

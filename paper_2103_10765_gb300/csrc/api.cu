@@ -93,12 +93,17 @@ static void kaiser8(float beta, float *out)
     }
 }
 
+// One workspace layout serves every call (offsets in bytes):
+//   csr    inverted match lists of the current stage (+ slot_of)
+//   ht     stage-1 wavelet pyramid and pixel-offset table
+//   planes filtered blocks, position-planar (aggregation order), G*Kmax*64
+//   wslot  per-slot weights, G*Kmax
+//   idx    match lists, G*Kmax
+//   y1     stage-1 estimate (pitch W); zs, ys, y1s translation buffers
 struct Sizes {
     int By, Bx, G, Kmax;
     HtGeom ht;
-    AggLayout agg1, agg2;
-    size_t sub;                                 // shared scratch for HT / aggregation
-    size_t idx, groups, w, y1, zs, ys, y1s, total; // byte offsets of the denoise layout
+    size_t csr, ht_off, planes, wslot, idx, y1, zs, ys, y1s, total;
 };
 
 static Sizes sizes(int H, int W, const gbm3d_params *p)
@@ -109,19 +114,18 @@ static Sizes sizes(int H, int W, const gbm3d_params *p)
     z.G = z.By * z.Bx;
     z.Kmax = p->k1 > p->k2 ? p->k1 : p->k2;
     z.ht = ht_geom(z.By, z.Bx, p->k1, p->levels);
-    z.agg1 = agg_layout(H, W, z.G, p->k1);
-    z.agg2 = agg_layout(H, W, z.G, p->k2);
-    z.sub = z.ht.bytes;
-    if (z.agg1.bytes > z.sub) z.sub = z.agg1.bytes;
-    if (z.agg2.bytes > z.sub) z.sub = z.agg2.bytes;
     const size_t img = align_up((size_t)H * W * sizeof(float));
-    size_t o = align_up(z.sub);
+    size_t o = 0;
+    z.csr = o;
+    o += align_up(agg_layout(H, W, z.G, z.Kmax, true).bytes);
+    z.ht_off = o;
+    o += align_up(z.ht.bytes);
+    z.planes = o;
+    o += align_up((size_t)z.G * z.Kmax * kPatch * kPatch * sizeof(float));
+    z.wslot = o;
+    o += align_up((size_t)z.G * z.Kmax * sizeof(float));
     z.idx = o;
     o += align_up((size_t)z.G * z.Kmax * sizeof(int32_t));
-    z.groups = o;
-    o += align_up((size_t)z.G * z.Kmax * kPatch * kPatch * sizeof(float));
-    z.w = o;
-    o += align_up((size_t)z.G * sizeof(float));
     z.y1 = o;
     o += img;
     if (p->translations > 1) {
@@ -138,20 +142,31 @@ static Sizes sizes(int H, int W, const gbm3d_params *p)
 
 static bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+// Position-planar output descriptor over the workspace for a stage with K.
+static GroupOut planar_out(const Sizes &S, char *ws, int H, int W, int K)
+{
+    const AggLayout L = agg_layout(H, W, S.G, K, true);
+    return position_planar((float *)(ws + S.planes), (const int *)(ws + S.csr + L.slot_of), (long long)S.G * K,
+                           (float *)(ws + S.wslot));
+}
+
 // ---- one stage on (possibly shifted) images ------------------------------
 static int run_stage1(const float *z, int zp, int H, int W, float sigma, const gbm3d_params *p, const Sizes &S,
                       char *ws, float *out, int op, cudaStream_t st)
 {
+    const int K = p->k1;
     int32_t *idx = (int32_t *)(ws + S.idx);
-    float *groups = (float *)(ws + S.groups), *w = (float *)(ws + S.w);
-    cudaError_t e = launch_match(z, H, W, zp, S.By, S.Bx, p->step, p->search_radius, p->k1, idx, nullptr, st);
+    cudaError_t e = launch_match(z, H, W, zp, S.By, S.Bx, p->step, p->search_radius, K, idx, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "match (stage 1)");
-    e = launch_filter_ht(z, H, W, zp, idx, S.ht, sigma, p->tau_a, p->tau_b, p->cycle_spins, p->eps_w, groups, w, ws,
-                         st);
+    e = build_csr(idx, S.G, K, H, W, ws + S.csr, true, st);
+    if (e != cudaSuccess) return cuda_fail(e, "inverted lists (stage 1)");
+    const GroupOut go = planar_out(S, ws, H, W, K);
+    e = launch_filter_ht(z, H, W, zp, idx, S.ht, sigma, p->tau_a, p->tau_b, p->cycle_spins, p->eps_w, go,
+                         ws + S.ht_off, st);
     if (e != cudaSuccess) return cuda_fail(e, "filter_ht");
     float win[8];
     kaiser8(0.f, win);
-    e = launch_aggregate(groups, w, idx, S.G, p->k1, H, W, op, win, out, ws, st);
+    e = launch_aggregate_planar(go.base, go.w, S.G * K, H, W, op, win, out, ws + S.csr, st);
     if (e != cudaSuccess) return cuda_fail(e, "aggregate (stage 1)");
     return GBM3D_OK;
 }
@@ -159,15 +174,18 @@ static int run_stage1(const float *z, int zp, int H, int W, float sigma, const g
 static int run_stage2(const float *z, int zp, const float *y1, int yp, int H, int W, float sigma,
                       const gbm3d_params *p, const Sizes &S, char *ws, float *out, int op, cudaStream_t st)
 {
+    const int K = p->k2;
     int32_t *idx = (int32_t *)(ws + S.idx);
-    float *groups = (float *)(ws + S.groups), *w = (float *)(ws + S.w);
-    cudaError_t e = launch_match(y1, H, W, yp, S.By, S.Bx, p->step, p->search_radius, p->k2, idx, nullptr, st);
+    cudaError_t e = launch_match(y1, H, W, yp, S.By, S.Bx, p->step, p->search_radius, K, idx, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "match (stage 2)");
-    e = launch_filter_wiener(z, zp, y1, yp, H, W, idx, S.G, p->k2, sigma, p->eps_w, groups, w, st);
+    e = build_csr(idx, S.G, K, H, W, ws + S.csr, true, st);
+    if (e != cudaSuccess) return cuda_fail(e, "inverted lists (stage 2)");
+    const GroupOut go = planar_out(S, ws, H, W, K);
+    e = launch_filter_wiener(z, zp, y1, yp, H, W, idx, S.G, K, sigma, p->eps_w, go, st);
     if (e != cudaSuccess) return cuda_fail(e, "filter_wiener");
     float win[8];
     kaiser8(p->kaiser_beta, win);
-    e = launch_aggregate(groups, w, idx, S.G, p->k2, H, W, op, win, out, ws, st);
+    e = launch_aggregate_planar(go.base, go.w, S.G * K, H, W, op, win, out, ws + S.csr, st);
     if (e != cudaSuccess) return cuda_fail(e, "aggregate (stage 2)");
     return GBM3D_OK;
 }
@@ -281,7 +299,7 @@ int gbm3d_filter_ht(const float *noisy, int H, int W, int pitch, const int32_t *
     if (!aligned(ws, kAlign) || !aligned(groups, 16)) return fail(GBM3D_EINVAL, "ws must be 256-byte aligned");
     const Sizes S = sizes(H, W, p);
     cudaError_t e = launch_filter_ht(noisy, H, W, pitch, idx, S.ht, sigma, p->tau_a, p->tau_b, p->cycle_spins,
-                                     p->eps_w, groups, w, ws, (cudaStream_t)stream);
+                                     p->eps_w, group_major(groups, w), (char *)ws + S.ht_off, (cudaStream_t)stream);
     return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "filter_ht");
 }
 
@@ -296,8 +314,8 @@ int gbm3d_filter_wiener(const float *noisy, const float *pilot, int H, int W, in
     if (!(sigma >= 0.f) || !isfinite(sigma)) return fail(GBM3D_EINVAL, "sigma must be finite and >= 0");
     if (!aligned(groups, 16)) return fail(GBM3D_EINVAL, "groups must be 16-byte aligned");
     const int G = grid_count(H, kPatch, p->step) * grid_count(W, kPatch, p->step);
-    cudaError_t e = launch_filter_wiener(noisy, pitch, pilot, pitch, H, W, idx, G, p->k2, sigma, p->eps_w, groups, w,
-                                         (cudaStream_t)stream);
+    cudaError_t e = launch_filter_wiener(noisy, pitch, pilot, pitch, H, W, idx, G, p->k2, sigma, p->eps_w,
+                                         group_major(groups, w), (cudaStream_t)stream);
     return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "filter_wiener");
 }
 
@@ -316,7 +334,9 @@ int gbm3d_aggregate(const float *groups, const float *w, const int32_t *idx, int
     const int G = grid_count(H, kPatch, p->step) * grid_count(W, kPatch, p->step);
     float win[8];
     kaiser8(window_beta, win);
-    cudaError_t e = launch_aggregate(groups, w, idx, G, K, H, W, pitch, win, out, ws, (cudaStream_t)stream);
+    const Sizes S = sizes(H, W, p);
+    cudaError_t e =
+        launch_aggregate(groups, w, idx, G, K, H, W, pitch, win, out, (char *)ws + S.csr, (cudaStream_t)stream);
     return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "aggregate");
 }
 

@@ -25,10 +25,29 @@ constexpr int TY = 16, TX = 32;            // output positions per tile
 constexpr int IY = 2 * TY + 8, IX = 2 * TX + 8; // analysis input tile (halo 4 / 4 after the pair)
 constexpr int HY = TY + 4, HX = TX + 4;    // synthesis band tile (halo 2 each side)
 
-__device__ __forceinline__ int pmod(int i, int n)
+// Periodic index (eq. (1)).  Tile halos reach at most a few samples past
+// either end, so one conditional add or subtract suffices unless the axis is
+// shorter than the halo (coarse levels of tiny images): then the true modulo.
+__device__ __forceinline__ int pwrap(int i, int n)
 {
-    int r = i % n;
-    return r < 0 ? r + n : r;
+    if (i < 0) i += n;
+    if (i >= n) i -= n;
+    if ((unsigned)i >= (unsigned)n) {
+        i %= n;
+        if (i < 0) i += n;
+    }
+    return i;
+}
+
+// Pixel offset k*pitch + l of every match-list entry (once per call, so the
+// gathers need no division).
+__global__ void k_offsets(const int32_t *__restrict__ idx, int n, int H, int W, int pitch, int *__restrict__ ofs)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int k, l;
+    block_kl(idx[e], H, W, k, l);
+    ofs[e] = k * pitch + l;
 }
 
 // Lifting update U(d)[n] from the five detail values d[n-2..n+2].
@@ -54,9 +73,8 @@ __device__ __forceinline__ void ana10(const float *v, int stride, float &lo, flo
 // image through idx (level 1); otherwise a [Z][Y][X] plane stack.
 template <bool GATHER>
 __global__ void __launch_bounds__(256)
-k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int H, int W, int pitch,
-          const int32_t *__restrict__ idx, int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst,
-          float tau)
+k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitch, const int *__restrict__ ofs,
+          int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst, float tau)
 {
     __shared__ float s_in[2][IY][IX];
     __shared__ float s_y[2][2][TY][IX]; // [z band][y band][row][col]
@@ -68,14 +86,13 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int H, i
         const int yy = rem / IX, xx = rem - yy * IX;
         float v;
         if (GATHER) {
-            const int z = pmod(2 * m + zz - shift, Z);
-            const int y = pmod(iy0 + yy - shift, Y), x = pmod(ix0 + xx - shift, X);
+            const int z = pwrap(2 * m + zz - shift, Z);
+            const int y = pwrap(iy0 + yy - shift, Y), x = pwrap(ix0 + xx - shift, X);
             const int g = (y >> 3) * Bx + (x >> 3);
-            int k, l;
-            block_kl(__ldg(idx + (size_t)g * Z + z), H, W, k, l);
-            v = __ldg(img + (size_t)(k + (y & 7)) * pitch + l + (x & 7));
+            const int o = __ldg(ofs + (size_t)g * Z + z);
+            v = __ldg(img + o + (size_t)(y & 7) * pitch + (x & 7));
         } else {
-            const int y = pmod(iy0 + yy, Y), x = pmod(ix0 + xx, X);
+            const int y = pwrap(iy0 + yy, Y), x = pwrap(ix0 + xx, X);
             v = __ldg(src + ((size_t)(2 * m + zz) * Y + y) * X + x);
         }
         s_in[zz][yy][xx] = v;
@@ -130,11 +147,11 @@ __device__ __forceinline__ void syn_pair(float lo, const float *h, int stride, f
 // Level synthesis: 8 bands [band][Zc][Yc][Xc] -> (2Zc, 2Yc, 2Xc).  SCATTER
 // (level 1): the voxel at spun position (z,y,x) belongs to mosaic position
 // (z,y,x) - shift, i.e. block r = z of group (y/8, x/8) at (y%8, x%8); it is
-// written (or added) scaled into groups[g][r][a][b].
+// written (or added) scaled into the output blocks.
 template <bool SCATTER>
 __global__ void __launch_bounds__(256)
-k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restrict__ dst,
-          float *__restrict__ groups, int Bx, int shift, float scale, int accumulate)
+k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restrict__ dst, GroupOut out, int Bx,
+          int shift, float scale, int accumulate)
 {
     __shared__ float s_b[8][HY][HX];
     __shared__ float s_x[2][2][HY][2 * TX]; // [z band][y band][coef row][output col]
@@ -144,7 +161,7 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
     for (int e = threadIdx.x; e < 8 * HY * HX; e += blockDim.x) {
         const int band = e / (HY * HX), rem = e - band * (HY * HX);
         const int yy = rem / HX, xx = rem - yy * HX;
-        const int y = pmod(y0 - 2 + yy, Yc), x = pmod(x0 - 2 + xx, Xc);
+        const int y = pwrap(y0 - 2 + yy, Yc), x = pwrap(x0 - 2 + xx, Xc);
         s_b[band][yy][xx] = __ldg(coef + (size_t)band * band_elems + ((size_t)m * Yc + y) * Xc + x);
     }
     __syncthreads();
@@ -176,9 +193,9 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
                 const int zs = 2 * m + zz, ys = yb + yy;
                 const float v = vz[zz][yy];
                 if (SCATTER) {
-                    const int z = pmod(zs - shift, Zo), y = pmod(ys - shift, Yo), x = pmod(xo - shift, Xo);
-                    const size_t g = (size_t)(y >> 3) * Bx + (x >> 3);
-                    float *o_ = groups + ((g * Zo + z) * 8 + (y & 7)) * 8 + (x & 7);
+                    const int z = pwrap(zs - shift, Zo), y = pwrap(ys - shift, Yo), x = pwrap(xo - shift, Xo);
+                    const long long g = (long long)(y >> 3) * Bx + (x >> 3);
+                    float *o_ = out.row(g * Zo + z, y & 7) + (x & 7);
                     *o_ = accumulate ? (*o_ + scale * v) : scale * v;
                 } else {
                     dst[((size_t)zs * Yo + ys) * Xo + xo] = v;
@@ -189,24 +206,38 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
 
 // Stage-1 weights: w = 1 / max(TV(u), eps) with TV the sum of absolute
 // forward differences along rows, columns and the group axis inside the
-// N x N x K block (no wrap).  One warp per group.
-__global__ void k_tv(const float *__restrict__ groups, int G, int K, float eps, float *__restrict__ w)
+// N x N x K block (no wrap).  One warp per group; lane = 4 a + bh owns the
+// two columns 2bh, 2bh+1 of row a of every block.
+__global__ void k_tv(GroupOut out, int G, int K, float eps)
 {
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= G) return;
-    const float *u = groups + (size_t)g * K * 64;
+    const int a = lane >> 2, bh = lane & 3;
     float tv = 0.f;
-    for (int e = lane; e < K * 64; e += 32) {
-        const int r = e >> 6, a = (e >> 3) & 7, b = e & 7;
-        const float c = u[e];
-        if (a < 7) tv += fabsf(u[e + 8] - c);
-        if (b < 7) tv += fabsf(u[e + 1] - c);
-        if (r < K - 1) tv += fabsf(u[e + 64] - c);
+    for (int r = 0; r < K; r++) {
+        const long long e = (long long)g * K + r;
+        const float *row = out.row(e, a);
+        const float v0 = row[2 * bh], v1 = row[2 * bh + 1];
+        tv += fabsf(v1 - v0);
+        if (bh < 3) tv += fabsf(row[2 * bh + 2] - v1);
+        if (a < 7) {
+            const float *nxt = out.row(e, a + 1);
+            tv += fabsf(nxt[2 * bh] - v0) + fabsf(nxt[2 * bh + 1] - v1);
+        }
+        if (r < K - 1) {
+            const float *nz = out.row(e + 1, a);
+            tv += fabsf(nz[2 * bh] - v0) + fabsf(nz[2 * bh + 1] - v1);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tv += __shfl_xor_sync(0xffffffffu, tv, o);
-    if (lane == 0) w[g] = 1.f / fmaxf(tv, eps);
+    const float wv = 1.f / fmaxf(tv, eps);
+    if (out.per_slot) {
+        for (int r = lane; r < K; r += 32) out.w[out.slot((long long)g * K + r)] = wv;
+    } else if (lane == 0) {
+        out.w[g] = wv;
+    }
 }
 
 } // namespace
@@ -227,15 +258,20 @@ HtGeom ht_geom(int By, int Bx, int K, int levels)
         g.level_off[l] = off;
         off += align_up(g.level_elems[l] * sizeof(float));
     }
+    g.ofs_off = off;
+    off += align_up((size_t)By * Bx * K * sizeof(int));
     g.bytes = off;
     return g;
 }
 
 cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
-                             float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, float *groups,
-                             float *w, void *ht_ws, cudaStream_t st)
+                             float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, const GroupOut &out,
+                             void *ht_ws, cudaStream_t st)
 {
     char *base = (char *)ht_ws;
+    int *ofs = (int *)(base + g.ofs_off);
+    const int nent = g.By * g.Bx * g.K;
+    k_offsets<<<(nent + 255) / 256, 256, 0, st>>>(idx, nent, H, W, pitch, ofs);
     float *C[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int l = 1; l <= g.levels; l++) C[l] = (float *)(base + g.level_off[l]);
     const float inv_c = 1.f / (float)cycle_spins;
@@ -246,9 +282,9 @@ cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const in
             const float tau = sigma * (tau_a - tau_b * (float)l);
             dim3 grid((X / 2 + TX - 1) / TX, (Y / 2 + TY - 1) / TY, Z / 2);
             if (l == 1)
-                k_dwt_ana<true><<<grid, 256, 0, st>>>(nullptr, img, H, W, pitch, idx, g.Bx, c, Y, X, Z, C[1], tau);
+                k_dwt_ana<true><<<grid, 256, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau);
             else
-                k_dwt_ana<false><<<grid, 256, 0, st>>>(C[l - 1], nullptr, 0, 0, 0, nullptr, 0, 0, Y, X, Z, C[l], tau);
+                k_dwt_ana<false><<<grid, 256, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau);
         }
         // synthesis, levels L..1; level l writes the approximation of level
         // l-1, i.e. band 0 of C[l-1] (or the groups for l = 1)
@@ -256,13 +292,13 @@ cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const in
             const int Yc = g.Yd >> l, Xc = g.Xd >> l, Zc = g.K >> l;
             dim3 grid((Xc + TX - 1) / TX, (Yc + TY - 1) / TY, Zc);
             if (l == 1)
-                k_dwt_syn<true><<<grid, 256, 0, st>>>(C[1], Yc, Xc, Zc, nullptr, groups, g.Bx, c, inv_c, c > 0);
+                k_dwt_syn<true><<<grid, 256, 0, st>>>(C[1], Yc, Xc, Zc, nullptr, out, g.Bx, c, inv_c, c > 0);
             else
-                k_dwt_syn<false><<<grid, 256, 0, st>>>(C[l], Yc, Xc, Zc, C[l - 1], nullptr, 0, 0, 0.f, 0);
+                k_dwt_syn<false><<<grid, 256, 0, st>>>(C[l], Yc, Xc, Zc, C[l - 1], out, 0, 0, 0.f, 0);
         }
     }
     const int G = g.By * g.Bx;
-    k_tv<<<(G + 7) / 8, 256, 0, st>>>(groups, G, g.K, eps_w, w);
+    k_tv<<<(G + 7) / 8, 256, 0, st>>>(out, G, g.K, eps_w);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,32 @@ __device__ __forceinline__ bool block_ok(int pos, int H, int W)
     return k <= H - kPatch && l <= W - kPatch;
 }
 
+// Where the filters put block r of group g (entry e = g*K + r), row a:
+//   base + slot(e) * s_slot + a * s_row   (8 consecutive floats, b = 0..7),
+// slot(e) = slot_of[e] (position-sorted order used by the aggregation) or e
+// itself (the group-major [G][K][8][8] layout of the public calls).  Weights
+// go to w[g] (per_slot = 0) or to w[slot(e)] for each of the group's K
+// entries (per_slot = 1).
+struct GroupOut {
+    float *base;
+    const int *slot_of;
+    long long s_slot, s_row;
+    float *w;
+    int per_slot;
+    __device__ __forceinline__ long long slot(long long e) const { return slot_of ? (long long)__ldg(slot_of + e) : e; }
+    __device__ __forceinline__ float *row(long long e, int a) const { return base + slot(e) * s_slot + a * s_row; }
+};
+
+inline GroupOut group_major(float *groups, float *w)
+{
+    return GroupOut{groups, nullptr, 64, 8, w, 0};
+}
+
+inline GroupOut position_planar(float *planes, const int *slot_of, long long n_entries, float *w_slot)
+{
+    return GroupOut{planes, slot_of, 8, n_entries * 8, w_slot, 1};
+}
+
 // Geometry of the stage-1 mosaic volume and of its wavelet pyramid.
 struct HtGeom {
     int By, Bx, K;          // groups along y, x; blocks per group
@@ -58,15 +84,21 @@ struct HtGeom {
     int levels;
     size_t level_elems[4];  // elements of the coefficient buffer of level l (1-based)
     size_t level_off[4];    // byte offset of each level buffer in the HT scratch
+    size_t ofs_off;         // byte offset of the pixel-offset table (G*K ints)
     size_t bytes;           // total HT scratch
 };
 HtGeom ht_geom(int By, int Bx, int K, int levels);
 
 struct AggLayout {
-    size_t cnt, off, cursor, list, bsum, bytes; // byte offsets and total
+    size_t cnt, off, cursor, list, slot_of, bsum, bytes; // byte offsets and total
     int npos, nblk;
 };
-AggLayout agg_layout(int H, int W, int G, int K);
+AggLayout agg_layout(int H, int W, int G, int K, bool with_slots = false);
+
+// Inverted match lists (block position -> entries, entries ascending within a
+// position) in the aggregation scratch; with_slots also fills slot_of.
+cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, void *agg_ws, bool with_slots,
+                      cudaStream_t st);
 
 size_t match_smem_bytes(int s, int R);
 
@@ -80,12 +112,17 @@ cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int 
                          int32_t *idx, float *dist, cudaStream_t st);
 
 cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
-                             float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, float *groups,
-                             float *w, void *ht_ws, cudaStream_t st);
+                             float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, const GroupOut &out,
+                             void *ht_ws, cudaStream_t st);
 
 cudaError_t launch_filter_wiener(const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
-                                 const int32_t *idx, int G, int K, float sigma, float eps_w, float *groups, float *w,
+                                 const int32_t *idx, int G, int K, float sigma, float eps_w, const GroupOut &out,
                                  cudaStream_t st);
+
+// Aggregation from the position-planar layout written through a GroupOut
+// made by position_planar() with the slot_of of build_csr.
+cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, int n_entries, int H, int W,
+                                    int pitch, const float *window8, float *out, const void *agg_ws, cudaStream_t st);
 
 cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t *idx, int G, int K, int H, int W,
                              int pitch, const float *window8, float *out, void *agg_ws, cudaStream_t st);

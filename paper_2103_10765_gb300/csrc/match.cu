@@ -4,17 +4,29 @@
 // One warp per reference block, eight references (consecutive grid columns
 // of one grid row) per CTA sharing one shared-memory copy of their search
 // region.  The reference block lives in registers (64 floats per lane, the
-// same in every lane); each lane takes four vertically stacked candidates at
+// same in every lane); each lane takes eight vertically stacked candidates at
 // a time, so every 8-pixel image row it loads from shared memory serves up
-// to four candidate rows (11 row loads per 4 candidates instead of 32).
+// to eight candidate rows (15 row loads per 8 candidates instead of 64).
 // Distances are the exact sum of squared differences in FP32 -- the direct
-// form, not the norm expansion of eq. (expand), which cancels badly in FP32.
+// form, not the norm expansion of eq. (expand), which cancels badly in FP32 --
+// computed with Blackwell's packed FP32 pairs (sub/fma.rn.f32x2): the even
+// and odd columns of a block row are two independent FP32 partial sums, each
+// rounded exactly as scalar FSUB/FFMA would be.
 //
-// Selection keeps the K-1 best (distance, k*W+l) keys in a warp-distributed
-// sorted list: lane t holds the t-th best.  Each batch of candidates is
-// compared against the current K-1-th key; the few that qualify (ballot) are
-// inserted one at a time with a shuffle-based shift.  The reference block
-// itself is excluded and written to slot 0.
+// Lane layout: a work unit is (block of kVB candidate rows, candidate
+// column); units are numbered row-major with the column count padded to a
+// multiple of 8 (col_pad), and the shared-memory row stride is chosen so that
+// kVB * stride == col_pad (mod 32).  A warp's 32 consecutive units then read
+// 32 distinct banks even where they straddle two unit rows.
+//
+// Selection (K-1 best keys (distance, k*W+l)) follows the warp-select
+// pattern: lane t holds the t-th best of a sorted 32-entry list; candidates
+// that beat the current (K-1)-th key are appended to a per-warp buffer in
+// shared memory (ballot + prefix count, no serialisation); whenever 32 have
+// accumulated they are bitonic-sorted across the warp and merged into the
+// list.  The scan starts at the reference's own rows so that the threshold
+// tightens early.  The reference block itself is excluded and written to
+// slot 0.
 #include <float.h>
 #include <limits.h>
 
@@ -24,18 +36,78 @@ namespace gbm3d {
 namespace {
 
 constexpr int kRefsPerCta = 8;
-constexpr int kVB = 4;
+constexpr int kVB = 8;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBuf = 64; // per-warp candidate buffer (entries)
+
+typedef unsigned long long f2; // two packed FP32 values
+
+__device__ __forceinline__ f2 pack2(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// acc += (r - x)^2, elementwise on both halves.
+__device__ __forceinline__ f2 sqdiff_acc2(f2 r, f2 x, f2 acc)
+{
+    f2 e, o;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(r), "l"(x));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(o) : "l"(e), "l"(acc));
+    return o;
+}
 
 __device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
 {
     return da < db || (da == db && ia < ib);
 }
 
+// Compare-exchange across lanes lane and lane^j; `asc` selects the order of
+// the enclosing bitonic block.
+__device__ __forceinline__ void cmpx(float &d, int &i, int j, bool asc, int lane)
+{
+    const float od = __shfl_xor_sync(kFull, d, j);
+    const int oi = __shfl_xor_sync(kFull, i, j);
+    const bool lower = (lane & j) == 0;
+    const bool take = (lower == asc) ? key_less(od, oi, d, i) : key_less(d, i, od, oi);
+    if (take) {
+        d = od;
+        i = oi;
+    }
+}
+
+// Sort 32 keys (one per lane) ascending by lane.
+__device__ __forceinline__ void bitonic_sort32(float &d, int &i, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) cmpx(d, i, j, (lane & k) == 0, lane);
+}
+
+// list (ascending by lane) <- the 32 smallest of list and b (ascending).
+__device__ __forceinline__ void merge32(float &ld, int &li, float bd, int bi, int lane)
+{
+    const float rd = __shfl_sync(kFull, bd, 31 - lane);
+    const int ri = __shfl_sync(kFull, bi, 31 - lane);
+    if (key_less(rd, ri, ld, li)) {
+        ld = rd;
+        li = ri;
+    }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) cmpx(ld, li, j, true, lane);
+}
+
 template <int N>
 __global__ void __launch_bounds__(kRefsPerCta * 32)
-k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, int R, int K,
-        int32_t *__restrict__ idx, float *__restrict__ dist)
+k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, int R, int K, int col_pad,
+        int rw, int32_t *__restrict__ idx, float *__restrict__ dist)
 {
     extern __shared__ float sm[];
     const int p = blockIdx.y;
@@ -45,11 +117,13 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
     const int jf = grid_pos(q0, s, W, N), jl = grid_pos(qlast, s, W, N);
     const int ry0 = max(0, i - R), ry1 = min(H - N, i + R) + N;
     const int rx0 = max(0, jf - R), rx1 = min(W - N, jl + R) + N;
-    const int rw = rx1 - rx0, rh = ry1 - ry0;
+    const int rwd = rx1 - rx0, rh = ry1 - ry0;
     const int rhp = rh + kVB; // zero rows below absorb the last vertical block
+    float *buf_d = sm + rhp * rw;
+    int *buf_i = reinterpret_cast<int *>(buf_d + kRefsPerCta * kBuf);
     for (int e = threadIdx.x; e < rhp * rw; e += blockDim.x) {
         const int y = e / rw, x = e - y * rw;
-        sm[e] = (y < rh) ? __ldg(img + (size_t)(ry0 + y) * pitch + rx0 + x) : 0.f;
+        sm[e] = (y < rh && x < rwd) ? __ldg(img + (size_t)(ry0 + y) * pitch + rx0 + x) : 0.f;
     }
     __syncthreads();
 
@@ -57,53 +131,59 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
     const int q = q0 + warp;
     if (q >= Bx) return;
     const int j = grid_pos(q, s, W, N);
+    float *wb_d = buf_d + warp * kBuf;
+    int *wb_i = buf_i + warp * kBuf;
 
-    float r[N][N];
+    f2 r[N][N / 2]; // reference block, column pairs (b, b+1) packed
 #pragma unroll
     for (int a = 0; a < N; a++)
 #pragma unroll
-        for (int b = 0; b < N; b++) r[a][b] = sm[(i - ry0 + a) * rw + (j - rx0 + b)];
+        for (int b = 0; b < N; b += 2)
+            r[a][b / 2] = pack2(sm[(i - ry0 + a) * rw + (j - rx0 + b)], sm[(i - ry0 + a) * rw + (j - rx0 + b + 1)]);
 
     const int k0 = ry0, k1 = min(H - N, i + R);
     const int l0 = max(0, j - R), l1 = min(W - N, j + R);
     const int ny = k1 - k0 + 1, nx = l1 - l0 + 1;
-    const int nunits = ((ny + kVB - 1) / kVB) * nx;
+    const int nkb = (ny + kVB - 1) / kVB;
+    const int nunits = nkb * col_pad;
+    const int kb_start = (i - k0) / kVB; // scan the reference's own rows first
     const int Kc = K - 1;
     const float kInf = __int_as_float(0x7f800000);
+    const unsigned lt_mask = (1u << lane) - 1u;
 
-    float ld = kInf;  // this lane's list entry (lane t = t-th best)
+    float ld = kInf; // sorted list: lane t holds the t-th best key
     int li = INT_MAX;
-    float thr_d = kInf; // current (K-1)-th best key
+    float thr_d = kInf;
     int thr_i = INT_MAX;
+    int cnt = 0; // entries in the warp buffer (warp-uniform)
 
     for (int u0 = 0; u0 < nunits; u0 += 32) {
         const int u = u0 + lane;
         const bool vu = u < nunits;
         int kb = 0, dl = 0;
         if (vu) {
-            kb = u / nx;
-            dl = u - kb * nx;
+            kb = u / col_pad;
+            dl = u - kb * col_pad;
+            kb += kb_start;
+            if (kb >= nkb) kb -= nkb;
         }
         const int k = k0 + kb * kVB, l = l0 + dl;
-        float d[kVB];
+        f2 dd[kVB]; // (even-column, odd-column) partial sums per candidate
 #pragma unroll
-        for (int c = 0; c < kVB; c++) d[c] = 0.f;
+        for (int c = 0; c < kVB; c++) dd[c] = 0ull;
         if (vu) {
             const float *base = sm + (k - ry0) * rw + (l - rx0);
 #pragma unroll
             for (int t = 0; t < kVB + N - 1; t++) {
-                float x[N];
+                f2 x[N / 2];
 #pragma unroll
-                for (int b = 0; b < N; b++) x[b] = base[t * rw + b];
+                for (int b = 0; b < N; b += 2) x[b / 2] = pack2(base[t * rw + b], base[t * rw + b + 1]);
 #pragma unroll
                 for (int c = 0; c < kVB; c++) {
                     const int a = t - c;
                     if (a >= 0 && a < N) {
 #pragma unroll
-                        for (int b = 0; b < N; b++) {
-                            const float df = r[a][b] - x[b];
-                            d[c] = fmaf(df, df, d[c]);
-                        }
+                        for (int b = 0; b < N / 2; b++) dd[c] = sqdiff_acc2(r[a][b], x[b], dd[c]);
                     }
                 }
             }
@@ -111,33 +191,53 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
 #pragma unroll
         for (int c = 0; c < kVB; c++) {
             const int kc = k + c;
-            const bool valid = vu && kc <= k1 && !(kc == i && l == j);
+            const bool valid = vu && dl < nx && kc <= k1 && !(kc == i && l == j);
             const int cid = kc * W + l;
-            const float cd = d[c];
-            bool pend = valid && key_less(cd, cid, thr_d, thr_i);
-            unsigned mask = __ballot_sync(kFull, pend);
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                const float nd = __shfl_sync(kFull, cd, src);
-                const int ni = __shfl_sync(kFull, cid, src);
-                const float pd = __shfl_up_sync(kFull, ld, 1);
-                const int pi = __shfl_up_sync(kFull, li, 1);
-                if (lane < Kc && key_less(nd, ni, ld, li)) {
-                    if (lane == 0 || key_less(pd, pi, nd, ni)) {
-                        ld = nd;
-                        li = ni;
-                    } else {
-                        ld = pd;
-                        li = pi;
-                    }
+            float d0, d1;
+            unpack2(dd[c], d0, d1);
+            const float cd = d0 + d1;
+            const bool pend = valid && key_less(cd, cid, thr_d, thr_i);
+            const unsigned mask = __ballot_sync(kFull, pend);
+            if (pend) {
+                const int pos = cnt + __popc(mask & lt_mask);
+                wb_d[pos] = cd;
+                wb_i[pos] = cid;
+            }
+            cnt += __popc(mask);
+            if (cnt >= 32) {
+                __syncwarp();
+                float bd = wb_d[lane];
+                int bi = wb_i[lane];
+                bitonic_sort32(bd, bi, lane);
+                merge32(ld, li, bd, bi, lane);
+                cnt -= 32;
+                float md = 0.f;
+                int mi = 0;
+                if (lane < cnt) {
+                    md = wb_d[32 + lane];
+                    mi = wb_i[32 + lane];
                 }
+                __syncwarp();
+                if (lane < cnt) {
+                    wb_d[lane] = md;
+                    wb_i[lane] = mi;
+                }
+                __syncwarp();
                 thr_d = __shfl_sync(kFull, ld, Kc - 1);
                 thr_i = __shfl_sync(kFull, li, Kc - 1);
-                if (lane == src) pend = false;
-                pend = pend && key_less(cd, cid, thr_d, thr_i);
-                mask = __ballot_sync(kFull, pend);
             }
         }
+    }
+    if (cnt > 0) { // flush the partial buffer
+        __syncwarp();
+        float bd = kInf;
+        int bi = INT_MAX;
+        if (lane < cnt) {
+            bd = wb_d[lane];
+            bi = wb_i[lane];
+        }
+        bitonic_sort32(bd, bi, lane);
+        merge32(ld, li, bd, bi, lane);
     }
 
     const size_t gi = ((size_t)p * Bx + q) * K;
@@ -151,23 +251,42 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
     }
 }
 
+struct MatchGeom {
+    int col_pad, rw, rows;
+};
+
+MatchGeom match_geom(int s, int R)
+{
+    MatchGeom g;
+    g.col_pad = (2 * R + 1 + 7) / 8 * 8;
+    // widest row a lane can touch: (l0 - rx0) <= (kRefsPerCta-1) s, plus the
+    // padded column count, plus the block width
+    int need = (kRefsPerCta - 1) * s + g.col_pad + kPatch;
+    const int data = (kRefsPerCta - 1) * s + 2 * R + kPatch;
+    if (data > need) need = data;
+    g.rw = need; // kVB * rw == col_pad (mod 32)
+    while ((kVB * g.rw - g.col_pad) % 32 != 0) g.rw++;
+    g.rows = 2 * R + kPatch + kVB;
+    return g;
+}
+
 } // namespace
 
 size_t match_smem_bytes(int s, int R)
 {
-    const int rows = 2 * R + kPatch + kVB;
-    const int cols = (kRefsPerCta - 1) * s + 2 * R + kPatch;
-    return (size_t)rows * cols * sizeof(float);
+    const MatchGeom g = match_geom(s, R);
+    return (size_t)g.rows * g.rw * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int));
 }
 
 cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                          int32_t *idx, float *dist, cudaStream_t st)
 {
+    const MatchGeom g = match_geom(s, R);
     const size_t smem = match_smem_bytes(s, R);
     cudaError_t e = cudaFuncSetAttribute(k_match<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kRefsPerCta - 1) / kRefsPerCta, By);
-    k_match<kPatch><<<grid, kRefsPerCta * 32, smem, st>>>(img, H, W, pitch, Bx, s, R, K, idx, dist);
+    k_match<kPatch><<<grid, kRefsPerCta * 32, smem, st>>>(img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, idx, dist);
     return cudaGetLastError();
 }
 

@@ -56,43 +56,40 @@ __device__ __forceinline__ void idct8(float *X)
     X[4] = e3 - o3;
 }
 
-template <int K>
+// Full-depth orthonormal Haar along the group, in registers: one level on
+// the first LEN entries, then recurse on the LEN/2 low-pass entries.
+template <int LEN>
 __device__ __forceinline__ void haar_fwd(float *h)
 {
+    float t[LEN];
 #pragma unroll
-    for (int len = K; len >= 2; len >>= 1) {
-        float t[K];
-#pragma unroll
-        for (int m = 0; m < len / 2; m++) {
-            t[m] = (h[2 * m] + h[2 * m + 1]) * kS;
-            t[len / 2 + m] = (h[2 * m] - h[2 * m + 1]) * kS;
-        }
-#pragma unroll
-        for (int m = 0; m < len; m++) h[m] = t[m];
+    for (int m = 0; m < LEN / 2; m++) {
+        t[m] = (h[2 * m] + h[2 * m + 1]) * kS;
+        t[LEN / 2 + m] = (h[2 * m] - h[2 * m + 1]) * kS;
     }
+#pragma unroll
+    for (int m = 0; m < LEN; m++) h[m] = t[m];
+    if constexpr (LEN > 2) haar_fwd<LEN / 2>(h);
 }
 
-template <int K>
+template <int LEN>
 __device__ __forceinline__ void haar_inv(float *h)
 {
+    if constexpr (LEN > 2) haar_inv<LEN / 2>(h);
+    float t[LEN];
 #pragma unroll
-    for (int len = 2; len <= K; len <<= 1) {
-        float t[K];
-#pragma unroll
-        for (int m = 0; m < len / 2; m++) {
-            t[2 * m] = (h[m] + h[len / 2 + m]) * kS;
-            t[2 * m + 1] = (h[m] - h[len / 2 + m]) * kS;
-        }
-#pragma unroll
-        for (int m = 0; m < len; m++) h[m] = t[m];
+    for (int m = 0; m < LEN / 2; m++) {
+        t[2 * m] = (h[m] + h[LEN / 2 + m]) * kS;
+        t[2 * m + 1] = (h[m] - h[LEN / 2 + m]) * kS;
     }
+#pragma unroll
+    for (int m = 0; m < LEN; m++) h[m] = t[m];
 }
 
 template <int K>
 __global__ void __launch_bounds__(K * 8)
 k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ pilot, int ppitch, int H, int W,
-         const int32_t *__restrict__ idx, float sigma2, float eps_w, float *__restrict__ groups,
-         float *__restrict__ w)
+         const int32_t *__restrict__ idx, float sigma2, float eps_w, GroupOut out)
 {
     constexpr int NT = K * 8;
     __shared__ __align__(16) float sp[K * PS];
@@ -170,10 +167,12 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
 #pragma unroll
         for (int rr = 0; rr < K; rr++) sq[rr * PS + e] = h[rr];
     }
-    if (t == 0) {
+    if (t < K) {
         float s = 0.f;
         for (int i = 0; i < NT / 32; i++) s += red[i];
-        w[g] = 1.f / fmaxf(sigma2 * s, eps_w);
+        const float wv = 1.f / fmaxf(sigma2 * s, eps_w);
+        if (out.per_slot) out.w[out.slot((long long)g * K + t)] = wv;
+        else if (t == 0) out.w[g] = wv;
     }
     __syncthreads();
     {
@@ -191,7 +190,7 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
 #pragma unroll
         for (int b = 0; b < 8; b++) x[b] = sq[r * PS + a * 8 + b];
         idct8(x);
-        float4 *o = reinterpret_cast<float4 *>(groups + (((size_t)g * K + r) * 8 + a) * 8);
+        float4 *o = reinterpret_cast<float4 *>(out.row((long long)g * K + r, a));
         o[0] = make_float4(x[0], x[1], x[2], x[3]);
         o[1] = make_float4(x[4], x[5], x[6], x[7]);
     }
@@ -200,14 +199,14 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
 } // namespace
 
 cudaError_t launch_filter_wiener(const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
-                                 const int32_t *idx, int G, int K, float sigma, float eps_w, float *groups, float *w,
+                                 const int32_t *idx, int G, int K, float sigma, float eps_w, const GroupOut &out,
                                  cudaStream_t st)
 {
     const float s2 = sigma * sigma;
     switch (K) {
-    case 8: k_wiener<8><<<G, 64, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, groups, w); break;
-    case 16: k_wiener<16><<<G, 128, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, groups, w); break;
-    case 32: k_wiener<32><<<G, 256, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, groups, w); break;
+    case 8: k_wiener<8><<<G, 64, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out); break;
+    case 16: k_wiener<16><<<G, 128, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out); break;
+    case 32: k_wiener<32><<<G, 256, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
