@@ -124,11 +124,16 @@ __global__ void k_sort(const int *__restrict__ off, int npos, int *__restrict__ 
     }
 }
 
-// slot_of[entry] = its index in the position-sorted entry list.
-__global__ void k_slots(const int *__restrict__ list, const int *__restrict__ total, int *__restrict__ slot_of)
+// slot_of[entry] = its index in the position-sorted entry list; lpos[slot] =
+// the block column l of that slot's position.
+__global__ void k_slots(const int *__restrict__ list, const int *__restrict__ total, const int32_t *__restrict__ idx,
+                        int W, int *__restrict__ slot_of, int *__restrict__ lpos)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < *total) slot_of[list[j]] = j;
+    if (j >= *total) return;
+    const int e = list[j];
+    slot_of[e] = j;
+    lpos[j] = idx[e] % W;
 }
 
 struct Win8 {
@@ -193,14 +198,16 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
     if (x < W) out[(size_t)y * pitch + x] = num / den;
 }
 
-// The same walk over the planar, position-sorted layout: the entries of
-// position pos are slots off[pos] .. off[pos+1]-1, row a of slot j is the 8
-// floats at planes + a * n_entries * 8 + j * 8, its weight w_slot[j].  For a
-// fixed block row k the slots of consecutive positions are consecutive, so
-// the reads stream through memory.  Same per-pixel order as k_gather.
+// The same sums over the planar, position-sorted layout: row a of slot j is
+// the 8 floats at planes + a * plane_stride + 8 j, its weight w_slot[j], its
+// block column lpos[j].  For one block row k the slots of positions
+// k*W + la .. k*W + lb are one contiguous range, walked in order (= columns
+// ascending, entries ascending: the same per-pixel order as k_gather), so
+// the reads stream through memory.
 __global__ void __launch_bounds__(256)
 k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_slot, const int *__restrict__ off,
-                long long plane_stride, int H, int W, int pitch, Win8 win, float *__restrict__ out)
+                const int *__restrict__ lpos, long long plane_stride, int H, int W, int pitch, Win8 win,
+                float *__restrict__ out)
 {
     __shared__ float sw[8];
     if (threadIdx.x == 0) {
@@ -213,6 +220,7 @@ k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_sl
     const int y = blockIdx.y * kSegRows + (threadIdx.x >> 6);
     if (x0 >= W || y >= H) return;
     const int x = x0 + j;
+    const bool xin = x < W;
     float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
     const int ka = max(0, y - 7), kb = min(y, H - 8);
     const int la = max(0, x0 - 7), lb = min(x0 + 7, W - 8);
@@ -220,23 +228,19 @@ k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_sl
         const int a = y - k;
         const float wa = sw[a];
         const float *plane = planes + a * plane_stride;
-        for (int l = la; l <= lb; l++) {
-            const int b = x - l;
-            const bool inb = b >= 0 && b < 8 && x < W;
-            const int pos = k * W + l;
-            const int e0 = __ldg(off + pos), e1 = __ldg(off + pos + 1);
-            if (inb) {
-                const float wab = wa * sw[b];
-                for (int e = e0; e < e1; e++) {
-                    const float wt = __ldg(w_slot + e) * wab;
-                    const float v = __ldg(plane + (size_t)e * 8 + b);
-                    kahan_add(num, cn, wt * v);
-                    kahan_add(den, cd, wt);
-                }
+        const int s0 = __ldg(off + k * W + la), s1 = __ldg(off + k * W + lb + 1);
+#pragma unroll 4
+        for (int e = s0; e < s1; e++) {
+            const int b = x - __ldg(lpos + e);
+            if (xin && b >= 0 && b < 8) {
+                const float wt = __ldg(w_slot + e) * wa * sw[b];
+                const float v = __ldg(plane + (size_t)e * 8 + b);
+                kahan_add(num, cn, wt * v);
+                kahan_add(den, cd, wt);
             }
         }
     }
-    if (x < W) out[(size_t)y * pitch + x] = num / den;
+    if (xin) out[(size_t)y * pitch + x] = num / den;
 }
 
 } // namespace
@@ -282,6 +286,8 @@ AggLayout agg_layout(int H, int W, int G, int K, bool with_slots)
     o += align_up((size_t)G * K * sizeof(int));
     L.slot_of = o;
     if (with_slots) o += align_up((size_t)G * K * sizeof(int));
+    L.lpos = o;
+    if (with_slots) o += align_up((size_t)G * K * sizeof(int));
     L.bsum = o;
     o += align_up((size_t)L.nblk * sizeof(int));
     L.bytes = o;
@@ -305,7 +311,8 @@ cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, void *agg_
     k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(off, nscan, bsum);
     k_fill<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, off, cursor, list);
     k_sort<<<(L.npos + 255) / 256, 256, 0, st>>>(off, L.npos, list);
-    if (with_slots) k_slots<<<(n + 255) / 256, 256, 0, st>>>(list, off + L.npos, slot_of);
+    if (with_slots)
+        k_slots<<<(n + 255) / 256, 256, 0, st>>>(list, off + L.npos, idx, W, slot_of, (int *)(base + L.lpos));
     return cudaGetLastError();
 }
 
@@ -334,10 +341,11 @@ cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t 
 cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, int n_entries, int H, int W,
                                     int pitch, const float *window8, float *out, const void *agg_ws, cudaStream_t st)
 {
-    const AggLayout L = agg_layout(H, W, 1, 1, false);
+    const AggLayout L = agg_layout(H, W, n_entries, 1, true);
     const int *off = (const int *)((const char *)agg_ws + L.off);
+    const int *lpos = (const int *)((const char *)agg_ws + L.lpos);
     dim3 grid((W + 8 * kSegX - 1) / (8 * kSegX), (H + kSegRows - 1) / kSegRows);
-    k_gather_planar<<<grid, 256, 0, st>>>(planes, w_slot, off, (long long)n_entries * 8, H, W, pitch,
+    k_gather_planar<<<grid, 256, 0, st>>>(planes, w_slot, off, lpos, (long long)n_entries * 8, H, W, pitch,
                                           make_win(window8), out);
     return cudaGetLastError();
 }

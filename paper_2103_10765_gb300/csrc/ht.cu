@@ -10,9 +10,15 @@
 // group axis; rows and columns use the lifting form of bior1.5
 //   d[n]  = (x[2n] - x[2n+1]) / sqrt2,  a0[n] = (x[2n] + x[2n+1]) / sqrt2,
 //   a[n]  = a0[n] + (3 d[n-2] - 22 d[n-1] + 22 d[n+1] - 3 d[n+2]) / 128,
-// and its exact inverse.  Detail bands are hard-thresholded as they are
-// written.  The level-1 synthesis writes the filtered blocks straight into
-// the group-major output (undoing the spin shift), averaging the spins.
+// and its exact inverse.  Each thread of a lifting pass slides along one line
+// in registers (every pair's d and a0 computed once); shared-memory row
+// strides are odd so the column passes are conflict-free.  Detail bands are
+// hard-thresholded as they are written.
+//
+// The level-1 synthesis writes the filtered blocks into a group-major
+// buffer (averaging the spins); one last pass per group stages the group,
+// computes its TV weight and, for the aggregation, copies its rows into the
+// position-sorted planar layout.
 #include "internal.cuh"
 
 namespace gbm3d {
@@ -22,8 +28,11 @@ constexpr float kS = 0.70710678118654752f; // 1/sqrt(2)
 constexpr float kU1 = 0.171875f;           // 22/128
 constexpr float kU2 = 0.0234375f;          // 3/128
 constexpr int TY = 16, TX = 32;            // output positions per tile
-constexpr int IY = 2 * TY + 8, IX = 2 * TX + 8; // analysis input tile (halo 4 / 4 after the pair)
-constexpr int HY = TY + 4, HX = TX + 4;    // synthesis band tile (halo 2 each side)
+constexpr int IY = 2 * TY + 8, IX = 2 * TX + 8; // analysis input tile: 40 x 72
+constexpr int SX = IX + 1;                 // its shared row stride (odd)
+constexpr int HY = TY + 4, HX = TX + 4;    // synthesis band tile with halo 2: 20 x 36
+constexpr int SB = HX + 1;                 // its shared row stride (odd)
+constexpr int SO = 2 * TX + 1;             // synthesis output row stride (odd)
 
 // Periodic index (eq. (1)).  Tile halos reach at most a few samples past
 // either end, so one conditional add or subtract suffices unless the axis is
@@ -50,194 +59,253 @@ __global__ void k_offsets(const int32_t *__restrict__ idx, int n, int H, int W, 
     ofs[e] = k * pitch + l;
 }
 
-// Lifting update U(d)[n] from the five detail values d[n-2..n+2].
+// Lifting update U(d)[n] from the four detail values d[n-2], d[n-1], d[n+1], d[n+2].
 __device__ __forceinline__ float lift_u(float dm2, float dm1, float dp1, float dp2)
 {
     return kU2 * (dm2 - dp2) + kU1 * (dp1 - dm1);
 }
 
-// One analysis step on ten consecutive samples v[0..9] = x[2n-4 .. 2n+5]:
-// returns the low-pass a[n] and the high-pass d[n].
-__device__ __forceinline__ void ana10(const float *v, int stride, float &lo, float &hi)
-{
-    float d[5];
-#pragma unroll
-    for (int m = 0; m < 5; m++) d[m] = (v[(2 * m) * stride] - v[(2 * m + 1) * stride]) * kS;
-    const float a0 = (v[4 * stride] + v[5 * stride]) * kS;
-    lo = a0 + lift_u(d[0], d[1], d[3], d[4]);
-    hi = d[2];
-}
-
 // Level analysis: input (Z, Y, X) -> 8 bands [band][Z/2][Y/2][X/2], band =
 // 4 hz + 2 hy + hx.  GATHER: the input is the cycle-spun mosaic read from the
-// image through idx (level 1); otherwise a [Z][Y][X] plane stack.
+// image through the pixel offsets of the match list (level 1); otherwise a
+// [Z][Y][X] plane stack.  vec: X/2 is a multiple of 4 (float4 stores).
 template <bool GATHER>
 __global__ void __launch_bounds__(256)
 k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitch, const int *__restrict__ ofs,
-          int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst, float tau)
+          int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst, float tau, int vec)
 {
-    __shared__ float s_in[2][IY][IX];
-    __shared__ float s_y[2][2][TY][IX]; // [z band][y band][row][col]
+    __shared__ float s_in[2][IY][SX];   // z-low, z-high planes of the input tile
+    __shared__ float s_y[2][2][TY][SX]; // after the y pass: [z band][y band][row][col]
     const int m = blockIdx.z;            // slice pair
     const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
     const int iy0 = 2 * y0 - 4, ix0 = 2 * x0 - 4;
-    for (int e = threadIdx.x; e < 2 * IY * IX; e += blockDim.x) {
-        const int zz = e / (IY * IX), rem = e - zz * (IY * IX);
-        const int yy = rem / IX, xx = rem - yy * IX;
-        float v;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // load (one warp per tile row, row-uniform index math) + Haar along z
+    int z0 = 2 * m, z1 = 2 * m + 1;
+    if (GATHER) {
+        z0 = pwrap(z0 - shift, Z);
+        z1 = pwrap(z1 - shift, Z);
+    }
+    for (int yy = warp; yy < IY; yy += 8) {
         if (GATHER) {
-            const int z = pwrap(2 * m + zz - shift, Z);
-            const int y = pwrap(iy0 + yy - shift, Y), x = pwrap(ix0 + xx - shift, X);
-            const int g = (y >> 3) * Bx + (x >> 3);
-            const int o = __ldg(ofs + (size_t)g * Z + z);
-            v = __ldg(img + o + (size_t)(y & 7) * pitch + (x & 7));
+            const int y = pwrap(iy0 + yy - shift, Y);
+            const int gb = (y >> 3) * Bx;
+            const float *rowimg = img + (size_t)(y & 7) * pitch;
+            for (int xx = lane; xx < IX; xx += 32) {
+                const int x = pwrap(ix0 + xx - shift, X);
+                const size_t g = (size_t)(gb + (x >> 3)) * Z;
+                const float *b = rowimg + (x & 7);
+                const float v0 = __ldg(b + __ldg(ofs + g + z0)), v1 = __ldg(b + __ldg(ofs + g + z1));
+                s_in[0][yy][xx] = (v0 + v1) * kS;
+                s_in[1][yy][xx] = (v0 - v1) * kS;
+            }
         } else {
-            const int y = pwrap(iy0 + yy, Y), x = pwrap(ix0 + xx, X);
-            v = __ldg(src + ((size_t)(2 * m + zz) * Y + y) * X + x);
+            const int y = pwrap(iy0 + yy, Y);
+            const float *r0 = src + ((size_t)z0 * Y + y) * X, *r1 = src + ((size_t)z1 * Y + y) * X;
+            for (int xx = lane; xx < IX; xx += 32) {
+                const int x = pwrap(ix0 + xx, X);
+                const float v0 = __ldg(r0 + x), v1 = __ldg(r1 + x);
+                s_in[0][yy][xx] = (v0 + v1) * kS;
+                s_in[1][yy][xx] = (v0 - v1) * kS;
+            }
         }
-        s_in[zz][yy][xx] = v;
     }
     __syncthreads();
-    // Haar along z (slice pair) in place: [0] = low, [1] = high.
-    for (int e = threadIdx.x; e < IY * IX; e += blockDim.x) {
-        const int yy = e / IX, xx = e - yy * IX;
-        const float a = s_in[0][yy][xx], b = s_in[1][yy][xx];
-        s_in[0][yy][xx] = (a + b) * kS;
-        s_in[1][yy][xx] = (a - b) * kS;
+
+    // y pass: one thread per (z band, column); output row o uses pairs o .. o+4
+    if (tid < 2 * IX) {
+        const int zb = tid >= IX, xx = tid - zb * IX;
+        float d[IY / 2], a0[IY / 2];
+#pragma unroll
+        for (int n = 0; n < IY / 2; n++) {
+            const float u = s_in[zb][2 * n][xx], v = s_in[zb][2 * n + 1][xx];
+            d[n] = (u - v) * kS;
+            a0[n] = (u + v) * kS;
+        }
+#pragma unroll
+        for (int o = 0; o < TY; o++) {
+            s_y[zb][0][o][xx] = a0[o + 2] + lift_u(d[o], d[o + 1], d[o + 3], d[o + 4]);
+            s_y[zb][1][o][xx] = d[o + 2];
+        }
     }
     __syncthreads();
-    // bior1.5 along y: output row o uses input rows 2o .. 2o+9 of the tile.
-    for (int e = threadIdx.x; e < 2 * TY * IX; e += blockDim.x) {
-        const int zb = e / (TY * IX), rem = e - zb * (TY * IX);
-        const int o = rem / IX, xx = rem - o * IX;
-        float lo, hi;
-        ana10(&s_in[zb][2 * o][xx], IX, lo, hi);
-        s_y[zb][0][o][xx] = lo;
-        s_y[zb][1][o][xx] = hi;
+
+    // x pass: thread (row = tid & 63: z band, y band, output row; chunk of 8
+    // output columns = tid >> 6), sliding over 12 pairs
+    const int row = tid & 63, chunk = tid >> 6;
+    const int zb = row >> 5, yb = (row >> 4) & 1, o = row & 15;
+    const float *sr = &s_y[zb][yb][o][16 * chunk];
+    float d[12], a0[12];
+#pragma unroll
+    for (int n = 0; n < 12; n++) {
+        const float u = sr[2 * n], v = sr[2 * n + 1];
+        d[n] = (u - v) * kS;
+        a0[n] = (u + v) * kS;
     }
-    __syncthreads();
-    // bior1.5 along x, threshold, store.
+    const int band = zb * 4 + yb * 2;
+    float lo[8], hi[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const float a = a0[j + 2] + lift_u(d[j], d[j + 1], d[j + 3], d[j + 4]);
+        const float h = d[j + 2];
+        lo[j] = (band == 0 || fabsf(a) >= tau) ? a : 0.f;
+        hi[j] = (fabsf(h) >= tau) ? h : 0.f;
+    }
     const int Zo = Z >> 1, Yo = Y >> 1, Xo = X >> 1;
-    const size_t band_elems = (size_t)Zo * Yo * Xo;
-    for (int e = threadIdx.x; e < 4 * TY * TX; e += blockDim.x) {
-        const int zy = e / (TY * TX), rem = e - zy * (TY * TX);
-        const int o = rem / TX, ox = rem - o * TX;
-        const int zb = zy >> 1, yb = zy & 1;
-        const int yo = y0 + o, xo = x0 + ox;
-        if (yo >= Yo || xo >= Xo) continue;
-        float lo, hi;
-        ana10(&s_y[zb][yb][o][2 * ox], 1, lo, hi);
-        const int band = zb * 4 + yb * 2;
-        const size_t off = ((size_t)m * Yo + yo) * Xo + xo;
-        dst[(size_t)band * band_elems + off] = (band == 0 || fabsf(lo) >= tau) ? lo : 0.f;
-        dst[(size_t)(band + 1) * band_elems + off] = (fabsf(hi) >= tau) ? hi : 0.f;
+    const int yo = y0 + o, xo = x0 + 8 * chunk;
+    if (yo >= Yo || xo >= Xo) return;
+    const size_t E = (size_t)Zo * Yo * Xo;
+    float *pl = dst + band * E + ((size_t)m * Yo + yo) * Xo + xo;
+    float *ph = pl + E;
+    if (vec && xo + 8 <= Xo) {
+        reinterpret_cast<float4 *>(pl)[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        reinterpret_cast<float4 *>(pl)[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
+        reinterpret_cast<float4 *>(ph)[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        reinterpret_cast<float4 *>(ph)[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (xo + j < Xo) {
+                pl[j] = lo[j];
+                ph[j] = hi[j];
+            }
     }
 }
 
-// Inverse lifting for one output pair from the low value at n and the five
-// high values h[n-2..n+2]; writes x[2n], x[2n+1].
-__device__ __forceinline__ void syn_pair(float lo, const float *h, int stride, float &x0, float &x1)
-{
-    const float hm2 = h[0], hm1 = h[stride], hc = h[2 * stride], hp1 = h[3 * stride], hp2 = h[4 * stride];
-    const float a0 = lo - lift_u(hm2, hm1, hp1, hp2);
-    x0 = (a0 + hc) * kS;
-    x1 = (a0 - hc) * kS;
-}
-
-// Level synthesis: 8 bands [band][Zc][Yc][Xc] -> (2Zc, 2Yc, 2Xc).  SCATTER
-// (level 1): the voxel at spun position (z,y,x) belongs to mosaic position
+// Level synthesis: 8 bands [band][Zc][Yc][Xc] -> (2Zc, 2Yc, 2Xc) for one tile
+// of 16 x 32 coefficient positions and one slice pair.  SCATTER (level 1):
+// the voxel at spun position (z,y,x) belongs to mosaic position
 // (z,y,x) - shift, i.e. block r = z of group (y/8, x/8) at (y%8, x%8); it is
-// written (or added) scaled into the output blocks.
+// written (or added) scaled through the GroupOut.
 template <bool SCATTER>
 __global__ void __launch_bounds__(256)
 k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restrict__ dst, GroupOut out, int Bx,
           int shift, float scale, int accumulate)
 {
-    __shared__ float s_b[8][HY][HX];
-    __shared__ float s_x[2][2][HY][2 * TX]; // [z band][y band][coef row][output col]
+    __shared__ float s_b[8][HY][SB];     // band tile with halo; later reused for the y-pass output
+    __shared__ float s_x[2][2][HY][SO];  // after the x inverse: [z band][y band][coef row][output col]
     const int m = blockIdx.z;
     const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
-    const size_t band_elems = (size_t)Zc * Yc * Xc;
-    for (int e = threadIdx.x; e < 8 * HY * HX; e += blockDim.x) {
-        const int band = e / (HY * HX), rem = e - band * (HY * HX);
-        const int yy = rem / HX, xx = rem - yy * HX;
-        const int y = pwrap(y0 - 2 + yy, Yc), x = pwrap(x0 - 2 + xx, Xc);
-        s_b[band][yy][xx] = __ldg(coef + (size_t)band * band_elems + ((size_t)m * Yc + y) * Xc + x);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t E = (size_t)Zc * Yc * Xc;
+
+    for (int rr = warp; rr < 8 * HY; rr += 8) { // one warp per (band, halo row)
+        const int band = rr / HY, yy = rr - band * HY;
+        const float *src = coef + band * E + ((size_t)m * Yc + pwrap(y0 - 2 + yy, Yc)) * Xc;
+        for (int xx = lane; xx < HX; xx += 32) s_b[band][yy][xx] = __ldg(src + pwrap(x0 - 2 + xx, Xc));
     }
     __syncthreads();
-    // inverse along x for every (z band, y band) and coefficient row
-    for (int e = threadIdx.x; e < 4 * HY * TX; e += blockDim.x) {
-        const int zy = e / (HY * TX), rem = e - zy * (HY * TX);
-        const int row = rem / TX, o = rem - row * TX;
-        const int lo_band = zy * 2; // (hz, hy, hx = 0); high band is lo_band + 1
-        float v0, v1;
-        syn_pair(s_b[lo_band][row][o + 2], &s_b[lo_band + 1][row][o], 1, v0, v1);
-        s_x[zy >> 1][zy & 1][row][2 * o] = v0;
-        s_x[zy >> 1][zy & 1][row][2 * o + 1] = v1;
+
+    // inverse along x: job (halo row id 0..79 = (z band, y band, row), chunk of
+    // 4 output pairs); pair n of the tile needs low n and highs n-2 .. n+2
+    for (int job = tid; job < 4 * HY * 8; job += 256) {
+        const int rid = job % (4 * HY), chunk = job / (4 * HY);
+        const int zy = rid / HY, rw = rid - zy * HY;
+        const float *lo = &s_b[2 * zy][rw][4 * chunk + 2];
+        const float *hi = &s_b[2 * zy + 1][rw][4 * chunk];
+        float h[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) h[i] = hi[i];
+        float *dst_x = &s_x[zy >> 1][zy & 1][rw][8 * chunk];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            const float a0 = lo[p] - lift_u(h[p], h[p + 1], h[p + 3], h[p + 4]);
+            dst_x[2 * p] = (a0 + h[p + 2]) * kS;
+            dst_x[2 * p + 1] = (a0 - h[p + 2]) * kS;
+        }
     }
     __syncthreads();
-    // inverse along y, then Haar along z; store
+
+    // inverse along y: thread (z band, half of the 16 pairs, output column)
+    float(*s_o)[2 * TY][SO] = reinterpret_cast<float(*)[2 * TY][SO]>(&s_b[0][0][0]); // [z band][row][col]
+    {
+        const int zb = tid >> 7, half = (tid >> 6) & 1, col = tid & 63;
+        float h[12];
+#pragma unroll
+        for (int i = 0; i < 12; i++) h[i] = s_x[zb][1][8 * half + i][col];
+#pragma unroll
+        for (int p = 0; p < 8; p++) {
+            const float a0 = s_x[zb][0][8 * half + 2 + p][col] - lift_u(h[p], h[p + 1], h[p + 3], h[p + 4]);
+            s_o[zb][16 * half + 2 * p][col] = (a0 + h[p + 2]) * kS;
+            s_o[zb][16 * half + 2 * p + 1][col] = (a0 - h[p + 2]) * kS;
+        }
+    }
+    __syncthreads();
+
+    // inverse along z, store
     const int Yo = 2 * Yc, Xo = 2 * Xc, Zo = 2 * Zc;
-    for (int e = threadIdx.x; e < TY * 2 * TX; e += blockDim.x) {
-        const int o = e / (2 * TX), col = e - o * (2 * TX);
-        float a0, a1, b0, b1;
-        syn_pair(s_x[0][0][o + 2][col], &s_x[0][1][o][col], 2 * TX, a0, a1);
-        syn_pair(s_x[1][0][o + 2][col], &s_x[1][1][o][col], 2 * TX, b0, b1);
-        const float vz[2][2] = {{(a0 + b0) * kS, (a1 + b1) * kS}, {(a0 - b0) * kS, (a1 - b1) * kS}};
-        const int yb = 2 * (y0 + o), xo = 2 * x0 + col;
-        if (xo >= Xo || yb >= Yo) continue;
+    for (int e = tid; e < 2 * TY * 2 * TX; e += 256) {
+        const int orow = e >> 6, col = e & 63;
+        const int ys = 2 * y0 + orow, xo = 2 * x0 + col;
+        if (ys >= Yo || xo >= Xo) continue;
+        const float L = s_o[0][orow][col], Hh = s_o[1][orow][col];
+        const float v[2] = {(L + Hh) * kS, (L - Hh) * kS};
 #pragma unroll
-        for (int zz = 0; zz < 2; zz++)
-#pragma unroll
-            for (int yy = 0; yy < 2; yy++) {
-                const int zs = 2 * m + zz, ys = yb + yy;
-                const float v = vz[zz][yy];
-                if (SCATTER) {
-                    const int z = pwrap(zs - shift, Zo), y = pwrap(ys - shift, Yo), x = pwrap(xo - shift, Xo);
-                    const long long g = (long long)(y >> 3) * Bx + (x >> 3);
-                    float *o_ = out.row(g * Zo + z, y & 7) + (x & 7);
-                    *o_ = accumulate ? (*o_ + scale * v) : scale * v;
-                } else {
-                    dst[((size_t)zs * Yo + ys) * Xo + xo] = v;
-                }
+        for (int zz = 0; zz < 2; zz++) {
+            const int zs = 2 * m + zz;
+            if (SCATTER) {
+                const int z = pwrap(zs - shift, Zo), y = pwrap(ys - shift, Yo), x = pwrap(xo - shift, Xo);
+                const long long g = (long long)(y >> 3) * Bx + (x >> 3);
+                float *o_ = out.row(g * Zo + z, y & 7) + (x & 7);
+                *o_ = accumulate ? (*o_ + scale * v[zz]) : scale * v[zz];
+            } else {
+                dst[((size_t)zs * Yo + ys) * Xo + xo] = v[zz];
             }
+        }
     }
 }
 
 // Stage-1 weights: w = 1 / max(TV(u), eps) with TV the sum of absolute
 // forward differences along rows, columns and the group axis inside the
-// N x N x K block (no wrap).  One warp per group; lane = 4 a + bh owns the
-// two columns 2bh, 2bh+1 of row a of every block.
-__global__ void k_tv(GroupOut out, int G, int K, float eps)
+// N x N x K block (no wrap).  One warp per group reads the group-major block
+// gm[g][r][a][b] (contiguous, float4), stages it in shared memory, sums the
+// differences and writes w; with permute it also copies each block row to
+// out.row(g*K + r, a) and w to each of the group's slots.
+constexpr int kTvWarps = 4;
+
+template <int K>
+__global__ void __launch_bounds__(kTvWarps * 32) k_tv(const float *__restrict__ gm, int G, float eps, GroupOut out,
+                                                      int permute)
 {
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+    constexpr int NV = K * 16 / 32; // float4 per lane
+    __shared__ __align__(16) float su[kTvWarps][K * 64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kTvWarps + warp;
     if (g >= G) return;
-    const int a = lane >> 2, bh = lane & 3;
+    float *u = su[warp];
+    const float4 *src = reinterpret_cast<const float4 *>(gm + (size_t)g * K * 64);
+    float4 v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; i++) v[i] = __ldg(src + lane + 32 * i);
+#pragma unroll
+    for (int i = 0; i < NV; i++) reinterpret_cast<float4 *>(u)[lane + 32 * i] = v[i];
+    __syncwarp();
     float tv = 0.f;
-    for (int r = 0; r < K; r++) {
-        const long long e = (long long)g * K + r;
-        const float *row = out.row(e, a);
-        const float v0 = row[2 * bh], v1 = row[2 * bh + 1];
-        tv += fabsf(v1 - v0);
-        if (bh < 3) tv += fabsf(row[2 * bh + 2] - v1);
-        if (a < 7) {
-            const float *nxt = out.row(e, a + 1);
-            tv += fabsf(nxt[2 * bh] - v0) + fabsf(nxt[2 * bh + 1] - v1);
-        }
-        if (r < K - 1) {
-            const float *nz = out.row(e + 1, a);
-            tv += fabsf(nz[2 * bh] - v0) + fabsf(nz[2 * bh + 1] - v1);
-        }
+#pragma unroll 4
+    for (int e = lane; e < K * 64; e += 32) {
+        const int r = e >> 6, a = (e >> 3) & 7, b = e & 7;
+        const float c = u[e];
+        if (a < 7) tv += fabsf(u[e + 8] - c);
+        if (b < 7) tv += fabsf(u[e + 1] - c);
+        if (r < K - 1) tv += fabsf(u[e + 64] - c);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tv += __shfl_xor_sync(0xffffffffu, tv, o);
     const float wv = 1.f / fmaxf(tv, eps);
-    if (out.per_slot) {
-        for (int r = lane; r < K; r += 32) out.w[out.slot((long long)g * K + r)] = wv;
-    } else if (lane == 0) {
-        out.w[g] = wv;
+    if (!permute) {
+        if (lane == 0) out.w[g] = wv;
+        return;
     }
+#pragma unroll
+    for (int i = 0; i < K * 8 / 32; i++) { // block row q = 8 r + a
+        const int q = lane + 32 * i;
+        const float4 *s = reinterpret_cast<const float4 *>(u + q * 8);
+        float4 *d = reinterpret_cast<float4 *>(out.row((long long)g * K + (q >> 3), q & 7));
+        d[0] = s[0];
+        d[1] = s[1];
+    }
+    if (lane < K) out.w[out.slot((long long)g * K + lane)] = wv;
 }
 
 } // namespace
@@ -260,6 +328,8 @@ HtGeom ht_geom(int By, int Bx, int K, int levels)
     }
     g.ofs_off = off;
     off += align_up((size_t)By * Bx * K * sizeof(int));
+    g.gm_off = off;
+    off += align_up((size_t)By * Bx * K * kPatch * kPatch * sizeof(float));
     g.bytes = off;
     return g;
 }
@@ -274,31 +344,41 @@ cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const in
     k_offsets<<<(nent + 255) / 256, 256, 0, st>>>(idx, nent, H, W, pitch, ofs);
     float *C[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int l = 1; l <= g.levels; l++) C[l] = (float *)(base + g.level_off[l]);
+    // the level-1 synthesis writes group-major: the output itself, or a
+    // scratch that the TV pass permutes into the output's layout
+    const bool permute = out.slot_of != nullptr;
+    float *gm = permute ? (float *)(base + g.gm_off) : out.base;
+    const GroupOut gm_out = group_major(gm, nullptr);
     const float inv_c = 1.f / (float)cycle_spins;
     for (int c = 0; c < cycle_spins; c++) {
-        // analysis, levels 1..L
-        for (int l = 1; l <= g.levels; l++) {
+        for (int l = 1; l <= g.levels; l++) { // analysis
             const int Y = g.Yd >> (l - 1), X = g.Xd >> (l - 1), Z = g.K >> (l - 1);
             const float tau = sigma * (tau_a - tau_b * (float)l);
+            const int vec = ((X >> 1) % 4) == 0;
             dim3 grid((X / 2 + TX - 1) / TX, (Y / 2 + TY - 1) / TY, Z / 2);
             if (l == 1)
-                k_dwt_ana<true><<<grid, 256, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau);
+                k_dwt_ana<true><<<grid, 256, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
             else
-                k_dwt_ana<false><<<grid, 256, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau);
+                k_dwt_ana<false><<<grid, 256, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau, vec);
         }
         // synthesis, levels L..1; level l writes the approximation of level
-        // l-1, i.e. band 0 of C[l-1] (or the groups for l = 1)
+        // l-1, i.e. band 0 of C[l-1] (or the blocks for l = 1)
         for (int l = g.levels; l >= 1; l--) {
             const int Yc = g.Yd >> l, Xc = g.Xd >> l, Zc = g.K >> l;
             dim3 grid((Xc + TX - 1) / TX, (Yc + TY - 1) / TY, Zc);
             if (l == 1)
-                k_dwt_syn<true><<<grid, 256, 0, st>>>(C[1], Yc, Xc, Zc, nullptr, out, g.Bx, c, inv_c, c > 0);
+                k_dwt_syn<true><<<grid, 256, 0, st>>>(C[1], Yc, Xc, Zc, nullptr, gm_out, g.Bx, c, inv_c, c > 0);
             else
-                k_dwt_syn<false><<<grid, 256, 0, st>>>(C[l], Yc, Xc, Zc, C[l - 1], out, 0, 0, 0.f, 0);
+                k_dwt_syn<false><<<grid, 256, 0, st>>>(C[l], Yc, Xc, Zc, C[l - 1], gm_out, 0, 0, 0.f, 0);
         }
     }
     const int G = g.By * g.Bx;
-    k_tv<<<(G + 7) / 8, 256, 0, st>>>(out, G, g.K, eps_w);
+    const int tb = (G + kTvWarps - 1) / kTvWarps;
+    switch (g.K) {
+    case 8: k_tv<8><<<tb, kTvWarps * 32, 0, st>>>(gm, G, eps_w, out, permute); break;
+    case 16: k_tv<16><<<tb, kTvWarps * 32, 0, st>>>(gm, G, eps_w, out, permute); break;
+    default: k_tv<32><<<tb, kTvWarps * 32, 0, st>>>(gm, G, eps_w, out, permute); break;
+    }
     return cudaGetLastError();
 }
 

@@ -85,12 +85,13 @@ struct HtGeom {
     size_t level_elems[4];  // elements of the coefficient buffer of level l (1-based)
     size_t level_off[4];    // byte offset of each level buffer in the HT scratch
     size_t ofs_off;         // byte offset of the pixel-offset table (G*K ints)
+    size_t gm_off;          // byte offset of the group-major block scratch (G*K*64 floats)
     size_t bytes;           // total HT scratch
 };
 HtGeom ht_geom(int By, int Bx, int K, int levels);
 
 struct AggLayout {
-    size_t cnt, off, cursor, list, slot_of, bsum, bytes; // byte offsets and total
+    size_t cnt, off, cursor, list, slot_of, lpos, bsum, bytes; // byte offsets and total
     int npos, nblk;
 };
 AggLayout agg_layout(int H, int W, int G, int K, bool with_slots = false);

@@ -22,9 +22,10 @@
 // Selection (K-1 best keys (distance, k*W+l)) follows the warp-select
 // pattern: lane t holds the t-th best of a sorted 32-entry list; candidates
 // that beat the current (K-1)-th key are appended to a per-warp buffer in
-// shared memory (ballot + prefix count, no serialisation); whenever 32 have
-// accumulated they are bitonic-sorted across the warp and merged into the
-// list.  The scan starts at the reference's own rows so that the threshold
+// shared memory (ballot + prefix count, no serialisation); after each batch
+// of kVB candidate rows, every full 32 buffered entries are bitonic-sorted
+// across the warp and merged into the list (one merge site, so the unrolled
+// loop body stays small).  The scan starts at the reference's own rows so that the threshold
 // tightens early.  The reference block itself is excluded and written to
 // slot 0.
 #include <float.h>
@@ -38,7 +39,7 @@ namespace {
 constexpr int kRefsPerCta = 8;
 constexpr int kVB = 8;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBuf = 64; // per-warp candidate buffer (entries)
+constexpr int kBuf = 32 * kVB + 32; // per-warp candidate buffer: one iteration's appends + a partial batch
 
 typedef unsigned long long f2; // two packed FP32 values
 
@@ -204,28 +205,32 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
                 wb_i[pos] = cid;
             }
             cnt += __popc(mask);
-            if (cnt >= 32) {
-                __syncwarp();
-                float bd = wb_d[lane];
-                int bi = wb_i[lane];
+        }
+        if (cnt >= 32) {
+            __syncwarp();
+            int head = 0;
+            do {
+                float bd = wb_d[head + lane];
+                int bi = wb_i[head + lane];
                 bitonic_sort32(bd, bi, lane);
                 merge32(ld, li, bd, bi, lane);
+                head += 32;
                 cnt -= 32;
-                float md = 0.f;
-                int mi = 0;
-                if (lane < cnt) {
-                    md = wb_d[32 + lane];
-                    mi = wb_i[32 + lane];
-                }
-                __syncwarp();
-                if (lane < cnt) {
-                    wb_d[lane] = md;
-                    wb_i[lane] = mi;
-                }
-                __syncwarp();
-                thr_d = __shfl_sync(kFull, ld, Kc - 1);
-                thr_i = __shfl_sync(kFull, li, Kc - 1);
+            } while (cnt >= 32);
+            float md = 0.f;
+            int mi = 0;
+            if (lane < cnt) {
+                md = wb_d[head + lane];
+                mi = wb_i[head + lane];
             }
+            __syncwarp();
+            if (lane < cnt) {
+                wb_d[lane] = md;
+                wb_i[lane] = mi;
+            }
+            __syncwarp();
+            thr_d = __shfl_sync(kFull, ld, Kc - 1);
+            thr_i = __shfl_sync(kFull, li, Kc - 1);
         }
     }
     if (cnt > 0) { // flush the partial buffer

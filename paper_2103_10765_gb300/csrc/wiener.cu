@@ -18,7 +18,6 @@ constexpr float kR8 = 0.35355339059327376f; // 1/sqrt(8)
 // cos(k pi / 16)
 constexpr float c1 = 0.98078528040323043f, c2 = 0.92387953251128674f, c3 = 0.83146961230254524f;
 constexpr float c5 = 0.55557023301960218f, c6 = 0.38268343236508977f, c7 = 0.19509032201612825f;
-constexpr int PS = 72; // smem block stride (64 + 8 pad: column passes are conflict-free)
 
 // Orthonormal 8-point DCT-II, even/odd split.
 __device__ __forceinline__ void dct8(float *x)
@@ -56,8 +55,22 @@ __device__ __forceinline__ void idct8(float *X)
     X[4] = e3 - o3;
 }
 
-// Full-depth orthonormal Haar along the group, in registers: one level on
-// the first LEN entries, then recurse on the LEN/2 low-pass entries.
+// Shared-memory address of coefficient (block r, row a, column b):
+//   r*72 + (r/8)*8 + a*9 + b.
+// Row pass (thread (r,a), 8 columns), column pass (thread (r,b), 8 rows) and
+// group pass (thread (8 blocks of one quarter, position a*8+b), lanes = 4
+// quarters x 8 columns) all hit 32 distinct banks.
+__device__ __forceinline__ int sidx(int r, int a, int b) { return r * 72 + (r >> 3) * 8 + a * 9 + b; }
+
+// Haar along the group, K = 2^L blocks, for one coefficient position: the
+// position's K values are spread over Q = K/8 neighbouring lanes (lane bits
+// 0..log2(Q)-1 = quarter q), 8 consecutive blocks each.  Levels 1..3 run in
+// registers on each lane's 8 values (Mallat order: approximation in v[0]);
+// levels 4..L combine the lanes' approximations by shuffles: at level 3+m
+// lanes whose quarter index is a multiple of 2^(m-1) pair with q ^ 2^(m-1),
+// the lower keeps the low-pass, the upper the high-pass.  These are exactly
+// the pairings of the full-depth Mallat transform; every coefficient is held
+// once, so the elementwise shrinkage needs no reordering.
 template <int LEN>
 __device__ __forceinline__ void haar_fwd(float *h)
 {
@@ -86,87 +99,120 @@ __device__ __forceinline__ void haar_inv(float *h)
     for (int m = 0; m < LEN; m++) h[m] = t[m];
 }
 
-template <int K>
+template <int Q>
+__device__ __forceinline__ void haar_fwd_lanes(float *v, int q)
+{
+    haar_fwd<8>(v);
+#pragma unroll
+    for (int st = 1; st < Q; st <<= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, v[0], st);
+        if ((q & (2 * st - 1)) == 0) v[0] = (v[0] + o) * kS;       // lower lane: low-pass
+        else if ((q & (2 * st - 1)) == st) v[0] = (o - v[0]) * kS;  // upper lane: high-pass
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void haar_inv_lanes(float *v, int q)
+{
+#pragma unroll
+    for (int st = Q >> 1; st >= 1; st >>= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, v[0], st);
+        if ((q & (2 * st - 1)) == 0) v[0] = (v[0] + o) * kS;       // low + high
+        else if ((q & (2 * st - 1)) == st) v[0] = (o - v[0]) * kS;  // low - high
+    }
+    haar_inv<8>(v);
+}
+
+// Row a of a block: the 8 floats at rowp[l .. l+7].  VEC: three aligned float4
+// loads (the third only when l is not 4-aligned) and a shift by l & 3.
+template <bool VEC>
+__device__ __forceinline__ void load_row8(const float *__restrict__ rowp, int l, float *v)
+{
+    if (VEC) {
+        const float4 *q = reinterpret_cast<const float4 *>(rowp + (l & ~3));
+        const int sft = l & 3;
+        const float4 A = __ldg(q), B = __ldg(q + 1);
+        const float4 C = sft ? __ldg(q + 2) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
+#pragma unroll
+        for (int b = 0; b < 8; b++)
+            v[b] = sft == 0 ? w[b] : sft == 1 ? w[b + 1] : sft == 2 ? w[b + 2] : w[b + 3];
+    } else {
+#pragma unroll
+        for (int b = 0; b < 8; b++) v[b] = __ldg(rowp + l + b);
+    }
+}
+
+template <int K, bool VEC>
 __global__ void __launch_bounds__(K * 8)
 k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ pilot, int ppitch, int H, int W,
          const int32_t *__restrict__ idx, float sigma2, float eps_w, GroupOut out)
 {
-    constexpr int NT = K * 8;
-    __shared__ __align__(16) float sp[K * PS];
-    __shared__ __align__(16) float sq[K * PS];
+    constexpr int NT = K * 8, Q = K / 8, SZ = K * 72 + K;
+    __shared__ float sp[SZ];
+    __shared__ float sq[SZ];
     __shared__ float red[NT / 32];
     const int g = blockIdx.x, t = threadIdx.x;
-    const int r = t >> 3, a = t & 7;
+    const int r = t >> 3, a = t & 7; // row and column passes: (block r, row/column a)
     {
         int k, l;
         block_kl(__ldg(idx + (size_t)g * K + r), H, W, k, l);
-        const float *pz = noisy + (size_t)(k + a) * npitch + l;
-        const float *py = pilot + (size_t)(k + a) * ppitch + l;
         float xz[8], xy[8];
-#pragma unroll
-        for (int b = 0; b < 8; b++) {
-            xz[b] = __ldg(pz + b);
-            xy[b] = __ldg(py + b);
-        }
+        load_row8<VEC>(noisy + (size_t)(k + a) * npitch, l, xz);
+        load_row8<VEC>(pilot + (size_t)(k + a) * ppitch, l, xy);
         dct8(xz);
         dct8(xy);
 #pragma unroll
         for (int b = 0; b < 8; b++) {
-            sq[r * PS + a * 8 + b] = xz[b];
-            sp[r * PS + a * 8 + b] = xy[b];
+            sq[sidx(r, a, b)] = xz[b];
+            sp[sidx(r, a, b)] = xy[b];
         }
     }
     __syncthreads();
     { // columns: thread (r, b = a)
-        const int b = a;
         float xz[8], xy[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
-            xz[u] = sq[r * PS + u * 8 + b];
-            xy[u] = sp[r * PS + u * 8 + b];
+            xz[u] = sq[sidx(r, u, a)];
+            xy[u] = sp[sidx(r, u, a)];
         }
         dct8(xz);
         dct8(xy);
 #pragma unroll
         for (int u = 0; u < 8; u++) {
-            sq[r * PS + u * 8 + b] = xz[u];
-            sp[r * PS + u * 8 + b] = xy[u];
+            sq[sidx(r, u, a)] = xz[u];
+            sp[sidx(r, u, a)] = xy[u];
         }
     }
     __syncthreads();
-    for (int job = t; job < 128; job += NT) { // Haar along the group, both arrays
-        float *arr = job < 64 ? sp : sq;
-        const int e = job & 63;
-        float h[K];
-#pragma unroll
-        for (int rr = 0; rr < K; rr++) h[rr] = arr[rr * PS + e];
-        haar_fwd<K>(h);
-#pragma unroll
-        for (int rr = 0; rr < K; rr++) arr[rr * PS + e] = h[rr];
-    }
-    __syncthreads();
     float acc = 0.f;
-    for (int e = t; e < K * 64; e += NT) {
-        const int o = (e >> 6) * PS + (e & 63);
-        const float P = sp[o];
-        const float p2 = P * P;
-        const float den = p2 + sigma2;
-        const float om = den > 0.f ? p2 / den : 0.f;
-        sq[o] *= om;
-        acc = fmaf(om, om, acc);
+    { // group axis: thread (position e, quarter q); Haar, shrink, inverse Haar
+        const int q = t & (Q - 1), e = t / Q;
+        const int ea = e >> 3, eb = e & 7;
+        float vp[8], vq[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            vp[i] = sp[sidx(8 * q + i, ea, eb)];
+            vq[i] = sq[sidx(8 * q + i, ea, eb)];
+        }
+        haar_fwd_lanes<Q>(vp, q);
+        haar_fwd_lanes<Q>(vq, q);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const float p2 = vp[i] * vp[i];
+            const float den = p2 + sigma2;
+            const float om = den > 0.f ? p2 / den : 0.f;
+            vq[i] *= om;
+            acc = fmaf(om, om, acc);
+        }
+        haar_inv_lanes<Q>(vq, q);
+#pragma unroll
+        for (int i = 0; i < 8; i++) sq[sidx(8 * q + i, ea, eb)] = vq[i];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((t & 31) == 0) red[t >> 5] = acc;
     __syncthreads();
-    for (int e = t; e < 64; e += NT) {
-        float h[K];
-#pragma unroll
-        for (int rr = 0; rr < K; rr++) h[rr] = sq[rr * PS + e];
-        haar_inv<K>(h);
-#pragma unroll
-        for (int rr = 0; rr < K; rr++) sq[rr * PS + e] = h[rr];
-    }
     if (t < K) {
         float s = 0.f;
         for (int i = 0; i < NT / 32; i++) s += red[i];
@@ -174,21 +220,19 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
         if (out.per_slot) out.w[out.slot((long long)g * K + t)] = wv;
         else if (t == 0) out.w[g] = wv;
     }
-    __syncthreads();
-    {
-        const int b = a;
+    { // inverse columns
         float x[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) x[u] = sq[r * PS + u * 8 + b];
+        for (int u = 0; u < 8; u++) x[u] = sq[sidx(r, u, a)];
         idct8(x);
 #pragma unroll
-        for (int u = 0; u < 8; u++) sq[r * PS + u * 8 + b] = x[u];
+        for (int u = 0; u < 8; u++) sq[sidx(r, u, a)] = x[u];
     }
     __syncthreads();
     {
         float x[8];
 #pragma unroll
-        for (int b = 0; b < 8; b++) x[b] = sq[r * PS + a * 8 + b];
+        for (int b = 0; b < 8; b++) x[b] = sq[sidx(r, a, b)];
         idct8(x);
         float4 *o = reinterpret_cast<float4 *>(out.row((long long)g * K + r, a));
         o[0] = make_float4(x[0], x[1], x[2], x[3]);
@@ -198,15 +242,29 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
 
 } // namespace
 
+template <int K>
+static void wiener_k(bool vec, int G, const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
+                     const int32_t *idx, float s2, float eps_w, const GroupOut &out, cudaStream_t st)
+{
+    if (vec)
+        k_wiener<K, true><<<G, K * 8, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out);
+    else
+        k_wiener<K, false><<<G, K * 8, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out);
+}
+
 cudaError_t launch_filter_wiener(const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
                                  const int32_t *idx, int G, int K, float sigma, float eps_w, const GroupOut &out,
                                  cudaStream_t st)
 {
     const float s2 = sigma * sigma;
+    // Vector row loads read up to 3 floats past a block row, inside the same
+    // 4-aligned span: safe when W, both pitches and both bases are 4-aligned.
+    const bool vec = (W % 4 == 0) && (npitch % 4 == 0) && (ppitch % 4 == 0) && ((uintptr_t)noisy % 16 == 0) &&
+                     ((uintptr_t)pilot % 16 == 0);
     switch (K) {
-    case 8: k_wiener<8><<<G, 64, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out); break;
-    case 16: k_wiener<16><<<G, 128, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out); break;
-    case 32: k_wiener<32><<<G, 256, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out); break;
+    case 8: wiener_k<8>(vec, G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
+    case 16: wiener_k<16>(vec, G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
+    case 32: wiener_k<32>(vec, G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
