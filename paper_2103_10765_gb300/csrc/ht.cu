@@ -36,15 +36,19 @@ constexpr int SO = 2 * TX + 1;             // synthesis output row stride (odd)
 
 // Periodic index (eq. (1)).  Tile halos reach at most a few samples past
 // either end, so one conditional add or subtract suffices unless the axis is
-// shorter than the halo (coarse levels of tiny images): then the true modulo.
+// shorter than the halo (coarse levels of tiny images): then the true modulo,
+// kept out of line so that it is never executed speculatively.
+__device__ __noinline__ int pwrap_slow(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
 __device__ __forceinline__ int pwrap(int i, int n)
 {
     if (i < 0) i += n;
     if (i >= n) i -= n;
-    if ((unsigned)i >= (unsigned)n) {
-        i %= n;
-        if (i < 0) i += n;
-    }
+    if ((unsigned)i >= (unsigned)n) i = pwrap_slow(i, n);
     return i;
 }
 
@@ -81,35 +85,69 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
     const int iy0 = 2 * y0 - 4, ix0 = 2 * x0 - 4;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // load (one warp per tile row, row-uniform index math) + Haar along z
+    // load (one warp per tile row) + Haar along z.  Gather: the tile's input
+    // rows and columns span at most 6 x 10 blocks of the mosaic (an 8-aligned
+    // block wraps as a whole), whose pixel offsets for the two slices are
+    // staged in shared memory first; every voxel is then one image load.
+    __shared__ int s_ofs[6][10][2];
     int z0 = 2 * m, z1 = 2 * m + 1;
+    const int uy0 = iy0 - shift, ux0 = ix0 - shift;
+    const int ybase = (uy0 >> 3) << 3, xbase = (ux0 >> 3) << 3; // floor to a block
     if (GATHER) {
         z0 = pwrap(z0 - shift, Z);
         z1 = pwrap(z1 - shift, Z);
+        for (int e = tid; e < 6 * 10 * 2; e += blockDim.x) {
+            const int ry = e / 20, rem = e - ry * 20, rx = rem >> 1, zz = rem & 1;
+            const int gy = pwrap(ybase + 8 * ry, Y) >> 3, gx = pwrap(xbase + 8 * rx, X) >> 3;
+            s_ofs[ry][rx][zz] = __ldg(ofs + (size_t)(gy * Bx + gx) * Z + (zz ? z1 : z0));
+        }
+        __syncthreads();
     }
-    for (int yy = warp; yy < IY; yy += 8) {
-        if (GATHER) {
-            const int y = pwrap(iy0 + yy - shift, Y);
-            const int gb = (y >> 3) * Bx;
-            const float *rowimg = img + (size_t)(y & 7) * pitch;
-            for (int xx = lane; xx < IX; xx += 32) {
-                const int x = pwrap(ix0 + xx - shift, X);
-                const size_t g = (size_t)(gb + (x >> 3)) * Z;
-                const float *b = rowimg + (x & 7);
-                const float v0 = __ldg(b + __ldg(ofs + g + z0)), v1 = __ldg(b + __ldg(ofs + g + z1));
-                s_in[0][yy][xx] = (v0 + v1) * kS;
-                s_in[1][yy][xx] = (v0 - v1) * kS;
-            }
-        } else {
-            const int y = pwrap(iy0 + yy, Y);
-            const float *r0 = src + ((size_t)z0 * Y + y) * X, *r1 = src + ((size_t)z1 * Y + y) * X;
-            for (int xx = lane; xx < IX; xx += 32) {
-                const int x = pwrap(ix0 + xx, X);
-                const float v0 = __ldg(r0 + x), v1 = __ldg(r1 + x);
-                s_in[0][yy][xx] = (v0 + v1) * kS;
-                s_in[1][yy][xx] = (v0 - v1) * kS;
+    { // one warp per tile row; all of a thread's loads in flight before any store
+        constexpr int NR = IY / 8, NH = (IX + 31) / 32; // 5 rows, 3 column chunks
+        float v0[NR][NH], v1[NR][NH];
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+            const int yy = warp + 8 * j;
+            if (GATHER) {
+                const int dy = uy0 + yy - ybase, ry = dy >> 3;
+                const float *rowimg = img + (size_t)(dy & 7) * pitch;
+#pragma unroll
+                for (int h = 0; h < NH; h++) {
+                    const int xx = lane + 32 * h;
+                    v0[j][h] = v1[j][h] = 0.f;
+                    if (xx < IX) {
+                        const int dx = ux0 + xx - xbase;
+                        const float *b = rowimg + (dx & 7);
+                        v0[j][h] = __ldg(b + s_ofs[ry][dx >> 3][0]);
+                        v1[j][h] = __ldg(b + s_ofs[ry][dx >> 3][1]);
+                    }
+                }
+            } else {
+                const int y = pwrap(iy0 + yy, Y);
+                const float *r0 = src + ((size_t)z0 * Y + y) * X, *r1 = src + ((size_t)z1 * Y + y) * X;
+#pragma unroll
+                for (int h = 0; h < NH; h++) {
+                    const int xx = lane + 32 * h;
+                    v0[j][h] = v1[j][h] = 0.f;
+                    if (xx < IX) {
+                        const int x = pwrap(ix0 + xx, X);
+                        v0[j][h] = __ldg(r0 + x);
+                        v1[j][h] = __ldg(r1 + x);
+                    }
+                }
             }
         }
+#pragma unroll
+        for (int j = 0; j < NR; j++)
+#pragma unroll
+            for (int h = 0; h < NH; h++) {
+                const int yy = warp + 8 * j, xx = lane + 32 * h;
+                if (xx < IX) {
+                    s_in[0][yy][xx] = (v0[j][h] + v1[j][h]) * kS;
+                    s_in[1][yy][xx] = (v0[j][h] - v1[j][h]) * kS;
+                }
+            }
     }
     __syncthreads();
 
@@ -190,10 +228,23 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t E = (size_t)Zc * Yc * Xc;
 
-    for (int rr = warp; rr < 8 * HY; rr += 8) { // one warp per (band, halo row)
-        const int band = rr / HY, yy = rr - band * HY;
-        const float *src = coef + band * E + ((size_t)m * Yc + pwrap(y0 - 2 + yy, Yc)) * Xc;
-        for (int xx = lane; xx < HX; xx += 32) s_b[band][yy][xx] = __ldg(src + pwrap(x0 - 2 + xx, Xc));
+    { // one warp per (band, halo row); all of a thread's loads in flight before any store
+        constexpr int NR = 8 * HY / 8; // rows per warp
+        const int xa = pwrap(x0 - 2 + lane, Xc), xb = pwrap(x0 - 2 + 32 + (lane & 3), Xc);
+        float va[NR], vb[NR];
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+            const int rr = warp + 8 * j, band = rr / HY, yy = rr - band * HY;
+            const float *src = coef + band * E + ((size_t)m * Yc + pwrap(y0 - 2 + yy, Yc)) * Xc;
+            va[j] = __ldg(src + xa);
+            vb[j] = lane < HX - 32 ? __ldg(src + xb) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+            const int rr = warp + 8 * j, band = rr / HY, yy = rr - band * HY;
+            s_b[band][yy][lane] = va[j];
+            if (lane < HX - 32) s_b[band][yy][32 + lane] = vb[j];
+        }
     }
     __syncthreads();
 
@@ -233,25 +284,35 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
     }
     __syncthreads();
 
-    // inverse along z, store
+    // inverse along z, store: each thread owns one output column (x index
+    // math once) and every fourth output row
     const int Yo = 2 * Yc, Xo = 2 * Xc, Zo = 2 * Zc;
-    for (int e = tid; e < 2 * TY * 2 * TX; e += 256) {
-        const int orow = e >> 6, col = e & 63;
-        const int ys = 2 * y0 + orow, xo = 2 * x0 + col;
-        if (ys >= Yo || xo >= Xo) continue;
+    const int col = tid & 63, xo = 2 * x0 + col;
+    if (xo >= Xo) return;
+    int bx = 0, z0 = 0, z1 = 0;
+    long long gx = 0;
+    if (SCATTER) {
+        const int x = pwrap(xo - shift, Xo);
+        gx = x >> 3;
+        bx = x & 7;
+        z0 = pwrap(2 * m - shift, Zo);
+        z1 = pwrap(2 * m + 1 - shift, Zo);
+    }
+    for (int orow = tid >> 6; orow < 2 * TY; orow += 4) {
+        const int ys = 2 * y0 + orow;
+        if (ys >= Yo) break;
         const float L = s_o[0][orow][col], Hh = s_o[1][orow][col];
-        const float v[2] = {(L + Hh) * kS, (L - Hh) * kS};
-#pragma unroll
-        for (int zz = 0; zz < 2; zz++) {
-            const int zs = 2 * m + zz;
-            if (SCATTER) {
-                const int z = pwrap(zs - shift, Zo), y = pwrap(ys - shift, Yo), x = pwrap(xo - shift, Xo);
-                const long long g = (long long)(y >> 3) * Bx + (x >> 3);
-                float *o_ = out.row(g * Zo + z, y & 7) + (x & 7);
-                *o_ = accumulate ? (*o_ + scale * v[zz]) : scale * v[zz];
-            } else {
-                dst[((size_t)zs * Yo + ys) * Xo + xo] = v[zz];
-            }
+        const float v0 = (L + Hh) * kS, v1 = (L - Hh) * kS;
+        if (SCATTER) {
+            const int y = pwrap(ys - shift, Yo);
+            const long long g = (long long)(y >> 3) * Bx + gx;
+            float *p0 = out.row(g * Zo + z0, y & 7) + bx;
+            float *p1 = out.row(g * Zo + z1, y & 7) + bx;
+            *p0 = accumulate ? (*p0 + scale * v0) : scale * v0;
+            *p1 = accumulate ? (*p1 + scale * v1) : scale * v1;
+        } else {
+            dst[((size_t)(2 * m) * Yo + ys) * Xo + xo] = v0;
+            dst[((size_t)(2 * m + 1) * Yo + ys) * Xo + xo] = v1;
         }
     }
 }

@@ -4,9 +4,9 @@
 // One warp per reference block, eight references (consecutive grid columns
 // of one grid row) per CTA sharing one shared-memory copy of their search
 // region.  The reference block lives in registers (64 floats per lane, the
-// same in every lane); each lane takes eight vertically stacked candidates at
+// same in every lane); each lane takes four vertically stacked candidates at
 // a time, so every 8-pixel image row it loads from shared memory serves up
-// to eight candidate rows (15 row loads per 8 candidates instead of 64).
+// to four candidate rows (11 row loads per 4 candidates instead of 32).
 // Distances are the exact sum of squared differences in FP32 -- the direct
 // form, not the norm expansion of eq. (expand), which cancels badly in FP32 --
 // computed with Blackwell's packed FP32 pairs (sub/fma.rn.f32x2): the even
@@ -21,12 +21,15 @@
 //
 // Selection (K-1 best keys (distance, k*W+l)) follows the warp-select
 // pattern: lane t holds the t-th best of a sorted 32-entry list; candidates
-// that beat the current (K-1)-th key are appended to a per-warp buffer in
-// shared memory (ballot + prefix count, no serialisation); after each batch
-// of kVB candidate rows, every full 32 buffered entries are bitonic-sorted
-// across the warp and merged into the list (one merge site, so the unrolled
-// loop body stays small).  The scan starts at the reference's own rows so that the threshold
-// tightens early.  The reference block itself is excluded and written to
+// that beat the current (K-1)-th key are handled per candidate row of the
+// batch: when at most kInsertMax lanes qualify (the common case once the list
+// has filled) they are inserted one at a time with a shuffle-based shift, the
+// threshold tightening after each; when more qualify (the first batches)
+// they are appended to a per-warp buffer (ballot + prefix count) and every
+// full 32 are bitonic-sorted across the warp and merged into the list.  The
+// batch's keys are staged in shared memory so that this selection loop is
+// not unrolled.  The scan starts at the reference's own rows so that the
+// threshold tightens early.  The reference block itself is excluded and written to
 // slot 0.
 #include <float.h>
 #include <limits.h>
@@ -37,9 +40,10 @@ namespace gbm3d {
 namespace {
 
 constexpr int kRefsPerCta = 8;
-constexpr int kVB = 8;
+constexpr int kVB = 4;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBuf = 32 * kVB + 32; // per-warp candidate buffer: one iteration's appends + a partial batch
+constexpr int kBuf = 64;       // per-warp candidate buffer: a partial batch + one step's appends
+constexpr int kInsertMax = 4;  // at most this many qualifying candidates: insert one by one
 
 typedef unsigned long long f2; // two packed FP32 values
 
@@ -105,8 +109,10 @@ __device__ __forceinline__ void merge32(float &ld, int &li, float bd, int bi, in
     for (int j = 16; j > 0; j >>= 1) cmpx(ld, li, j, true, lane);
 }
 
+// Three CTAs per SM (<= 85 registers): the extra warps hide the latency of
+// the FP chains better than the registers the compiler gives up cost.
 template <int N>
-__global__ void __launch_bounds__(kRefsPerCta * 32)
+__global__ void __launch_bounds__(kRefsPerCta * 32, 3)
 k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, int R, int K, int col_pad,
         int rw, int32_t *__restrict__ idx, float *__restrict__ dist)
 {
@@ -134,6 +140,9 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
     const int j = grid_pos(q, s, W, N);
     float *wb_d = buf_d + warp * kBuf;
     int *wb_i = buf_i + warp * kBuf;
+    float *cs_d = reinterpret_cast<float *>(buf_i + kRefsPerCta * kBuf) + warp * 32 * kVB; // [c][lane]
+    int *cs_i = reinterpret_cast<int *>(reinterpret_cast<float *>(buf_i + kRefsPerCta * kBuf) +
+                                        kRefsPerCta * 32 * kVB) + warp * 32 * kVB;
 
     f2 r[N][N / 2]; // reference block, column pairs (b, b+1) packed
 #pragma unroll
@@ -189,48 +198,89 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
                 }
             }
         }
+        // keys of the batch (invalid: +inf, INT_MAX never qualify); test them all
+        // against the threshold first -- once the list has filled, most batches
+        // have no qualifying candidate and skip the selection loop
+        float cdv[kVB];
+        int cidv[kVB];
+        unsigned any = 0;
 #pragma unroll
         for (int c = 0; c < kVB; c++) {
             const int kc = k + c;
             const bool valid = vu && dl < nx && kc <= k1 && !(kc == i && l == j);
-            const int cid = kc * W + l;
             float d0, d1;
             unpack2(dd[c], d0, d1);
-            const float cd = d0 + d1;
-            const bool pend = valid && key_less(cd, cid, thr_d, thr_i);
-            const unsigned mask = __ballot_sync(kFull, pend);
-            if (pend) {
-                const int pos = cnt + __popc(mask & lt_mask);
-                wb_d[pos] = cd;
-                wb_i[pos] = cid;
-            }
-            cnt += __popc(mask);
+            cdv[c] = valid ? d0 + d1 : kInf;
+            cidv[c] = valid ? kc * W + l : INT_MAX;
+            any |= __ballot_sync(kFull, key_less(cdv[c], cidv[c], thr_d, thr_i));
         }
-        if (cnt >= 32) {
-            __syncwarp();
-            int head = 0;
-            do {
-                float bd = wb_d[head + lane];
-                int bi = wb_i[head + lane];
-                bitonic_sort32(bd, bi, lane);
-                merge32(ld, li, bd, bi, lane);
-                head += 32;
-                cnt -= 32;
-            } while (cnt >= 32);
-            float md = 0.f;
-            int mi = 0;
-            if (lane < cnt) {
-                md = wb_d[head + lane];
-                mi = wb_i[head + lane];
+        if (!any) continue;
+        // stage the keys so the selection loop below stays rolled (one copy of
+        // its code)
+#pragma unroll
+        for (int c = 0; c < kVB; c++) {
+            cs_d[c * 32 + lane] = cdv[c];
+            cs_i[c * 32 + lane] = cidv[c];
+        }
+#pragma unroll 1
+        for (int c = 0; c < kVB; c++) {
+            const float cd = cs_d[c * 32 + lane];
+            const int cid = cs_i[c * 32 + lane];
+            bool pend = key_less(cd, cid, thr_d, thr_i);
+            unsigned mask = __ballot_sync(kFull, pend);
+            const int nq = __popc(mask);
+            if (nq > kInsertMax) { // many: buffer, merge each full 32 (sort + bitonic merge)
+                if (pend) {
+                    const int pos = cnt + __popc(mask & lt_mask);
+                    wb_d[pos] = cd;
+                    wb_i[pos] = cid;
+                }
+                cnt += nq;
+                if (cnt >= 32) {
+                    __syncwarp();
+                    float bd = wb_d[lane];
+                    int bi = wb_i[lane];
+                    bitonic_sort32(bd, bi, lane);
+                    merge32(ld, li, bd, bi, lane);
+                    cnt -= 32;
+                    float md = 0.f;
+                    int mi = 0;
+                    if (lane < cnt) {
+                        md = wb_d[32 + lane];
+                        mi = wb_i[32 + lane];
+                    }
+                    __syncwarp();
+                    if (lane < cnt) {
+                        wb_d[lane] = md;
+                        wb_i[lane] = mi;
+                    }
+                    __syncwarp();
+                    thr_d = __shfl_sync(kFull, ld, Kc - 1);
+                    thr_i = __shfl_sync(kFull, li, Kc - 1);
+                }
+            } else { // few: insert one at a time, tightening the threshold as we go
+                while (mask) {
+                    const int src = __ffs(mask) - 1;
+                    const float nd = __shfl_sync(kFull, cd, src);
+                    const int ni = __shfl_sync(kFull, cid, src);
+                    const float pd = __shfl_up_sync(kFull, ld, 1);
+                    const int pi = __shfl_up_sync(kFull, li, 1);
+                    if (key_less(nd, ni, ld, li)) {
+                        if (lane == 0 || key_less(pd, pi, nd, ni)) {
+                            ld = nd;
+                            li = ni;
+                        } else {
+                            ld = pd;
+                            li = pi;
+                        }
+                    }
+                    thr_d = __shfl_sync(kFull, ld, Kc - 1);
+                    thr_i = __shfl_sync(kFull, li, Kc - 1);
+                    if (lane == src) pend = false;
+                    pend = pend && key_less(cd, cid, thr_d, thr_i);
+                    mask = __ballot_sync(kFull, pend);
+                }
             }
-            __syncwarp();
-            if (lane < cnt) {
-                wb_d[lane] = md;
-                wb_i[lane] = mi;
-            }
-            __syncwarp();
-            thr_d = __shfl_sync(kFull, ld, Kc - 1);
-            thr_i = __shfl_sync(kFull, li, Kc - 1);
         }
     }
     if (cnt > 0) { // flush the partial buffer
@@ -280,7 +330,8 @@ MatchGeom match_geom(int s, int R)
 size_t match_smem_bytes(int s, int R)
 {
     const MatchGeom g = match_geom(s, R);
-    return (size_t)g.rows * g.rw * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int));
+    return (size_t)g.rows * g.rw * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int)) +
+           (size_t)kRefsPerCta * 32 * kVB * (sizeof(float) + sizeof(int));
 }
 
 cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,

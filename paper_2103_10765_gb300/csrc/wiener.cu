@@ -201,7 +201,7 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
         for (int i = 0; i < 8; i++) {
             const float p2 = vp[i] * vp[i];
             const float den = p2 + sigma2;
-            const float om = den > 0.f ? p2 / den : 0.f;
+            const float om = den > 0.f ? __fdividef(p2, den) : 0.f; // ~2 ulp; den << 2^126
             vq[i] *= om;
             acc = fmaf(om, om, acc);
         }
