@@ -229,15 +229,24 @@ k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_sl
         const float wa = sw[a];
         const float *plane = planes + a * plane_stride;
         const int s0 = __ldg(off + k * W + la), s1 = __ldg(off + k * W + lb + 1);
-#pragma unroll 4
-        for (int e = s0; e < s1; e++) {
-            const int b = x - __ldg(lpos + e);
-            if (xin && b >= 0 && b < 8) {
-                const float wt = __ldg(w_slot + e) * wa * sw[b];
-                const float v = __ldg(plane + (size_t)e * 8 + b);
-                kahan_add(num, cn, wt * v);
-                kahan_add(den, cd, wt);
+        for (int e0 = s0; e0 < s1; e0 += 8) { // chunks of 8 slots, loads issued before use
+            int bq[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) bq[q] = e0 + q < s1 ? x - __ldg(lpos + e0 + q) : -1;
+            float wq[8], vq[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const bool ok = xin && bq[q] >= 0 && bq[q] < 8;
+                wq[q] = ok ? __ldg(w_slot + e0 + q) : 0.f;
+                vq[q] = ok ? __ldg(plane + (size_t)(e0 + q) * 8 + bq[q]) : 0.f;
             }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (xin && bq[q] >= 0 && bq[q] < 8) {
+                    const float wt = wq[q] * wa * sw[bq[q]];
+                    kahan_add(num, cn, wt * vq[q]);
+                    kahan_add(den, cd, wt);
+                }
         }
     }
     if (xin) out[(size_t)y * pitch + x] = num / den;

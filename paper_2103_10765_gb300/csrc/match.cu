@@ -17,7 +17,10 @@
 // column); units are numbered row-major with the column count padded to a
 // multiple of 8 (col_pad), and the shared-memory row stride is chosen so that
 // kVB * stride == col_pad (mod 32).  A warp's 32 consecutive units then read
-// 32 distinct banks even where they straddle two unit rows.
+// 32 distinct banks even where they straddle two unit rows.  Pixels are read
+// as aligned float pairs straight into the packed registers: the region is
+// stored twice, the second copy shifted by one float, and each lane reads
+// whichever copy puts its row start on an even offset.
 //
 // Selection (K-1 best keys (distance, k*W+l)) follows the warp-select
 // pattern: lane t holds the t-th best of a sorted 32-entry list; candidates
@@ -114,7 +117,7 @@ __device__ __forceinline__ void merge32(float &ld, int &li, float bd, int bi, in
 template <int N>
 __global__ void __launch_bounds__(kRefsPerCta * 32, 3)
 k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, int R, int K, int col_pad,
-        int rw, int32_t *__restrict__ idx, float *__restrict__ dist)
+        int rw, int copy_off, int bufs_off, int32_t *__restrict__ idx, float *__restrict__ dist)
 {
     extern __shared__ float sm[];
     const int p = blockIdx.y;
@@ -126,12 +129,16 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
     const int rx0 = max(0, jf - R), rx1 = min(W - N, jl + R) + N;
     const int rwd = rx1 - rx0, rh = ry1 - ry0;
     const int rhp = rh + kVB; // zero rows below absorb the last vertical block
-    float *buf_d = sm + rhp * rw;
+    float *smB = sm + copy_off; // the region again, one float later: smB[e] = sm[e - 1]
+    float *buf_d = sm + bufs_off;
     int *buf_i = reinterpret_cast<int *>(buf_d + kRefsPerCta * kBuf);
     for (int e = threadIdx.x; e < rhp * rw; e += blockDim.x) {
         const int y = e / rw, x = e - y * rw;
-        sm[e] = (y < rh && x < rwd) ? __ldg(img + (size_t)(ry0 + y) * pitch + rx0 + x) : 0.f;
+        const float v = (y < rh && x < rwd) ? __ldg(img + (size_t)(ry0 + y) * pitch + rx0 + x) : 0.f;
+        sm[e] = v;
+        smB[e + 1] = v;
     }
+    if (threadIdx.x == 0) smB[0] = 0.f;
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -182,12 +189,15 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
 #pragma unroll
         for (int c = 0; c < kVB; c++) dd[c] = 0ull;
         if (vu) {
-            const float *base = sm + (k - ry0) * rw + (l - rx0);
+            // 8-byte-aligned start of this lane's rows: even offsets in the
+            // region, odd ones in the shifted copy (rw is even)
+            const int cc = (k - ry0) * rw + (l - rx0);
+            const f2 *base = reinterpret_cast<const f2 *>((cc & 1) ? smB + cc + 1 : sm + cc);
 #pragma unroll
             for (int t = 0; t < kVB + N - 1; t++) {
                 f2 x[N / 2];
 #pragma unroll
-                for (int b = 0; b < N; b += 2) x[b / 2] = pack2(base[t * rw + b], base[t * rw + b + 1]);
+                for (int b = 0; b < N / 2; b++) x[b] = base[t * (rw / 2) + b];
 #pragma unroll
                 for (int c = 0; c < kVB; c++) {
                     const int a = t - c;
@@ -308,6 +318,7 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
 
 struct MatchGeom {
     int col_pad, rw, rows;
+    int copy_off, bufs_off; // floats: offset of the shifted copy, of the selection buffers
 };
 
 MatchGeom match_geom(int s, int R)
@@ -322,6 +333,11 @@ MatchGeom match_geom(int s, int R)
     g.rw = need; // kVB * rw == col_pad (mod 32)
     while ((kVB * g.rw - g.col_pad) % 32 != 0) g.rw++;
     g.rows = 2 * R + kPatch + kVB;
+    // the shifted copy starts 14 words (mod 32) after the region so that the
+    // even-column lanes (region) and odd-column lanes (copy) of a half-warp
+    // fall on disjoint banks
+    g.copy_off = (g.rows * g.rw + 31) / 32 * 32 + 14;
+    g.bufs_off = (g.copy_off + g.rows * g.rw + 2 + 3) / 4 * 4;
     return g;
 }
 
@@ -330,7 +346,7 @@ MatchGeom match_geom(int s, int R)
 size_t match_smem_bytes(int s, int R)
 {
     const MatchGeom g = match_geom(s, R);
-    return (size_t)g.rows * g.rw * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int)) +
+    return (size_t)g.bufs_off * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int)) +
            (size_t)kRefsPerCta * 32 * kVB * (sizeof(float) + sizeof(int));
 }
 
@@ -342,7 +358,8 @@ cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int 
     cudaError_t e = cudaFuncSetAttribute(k_match<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kRefsPerCta - 1) / kRefsPerCta, By);
-    k_match<kPatch><<<grid, kRefsPerCta * 32, smem, st>>>(img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, idx, dist);
+    k_match<kPatch><<<grid, kRefsPerCta * 32, smem, st>>>(img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, g.copy_off,
+                                                          g.bufs_off, idx, dist);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,56 @@
+"""The multi-rank benchmark path on CPU: two gloo ranks, as torch.distributed.run
+would start them.  The path runs independent replicas (one image stream per
+GPU); the only collective is the max over ranks of the timed region."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        env = bench.dist_env()
+        slowest = bench.max_over_ranks(10.0 + 5.0 * rank)
+        q.put((rank, env, bench.rank_seeds(rank), slowest))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [(0, 2, 0), (1, 2, 1)]
+    assert all(r[3] == 15.0 for r in res)  # max over ranks, on every rank
+    seeds0, seeds1 = res[0][2], res[1][2]
+    assert len(set(seeds0) | set(seeds1)) == 6  # each replica has its own images
+
+
+def test_single_rank_helpers():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert abs(bench.job_mpix(2, 10, 1000.0) - 2 * 1024 * 1024 * 10 / 1e6) < 1e-9
+    assert bench.candidate_pairs(64, 64, R=3) == sum(
+        (min(56, i + 3) - max(0, i - 3) + 1) * (min(56, j + 3) - max(0, j - 3) + 1) - 1
+        for i in sorted(set(min(p * 3, 56) for p in range(20))) for j in sorted(set(min(q * 3, 56) for q in range(20))))
