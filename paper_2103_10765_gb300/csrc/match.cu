@@ -9,7 +9,8 @@
 // to four candidate rows (11 row loads per 4 candidates instead of 32).
 // Distances are the exact sum of squared differences in FP32 -- the direct
 // form, not the norm expansion of eq. (expand), which cancels badly in FP32 --
-// computed with Blackwell's packed FP32 pairs (sub/fma.rn.f32x2): the even
+// computed with Blackwell's packed FP32 pairs (add/fma.rn.f32x2 on the
+// negated reference): the even
 // and odd columns of a block row are two independent FP32 partial sums, each
 // rounded exactly as scalar FSUB/FFMA would be.
 //
@@ -25,14 +26,15 @@
 // Selection (K-1 best keys (distance, k*W+l)) follows the warp-select
 // pattern: lane t holds the t-th best of a sorted 32-entry list; candidates
 // that beat the current (K-1)-th key are handled per candidate row of the
-// batch: when at most kInsertMax lanes qualify (the common case once the list
-// has filled) they are inserted one at a time with a shuffle-based shift, the
-// threshold tightening after each; when more qualify (the first batches)
-// they are appended to a per-warp buffer (ballot + prefix count) and every
-// full 32 are bitonic-sorted across the warp and merged into the list.  The
-// batch's keys are staged in shared memory so that this selection loop is
-// not unrolled.  The scan starts at the reference's own rows so that the
-// threshold tightens early.  The reference block itself is excluded and written to
+// batch: all of a batch's keys are first tested against the threshold with
+// one ballot per candidate row; rows without a qualifying lane (most of them
+// once the list has filled) cost nothing more.  When at most kInsertMax lanes
+// of a row qualify they are inserted one at a time with a shuffle-based
+// shift, the threshold tightening after each; when more qualify (the first
+// batches) they are appended to a per-warp buffer (ballot + prefix count)
+// and every full 32 are bitonic-sorted across the warp and merged into the
+// list by an out-of-line function.  The scan starts at the reference's own
+// rows so that the threshold tightens early.  The reference block itself is excluded and written to
 // slot 0.
 #include <float.h>
 #include <limits.h>
@@ -62,11 +64,12 @@ __device__ __forceinline__ void unpack2(f2 v, float &lo, float &hi)
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-// acc += (r - x)^2, elementwise on both halves.
-__device__ __forceinline__ f2 sqdiff_acc2(f2 r, f2 x, f2 acc)
+// acc += (x + nr)^2 elementwise on both halves, with nr = -r the negated
+// reference pixels: x + (-r) is exactly x - r, and (x - r)^2 = (r - x)^2.
+__device__ __forceinline__ f2 sqdiff_acc2(f2 nr, f2 x, f2 acc)
 {
     f2 e, o;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(r), "l"(x));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(x), "l"(nr));
     asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(o) : "l"(e), "l"(acc));
     return o;
 }
@@ -114,6 +117,44 @@ __device__ __forceinline__ void merge32(float &ld, int &li, float bd, int bi, in
 
 // Three CTAs per SM (<= 85 registers): the extra warps hide the latency of
 // the FP chains better than the registers the compiler gives up cost.
+// The list, its threshold and the buffer fill, as passed to the out-of-line
+// merge (the rare path; keeping it out of the unrolled loop keeps the loop
+// body small).
+struct ListState {
+    float ld;
+    int li;
+    float thr_d;
+    int thr_i;
+    int cnt;
+};
+
+// Merges the first 32 buffered keys into the list, moves the rest of the
+// buffer to its front and refreshes the threshold.  Called by the whole warp.
+__device__ __noinline__ ListState merge_buffer(ListState s, float *wb_d, int *wb_i, int lane, int Kc)
+{
+    __syncwarp();
+    float bd = wb_d[lane];
+    int bi = wb_i[lane];
+    bitonic_sort32(bd, bi, lane);
+    merge32(s.ld, s.li, bd, bi, lane);
+    s.cnt -= 32;
+    float md = 0.f;
+    int mi = 0;
+    if (lane < s.cnt) {
+        md = wb_d[32 + lane];
+        mi = wb_i[32 + lane];
+    }
+    __syncwarp();
+    if (lane < s.cnt) {
+        wb_d[lane] = md;
+        wb_i[lane] = mi;
+    }
+    __syncwarp();
+    s.thr_d = __shfl_sync(kFull, s.ld, Kc - 1);
+    s.thr_i = __shfl_sync(kFull, s.li, Kc - 1);
+    return s;
+}
+
 template <int N>
 __global__ void __launch_bounds__(kRefsPerCta * 32, 3)
 k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, int R, int K, int col_pad,
@@ -147,16 +188,13 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
     const int j = grid_pos(q, s, W, N);
     float *wb_d = buf_d + warp * kBuf;
     int *wb_i = buf_i + warp * kBuf;
-    float *cs_d = reinterpret_cast<float *>(buf_i + kRefsPerCta * kBuf) + warp * 32 * kVB; // [c][lane]
-    int *cs_i = reinterpret_cast<int *>(reinterpret_cast<float *>(buf_i + kRefsPerCta * kBuf) +
-                                        kRefsPerCta * 32 * kVB) + warp * 32 * kVB;
 
-    f2 r[N][N / 2]; // reference block, column pairs (b, b+1) packed
+    f2 r[N][N / 2]; // negated reference block, column pairs (b, b+1) packed
 #pragma unroll
     for (int a = 0; a < N; a++)
 #pragma unroll
         for (int b = 0; b < N; b += 2)
-            r[a][b / 2] = pack2(sm[(i - ry0 + a) * rw + (j - rx0 + b)], sm[(i - ry0 + a) * rw + (j - rx0 + b + 1)]);
+            r[a][b / 2] = pack2(-sm[(i - ry0 + a) * rw + (j - rx0 + b)], -sm[(i - ry0 + a) * rw + (j - rx0 + b + 1)]);
 
     const int k0 = ry0, k1 = min(H - N, i + R);
     const int l0 = max(0, j - R), l1 = min(W - N, j + R);
@@ -213,7 +251,7 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
         // have no qualifying candidate and skip the selection loop
         float cdv[kVB];
         int cidv[kVB];
-        unsigned any = 0;
+        unsigned mk[kVB], any = 0;
 #pragma unroll
         for (int c = 0; c < kVB; c++) {
             const int kc = k + c;
@@ -222,24 +260,20 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
             unpack2(dd[c], d0, d1);
             cdv[c] = valid ? d0 + d1 : kInf;
             cidv[c] = valid ? kc * W + l : INT_MAX;
-            any |= __ballot_sync(kFull, key_less(cdv[c], cidv[c], thr_d, thr_i));
+            mk[c] = __ballot_sync(kFull, key_less(cdv[c], cidv[c], thr_d, thr_i));
+            any |= mk[c];
         }
         if (!any) continue;
-        // stage the keys so the selection loop below stays rolled (one copy of
-        // its code)
+        // only the candidate rows with a qualifying lane (warp-uniform tests)
 #pragma unroll
         for (int c = 0; c < kVB; c++) {
-            cs_d[c * 32 + lane] = cdv[c];
-            cs_i[c * 32 + lane] = cidv[c];
-        }
-#pragma unroll 1
-        for (int c = 0; c < kVB; c++) {
-            const float cd = cs_d[c * 32 + lane];
-            const int cid = cs_i[c * 32 + lane];
-            bool pend = key_less(cd, cid, thr_d, thr_i);
+            if (!mk[c]) continue;
+            const float cd = cdv[c];
+            const int cid = cidv[c];
+            bool pend = key_less(cd, cid, thr_d, thr_i); // the threshold may have tightened
             unsigned mask = __ballot_sync(kFull, pend);
             const int nq = __popc(mask);
-            if (nq > kInsertMax) { // many: buffer, merge each full 32 (sort + bitonic merge)
+            if (nq > kInsertMax) { // many: buffer them, merge each full 32
                 if (pend) {
                     const int pos = cnt + __popc(mask & lt_mask);
                     wb_d[pos] = cd;
@@ -247,26 +281,13 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
                 }
                 cnt += nq;
                 if (cnt >= 32) {
-                    __syncwarp();
-                    float bd = wb_d[lane];
-                    int bi = wb_i[lane];
-                    bitonic_sort32(bd, bi, lane);
-                    merge32(ld, li, bd, bi, lane);
-                    cnt -= 32;
-                    float md = 0.f;
-                    int mi = 0;
-                    if (lane < cnt) {
-                        md = wb_d[32 + lane];
-                        mi = wb_i[32 + lane];
-                    }
-                    __syncwarp();
-                    if (lane < cnt) {
-                        wb_d[lane] = md;
-                        wb_i[lane] = mi;
-                    }
-                    __syncwarp();
-                    thr_d = __shfl_sync(kFull, ld, Kc - 1);
-                    thr_i = __shfl_sync(kFull, li, Kc - 1);
+                    ListState st{ld, li, thr_d, thr_i, cnt};
+                    st = merge_buffer(st, wb_d, wb_i, lane, Kc);
+                    ld = st.ld;
+                    li = st.li;
+                    thr_d = st.thr_d;
+                    thr_i = st.thr_i;
+                    cnt = st.cnt;
                 }
             } else { // few: insert one at a time, tightening the threshold as we go
                 while (mask) {
@@ -346,8 +367,7 @@ MatchGeom match_geom(int s, int R)
 size_t match_smem_bytes(int s, int R)
 {
     const MatchGeom g = match_geom(s, R);
-    return (size_t)g.bufs_off * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int)) +
-           (size_t)kRefsPerCta * 32 * kVB * (sizeof(float) + sizeof(int));
+    return (size_t)g.bufs_off * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int));
 }
 
 cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
