@@ -70,6 +70,12 @@ typedef struct {
     float tau_b;        /* (0.3)                                              */
     float kaiser_beta;  /* stage-2 aggregation window, 0 = no window (2.0)    */
     float eps_w;        /* lower guard on TV and Wiener weight denominators   */
+    int match_engine;   /* block matching: 0 = tensor cores where supported,   */
+                        /* else direct; 1 = direct FP32 SSD; 2 = tensor cores */
+                        /* (EUNSUPPORTED where not).  Same results, bit for    */
+                        /* bit: the tensor-core engine ranks with the norm    */
+                        /* expansion of Theorem 1 and re-ranks its certified  */
+                        /* survivors with the exact direct sum.               */
 } gbm3d_params;
 
 /* Fill *p with a preset.  preset 0: N=8, s=3, R=19 (39x39 candidate offsets),
@@ -178,6 +184,18 @@ int gbm3d_aggregate_noalloc(const float *groups, const float *w, const int32_t *
  *   ws    : scratch, gbm3d_workspace_bytes. */
 int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, const gbm3d_params *p,
                   float *out, void *ws, gbm3d_stream_t stream);
+
+/* Counters of the tensor-core matcher on the current device, cumulative since
+ * the library was loaded:
+ *   timeouts  : bounded device-side waits that gave up (0 when healthy; the
+ *               tile is then re-matched by the direct engine, so results are
+ *               unaffected);
+ *   rematched : references whose candidate list could not be certified
+ *               (near-ties wider than the error margin, non-finite pixels,
+ *               a timeout) and were re-matched by the direct engine.
+ * Synchronous (waits for the device's pending work).  EINVAL if a pointer is
+ * NULL, ECUDA if the read fails. */
+int gbm3d_match_stats(unsigned long long *timeouts, unsigned long long *rematched);
 
 /* Description of the last failure on this host thread ("" if none). */
 const char *gbm3d_last_error_string(void);

@@ -46,6 +46,8 @@ static int check_params(const gbm3d_params *p)
     if (!(p->eps_w > 0.f) || !isfinite(p->eps_w)) return fail(GBM3D_EINVAL, "eps_w must be positive");
     if (!isfinite(p->tau_a) || !isfinite(p->tau_b) || !isfinite(p->kaiser_beta) || p->kaiser_beta < 0.f)
         return fail(GBM3D_EINVAL, "tau_a, tau_b, kaiser_beta must be finite (beta >= 0)");
+    if (p->match_engine < 0 || p->match_engine > 2)
+        return fail(GBM3D_EINVAL, "match_engine %d: 0 auto, 1 direct, 2 tensor cores", p->match_engine);
     if (match_smem_bytes(p->step, p->search_radius) > 227 * 1024)
         return fail(GBM3D_EUNSUPPORTED, "search region of R=%d, s=%d exceeds shared memory", p->search_radius,
                     p->step);
@@ -67,6 +69,24 @@ static int check_window(int H, int W, int R, int K)
     if (wy * wx < K)
         return fail(GBM3D_EINVAL, "search window holds %lld blocks, fewer than K = %d", wy * wx, K);
     return GBM3D_OK;
+}
+
+// The tensor-core engine where the parameters allow it (and it is not
+// switched off), else the direct one; engine 2 where unsupported is refused.
+static int check_engine(int H, int W, const gbm3d_params *p, int K)
+{
+    if (p->match_engine == 2 && !match_tc_supported(H, W, p->step, p->search_radius, K))
+        return fail(GBM3D_EUNSUPPORTED, "tensor-core matching needs 7 s + 2 R + 1 <= 64 and K <= 32 (s=%d R=%d K=%d)",
+                    p->step, p->search_radius, K);
+    return GBM3D_OK;
+}
+
+static cudaError_t match_any(const float *img, int H, int W, int pitch, int By, int Bx, const gbm3d_params *p, int K,
+                             int32_t *idx, float *dist, cudaStream_t st)
+{
+    if (p->match_engine != 1 && match_tc_supported(H, W, p->step, p->search_radius, K))
+        return launch_match_tc(img, H, W, pitch, By, Bx, p->step, p->search_radius, K, idx, dist, st);
+    return launch_match(img, H, W, pitch, By, Bx, p->step, p->search_radius, K, idx, dist, st);
 }
 
 // Kaiser window kappa[n] = I0(beta sqrt(1 - (2n/(N-1) - 1)^2)) / I0(beta), with
@@ -156,7 +176,7 @@ static int run_stage1(const float *z, int zp, int H, int W, float sigma, const g
 {
     const int K = p->k1;
     int32_t *idx = (int32_t *)(ws + S.idx);
-    cudaError_t e = launch_match(z, H, W, zp, S.By, S.Bx, p->step, p->search_radius, K, idx, nullptr, st);
+    cudaError_t e = match_any(z, H, W, zp, S.By, S.Bx, p, K, idx, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "match (stage 1)");
     e = build_csr(idx, S.G, K, H, W, ws + S.csr, true, st);
     if (e != cudaSuccess) return cuda_fail(e, "inverted lists (stage 1)");
@@ -176,7 +196,7 @@ static int run_stage2(const float *z, int zp, const float *y1, int yp, int H, in
 {
     const int K = p->k2;
     int32_t *idx = (int32_t *)(ws + S.idx);
-    cudaError_t e = launch_match(y1, H, W, yp, S.By, S.Bx, p->step, p->search_radius, K, idx, nullptr, st);
+    cudaError_t e = match_any(y1, H, W, yp, S.By, S.Bx, p, K, idx, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "match (stage 2)");
     e = build_csr(idx, S.G, K, H, W, ws + S.csr, true, st);
     if (e != cudaSuccess) return cuda_fail(e, "inverted lists (stage 2)");
@@ -220,7 +240,14 @@ extern "C" {
 
 const char *gbm3d_last_error_string(void) { return g_err; }
 
-const char *gbm3d_version(void) { return "gbm3d 0.1 (sm_103a)"; }
+const char *gbm3d_version(void) { return "gbm3d 0.2 (sm_103a)"; }
+
+int gbm3d_match_stats(unsigned long long *timeouts, unsigned long long *rematched)
+{
+    if (!timeouts || !rematched) return fail(GBM3D_EINVAL, "timeouts/rematched is NULL");
+    const cudaError_t e = tc_stats(timeouts, rematched);
+    return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "match_stats");
+}
 
 int gbm3d_params_default(gbm3d_params *p, int preset)
 {
@@ -234,6 +261,7 @@ int gbm3d_params_default(gbm3d_params *p, int preset)
     p->tau_b = 0.3f;
     p->kaiser_beta = 2.0f;
     p->eps_w = 1e-8f;
+    p->match_engine = 0;
     if (preset == 0) {
         p->step = 3;
         p->search_radius = 19;
@@ -282,9 +310,9 @@ int gbm3d_match(const float *img, int H, int W, int pitch, const gbm3d_params *p
     if (!img || !idx) return fail(GBM3D_EINVAL, "img/idx is NULL");
     if (K < 2 || K > kMaxK) return fail(GBM3D_EUNSUPPORTED, "K = %d: supported 2..32", K);
     if ((st = check_window(H, W, p->search_radius, K))) return st;
+    if ((st = check_engine(H, W, p, K))) return st;
     const int By = grid_count(H, kPatch, p->step), Bx = grid_count(W, kPatch, p->step);
-    cudaError_t e = launch_match(img, H, W, pitch, By, Bx, p->step, p->search_radius, K, idx, dist,
-                                 (cudaStream_t)stream);
+    cudaError_t e = match_any(img, H, W, pitch, By, Bx, p, K, idx, dist, (cudaStream_t)stream);
     return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "match");
 }
 
@@ -374,6 +402,8 @@ int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, cons
     if (!(sigma >= 0.f) || !isfinite(sigma)) return fail(GBM3D_EINVAL, "sigma must be finite and >= 0");
     if (!aligned(ws, kAlign)) return fail(GBM3D_EINVAL, "ws must be 256-byte aligned");
     if ((st = check_window(H, W, p->search_radius, p->k1 > p->k2 ? p->k1 : p->k2))) return st;
+    if ((st = check_engine(H, W, p, p->k1))) return st;
+    if (p->stages == 2 && (st = check_engine(H, W, p, p->k2))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const Sizes S = sizes(H, W, p);
     char *base = (char *)ws;

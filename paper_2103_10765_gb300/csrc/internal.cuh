@@ -112,6 +112,20 @@ cudaError_t fixed_scratch(void **ptr);
 cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                          int32_t *idx, float *dist, cudaStream_t st);
 
+// Tensor-core matching (same results as launch_match, bit for bit) where the
+// geometry fits (N = 8, union of 8 grid columns' windows <= 64 columns,
+// K <= 32); it ends with launch_match_fix, which re-matches with the direct
+// kernel the references it marked (slot 0 < 0).
+bool match_tc_supported(int H, int W, int s, int R, int K);
+cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+                            int32_t *idx, float *dist, cudaStream_t st);
+cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+                             int32_t *idx, float *dist, cudaStream_t st);
+// Cumulative counts of the tensor-core matcher on the current device: bounded
+// waits that gave up, references re-matched by the direct kernel
+// (synchronous read).
+cudaError_t tc_stats(unsigned long long *timeouts, unsigned long long *rematched);
+
 cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
                              float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, const GroupOut &out,
                              void *ht_ws, cudaStream_t st);

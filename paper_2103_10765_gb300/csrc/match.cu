@@ -155,14 +155,26 @@ __device__ __noinline__ ListState merge_buffer(ListState s, float *wb_d, int *wb
     return s;
 }
 
+// Arguments of one matching launch (the shared-memory geometry comes from
+// match_geom on the host).
+struct MatchArgs {
+    const float *img;
+    int H, W, pitch, Bx, s, R, K, col_pad, rw, copy_off, bufs_off;
+    int32_t *idx;
+    float *dist;
+};
+
+// Matches the references q0 .. q0+kRefsPerCta-1 of grid row p: one warp per
+// reference, the CTA's region in shared memory sm.  Every thread of the CTA
+// calls it (the region load ends in a __syncthreads).
 template <int N>
-__global__ void __launch_bounds__(kRefsPerCta * 32, 3)
-k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, int R, int K, int col_pad,
-        int rw, int copy_off, int bufs_off, int32_t *__restrict__ idx, float *__restrict__ dist)
+__device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, float *sm)
 {
-    extern __shared__ float sm[];
-    const int p = blockIdx.y;
-    const int q0 = blockIdx.x * kRefsPerCta;
+    const float *__restrict__ img = A.img;
+    const int H = A.H, W = A.W, pitch = A.pitch, Bx = A.Bx, s = A.s, R = A.R, K = A.K;
+    const int col_pad = A.col_pad, rw = A.rw, copy_off = A.copy_off, bufs_off = A.bufs_off;
+    int32_t *__restrict__ idx = A.idx;
+    float *__restrict__ dist = A.dist;
     const int i = grid_pos(p, s, H, N);
     const int qlast = min(q0 + kRefsPerCta - 1, Bx - 1);
     const int jf = grid_pos(q0, s, W, N), jl = grid_pos(qlast, s, W, N);
@@ -337,6 +349,49 @@ k_match(const float *__restrict__ img, int H, int W, int pitch, int Bx, int s, i
     }
 }
 
+template <int N>
+__global__ void __launch_bounds__(kRefsPerCta * 32, 3) k_match(MatchArgs a)
+{
+    extern __shared__ float sm[];
+    match_group<N>(a, blockIdx.y, blockIdx.x * kRefsPerCta, sm);
+}
+
+// Exact re-run of the CTAs (grid row p, references q0 .. q0+7) holding a
+// reference whose slot 0 is negative: the tensor-core matcher marks that way
+// the references whose candidate list it could not certify.  Each CTA scans a
+// strided subset of the groups, gathers the marked ones in shared memory and
+// matches them as k_match does (same results, bit for bit).
+template <int N>
+__global__ void __launch_bounds__(kRefsPerCta * 32, 3) k_match_fix(MatchArgs a, int By)
+{
+    extern __shared__ float sm[];
+    __shared__ int s_list[kRefsPerCta * 32];
+    __shared__ int s_n;
+    const int gx = (a.Bx + kRefsPerCta - 1) / kRefsPerCta;
+    const int ngroups = By * gx;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x; base < ngroups; base += stride) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        const int gid = base + threadIdx.x * gridDim.x;
+        if (gid < ngroups) {
+            const int p = gid / gx, q0 = (gid - p * gx) * kRefsPerCta;
+            bool marked = false;
+            for (int r = 0; r < kRefsPerCta && q0 + r < a.Bx; r++)
+                marked |= a.idx[((size_t)p * a.Bx + q0 + r) * a.K] < 0;
+            if (marked) s_list[atomicAdd(&s_n, 1)] = gid;
+        }
+        __syncthreads();
+        const int n = s_n;
+        for (int t = 0; t < n; t++) {
+            const int gid2 = s_list[t];
+            const int p = gid2 / gx;
+            match_group<N>(a, p, (gid2 - p * gx) * kRefsPerCta, sm);
+            __syncthreads();
+        }
+    }
+}
+
 struct MatchGeom {
     int col_pad, rw, rows;
     int copy_off, bufs_off; // floats: offset of the shifted copy, of the selection buffers
@@ -378,8 +433,27 @@ cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int 
     cudaError_t e = cudaFuncSetAttribute(k_match<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kRefsPerCta - 1) / kRefsPerCta, By);
-    k_match<kPatch><<<grid, kRefsPerCta * 32, smem, st>>>(img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, g.copy_off,
-                                                          g.bufs_off, idx, dist);
+    const MatchArgs a{img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, g.copy_off, g.bufs_off, idx, dist};
+    k_match<kPatch><<<grid, kRefsPerCta * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+                             int32_t *idx, float *dist, cudaStream_t st)
+{
+    const MatchGeom g = match_geom(s, R);
+    const size_t smem = match_smem_bytes(s, R);
+    cudaError_t e = cudaFuncSetAttribute(k_match_fix<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int ngroups = By * ((Bx + kRefsPerCta - 1) / kRefsPerCta);
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int blocks = 3 * nsm;
+    if (blocks > ngroups) blocks = ngroups;
+    if (blocks < 1) blocks = 1;
+    const MatchArgs a{img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, g.copy_off, g.bufs_off, idx, dist};
+    k_match_fix<kPatch><<<blocks, kRefsPerCta * 32, smem, st>>>(a, By);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,745 @@
+// match_tc.cu -- block matching on the 5th-generation tensor cores
+// (Theorem 1: d(a, b) = ||a||^2 + ||b||^2 - 2 a.b; Sec. 2 eq. dfg, Algorithm 1).
+//
+// The cross terms a.b of a tile of 128 references (16 grid rows x 8 grid
+// columns) against every candidate of the union of their search windows form
+// one dense product.  It runs as tcgen05.mma (kind::f16, FP32 accumulators in
+// tensor memory): M = 128 references, N = 128 candidates per chunk (two
+// candidate rows of 64 columns), K = 64 pixels.  The selection warps read the
+// accumulators back with tcgen05.ld, one reference per lane.
+//
+// Exactness.  The product only ranks; the returned list is the exact one of
+// the direct FP32 sum (match.cu), bit for bit:
+//  1. Pixels are centred on the tile mean and scaled by a power of two so the
+//     largest magnitude lies in [2^13, 2^14) (exact scaling), then split into
+//     two FP16 halves v = hi + lo; three products hi.hi + hi.lo + lo.hi give
+//     a.b to about 2^-21 relative.
+//  2. e~ = ||b||^2 - 2 a.b (the reference's own norm is a per-lane constant).
+//     Each lane keeps its L = K - 1 + margin (24 for K <= 16, 40 for
+//     K <= 32) smallest keys in registers; keys below its current L-th one
+//     wait in a small shared-memory queue and are merged eight at a time by
+//     a branch-free sorting network, so all 32 lanes do identical work.
+//  3. A rigorous bound delta on |e~ - e*| (e* = the exact-FP32 distance minus
+//     ||a||^2) certifies the list: if every key outside it is provably larger
+//     than the (K-1)-th key inside (lo(e~_L) > hi(e~_{K-1})), the true K-1
+//     best are inside.  Their exact FP32 distances (same operation order as
+//     match.cu) are then recomputed and sorted by (distance, k*W + l).
+//  4. A reference that fails the test (near-ties wider than the margin,
+//     non-finite input, a timed-out wait) is marked by slot 0 = -1 and
+//     re-matched by the direct kernel (k_match_fix).
+//
+// Work split: a CTA of 4 warps (two CTAs per SM); warp w owns tensor-memory
+// lanes 32w..32w+31, i.e. references 32w..32w+31.  Every thread also builds
+// one candidate row of the FP16 operand tiles (core-matrix layout, no
+// swizzle) and thread 0 issues the MMAs.  Two accumulator buffers of 128
+// columns alternate: the MMAs of chunk c+1 run while the warps select on
+// chunk c.  Chunks are visited nearest-first to each warp's references so
+// that thresholds tighten early.  Every mbarrier wait is bounded; on a
+// timeout the tile falls back to the direct kernel.  Device counters record
+// timeouts and re-matched references.
+#include <cuda_fp16.h>
+#include <float.h>
+#include <limits.h>
+
+#include "internal.cuh"
+
+namespace gbm3d {
+
+__device__ unsigned long long g_tc_timeouts = 0;  // bounded waits that gave up
+__device__ unsigned long long g_tc_rematched = 0; // references handed to the direct kernel
+
+namespace {
+
+constexpr int kTileY = 16, kTileX = 8, kM = kTileY * kTileX; // references per tile (MMA M)
+constexpr int kChunkRows = 2, kChunkCols = 64, kNc = kChunkRows * kChunkCols; // candidates per chunk (MMA N)
+constexpr int kKd = kPatch * kPatch;                       // contraction length
+constexpr int kRegStride = kChunkCols + kPatch;            // region row stride (floats)
+constexpr int kOp = kM * kKd * 2;                          // bytes of one FP16 operand tile (128 x 64)
+constexpr int kThreads = 128;                             // 4 warps: warp w owns tensor-memory lanes 32w..32w+31
+constexpr int kDBuf = 2;                                   // accumulator buffers
+constexpr uint32_t kTmemCols = 256;                        // power-of-two allocation >= kDBuf * kNc
+constexpr int kPend = 24, kFlushAt = 16;                   // per-lane pending keys (checked every 8 columns)
+constexpr int kSpin = 1 << 20;                             // bounded mbarrier polling
+constexpr unsigned kFull = 0xffffffffu;
+
+static_assert(kNc == kM, "operand tiles of A and B share one layout");
+static_assert(kDBuf * kNc <= (int)kTmemCols, "accumulators exceed the tensor-memory allocation");
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
+// A and B FP16 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kNc >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+
+// Byte offset of element row n, K-chunk a (8 FP16 = one block row) in an
+// operand tile: 8 x 16-byte core matrices, K-chunks 128 bytes apart (leading
+// byte offset), 8-row groups 1024 bytes apart (stride byte offset).
+__device__ __forceinline__ int op_off(int n, int a) { return (n >> 3) * 1024 + a * 128 + (n & 7) * 16; }
+
+// Shared-memory matrix descriptor for a K-major, non-swizzled tile starting
+// at shared address addr: start >> 4 (bits 0-13), leading byte offset 128
+// (bits 16-29), stride byte offset 1024 (bits 32-45), fixed 0b001 at 46-48,
+// base offset 0, swizzle none (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of parity `parity` to complete; gives up (returns
+// false, sets *err, counts the timeout) after kSpin polls, or at once when
+// *err is already set (err may be null: no early exit).
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *err)
+{
+    for (int it = 0; it < kSpin; it++) {
+        if (err && *err) return false;
+        if (mbar_test(a, parity)) return true;
+    }
+    if (err) *err = 1;
+    atomicAdd(&g_tc_timeouts, 1ull);
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                 "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes (lane t: row
+// 32 (warp % 4) + t), waited for inside the same statement so that no use of
+// the registers can be scheduled before the load completes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                   "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                   "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                   "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// 8 consecutive accumulator columns of this warp's 32 lanes (see tmem_ld32).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+typedef unsigned long long f2; // two packed FP32 values
+
+__device__ __forceinline__ f2 pack2(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// The direct kernel's step: acc += (x + nr)^2 on both halves (nr = -r).
+__device__ __forceinline__ f2 sqdiff_acc2(f2 nr, f2 x, f2 acc)
+{
+    f2 e, o;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(x), "l"(nr));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(o) : "l"(e), "l"(acc));
+    return o;
+}
+
+__device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+__device__ __forceinline__ unsigned range_mask(int lo, int hi)
+{
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > 31 ? 31 : hi;
+    if (lo > hi) return 0u;
+    return (kFull >> (31 - hi)) & (kFull << lo);
+}
+
+// Splits 8 scaled values into FP16 high and low halves (v = hi + lo + O(2^-22 v)).
+__device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const __half2 hh = __floats2half2_rn(v[2 * t], v[2 * t + 1]);
+        const float2 hf = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn(v[2 * t] - hf.x, v[2 * t + 1] - hf.y);
+        h[t] = *reinterpret_cast<const uint32_t *>(&hh);
+        l[t] = *reinterpret_cast<const uint32_t *>(&ll);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Compare-exchange: (a, ia) <= (b, ib) by key afterwards (ties: either order;
+// the certified re-rank decides ties exactly).
+__device__ __forceinline__ void cex(float &a, int &ia, float &b, int &ib)
+{
+    const bool sw = b < a;
+    const float ta = sw ? b : a, tb = sw ? a : b;
+    const int tia = sw ? ib : ia, tib = sw ? ia : ib;
+    a = ta;
+    b = tb;
+    ia = tia;
+    ib = tib;
+}
+
+// Batcher's odd-even merge sort of 8 keys (19 compare-exchanges).
+__device__ __forceinline__ void sort8(float (&k)[8], int (&v)[8])
+{
+#define CX(i, j) cex(k[i], v[i], k[j], v[j])
+    CX(0, 1); CX(2, 3); CX(4, 5); CX(6, 7);
+    CX(0, 2); CX(1, 3); CX(4, 6); CX(5, 7);
+    CX(1, 2); CX(5, 6);
+    CX(0, 4); CX(1, 5); CX(2, 6); CX(3, 7);
+    CX(2, 4); CX(3, 5);
+    CX(1, 2); CX(3, 4); CX(5, 6);
+#undef CX
+}
+
+// lk (ascending, LP keys) <- the LP smallest of lk and the 8 keys pk:
+// sort pk, take min(lk[LP-8+t], pk[7-t]) (a bitonic sequence holding the LP
+// smallest), then a bitonic merge.  Branch-free, identical work in every lane.
+template <int LP>
+__device__ __forceinline__ void merge8(float (&lk)[LP], int (&li)[LP], float (&pk)[8], int (&pi)[8])
+{
+    sort8(pk, pi);
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+        const bool sw = pk[7 - t] < lk[LP - 8 + t];
+        lk[LP - 8 + t] = sw ? pk[7 - t] : lk[LP - 8 + t];
+        li[LP - 8 + t] = sw ? pi[7 - t] : li[LP - 8 + t];
+    }
+#pragma unroll
+    for (int st = LP / 2; st > 0; st >>= 1)
+#pragma unroll
+        for (int i = 0; i < LP; i++)
+            if ((i & st) == 0) cex(lk[i], li[i], lk[i + st], li[i + st]);
+}
+
+} // namespace
+
+// Shared-memory layout of one tile (byte offsets from the 1024-aligned base).
+struct TcLayout {
+    int reg_rows, L;
+    int a_hi, a_lo, b_hi, b_lo, reg, nb, na2, pk, pi, misc, bytes;
+    int lk, li; // after the main loop the lists reuse the operand tiles
+};
+
+namespace {
+
+// LP: register list capacity (power of two); LT: keys kept per reference.
+template <int LP, int LT>
+__global__ void __launch_bounds__(kThreads, 2)
+k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+           TcLayout lay, int32_t *__restrict__ idx, float *__restrict__ dist)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int L = LT;
+    const int p0 = blockIdx.y * kTileY, q0 = blockIdx.x * kTileX;
+    const int nP = min(kTileY, By - p0), nQ = min(kTileX, Bx - q0);
+    const int iF = grid_pos(p0, s, H, kPatch), iL = grid_pos(p0 + nP - 1, s, H, kPatch);
+    const int jF = grid_pos(q0, s, W, kPatch), jL = grid_pos(q0 + nQ - 1, s, W, kPatch);
+    // union of the tile's search windows (candidate top-lefts)
+    const int uy0 = max(0, iF - R), uy1 = min(H - kPatch, iL + R);
+    const int ux0 = max(0, jF - R), ux1 = min(W - kPatch, jL + R);
+    const int UH = uy1 - uy0 + 1, UW = ux1 - ux0 + 1; // UW <= kChunkCols (host check)
+    const int nch = (UH + kChunkRows - 1) / kChunkRows;
+    const int rrows = nch * kChunkRows + kPatch - 1; // region rows read by the chunks (<= lay.reg_rows)
+
+    float *reg = reinterpret_cast<float *>(smem + lay.reg);
+    float *nbs = reinterpret_cast<float *>(smem + lay.nb);   // [2][kNc] candidate norms, by chunk parity
+    float *na2s = reinterpret_cast<float *>(smem + lay.na2); // [kM] reference norms
+    float *pk = reinterpret_cast<float *>(smem + lay.pk);    // [kPend][kM] pending keys
+    unsigned short *pi = reinterpret_cast<unsigned short *>(smem + lay.pi); // their candidate numbers
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + lay.misc);        // [2]
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + lay.misc + 32);
+    volatile int *s_err = reinterpret_cast<volatile int *>(smem + lay.misc + 36);
+    float *s_red = reinterpret_cast<float *>(smem + lay.misc + 64); // [4]
+    int *s_order = reinterpret_cast<int *>(smem + lay.misc + 128);  // chunk processing order
+    const uint32_t sbase = smem_u32(smem);
+
+    if (warp == 0) tmem_alloc(smem_u32(s_tmem), kTmemCols);
+    if (tid == 0) {
+        for (int b = 0; b < kDBuf; b++) mbar_init(smem_u32(&mbar[b]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_err = 0;
+    }
+
+    // ---- search region (raw pixels, zero outside the image) and its mean
+    const int vrows = UH + kPatch - 1, vcols = UW + kPatch - 1; // pixels of the union's blocks
+    float sum = 0.f;
+    for (int e = tid; e < rrows * kRegStride; e += kThreads) {
+        const int y = e / kRegStride, x = e - y * kRegStride;
+        const int gy = uy0 + y, gx = ux0 + x;
+        float v = 0.f;
+        if (gy < H && gx < W) v = __ldg(img + (size_t)gy * pitch + gx);
+        reg[e] = v;
+        if (y < vrows && x < vcols) sum += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    if (lane == 0) s_red[warp] = sum;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    float mu = 0.f;
+    for (int w = 0; w < kThreads / 32; w++) mu += s_red[w];
+    mu /= (float)(vrows * vcols);
+    float mx = 0.f;
+    for (int e = tid; e < vrows * vcols; e += kThreads) {
+        const int y = e / vcols, x = e - y * vcols;
+        mx = fmaxf(mx, fabsf(reg[y * kRegStride + x] - mu));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    __syncthreads(); // every thread has read the sums
+    if (lane == 0) s_red[warp] = mx;
+    __syncthreads();
+    float maxabs = 0.f;
+    for (int w = 0; w < kThreads / 32; w++) maxabs = fmaxf(maxabs, s_red[w]);
+    int ex = 0;
+    frexpf(maxabs, &ex);
+    // power-of-two scale: largest centred magnitude in [2^13, 2^14), inside FP16 range
+    const float sc = maxabs > 0.f ? ldexpf(1.f, 14 - ex) : 1.f;
+    const bool bad = !isfinite(mu) || !isfinite(maxabs) || ex > 100 || ex < -100 || !(fabsf(mu) * sc < 1e30f);
+    const float nms = -mu * sc; // fma(x, sc, nms) = (x - mu) sc, rounded once
+
+    // ---- this thread's reference (tensor-memory lane tid) and its window
+    const int m = tid;
+    const int rr = m >> 3, rc = m & 7;
+    const bool vref = rr < nP && rc < nQ;
+    const int ri = vref ? grid_pos(p0 + rr, s, H, kPatch) : 0;
+    const int rj = vref ? grid_pos(q0 + rc, s, W, kPatch) : 0;
+    const int iy = ri - uy0, ix = rj - ux0;
+
+    // ---- reference operand A (thread m builds reference m) and the chunk order
+    if (!bad) {
+        float n2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < kPatch; a++) {
+            float v[8];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                v[b] = vref ? fmaf(reg[(iy + a) * kRegStride + ix + b], sc, nms) : 0.f;
+                n2 = fmaf(v[b], v[b], n2);
+            }
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            *reinterpret_cast<uint4 *>(smem + lay.a_hi + op_off(m, a)) = hi;
+            *reinterpret_cast<uint4 *>(smem + lay.a_lo + op_off(m, a)) = lo;
+        }
+        na2s[m] = n2;
+    }
+    // chunk order: each chunk's rank is its distance (in chunks) to the
+    // nearest warp's own reference rows, so that every warp meets the
+    // candidates closest to its references first and its threshold tightens
+    // early (the result does not depend on the order)
+    if (tid < nch) {
+        int cw[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            const int r0 = min(4 * w, nP - 1), r1 = min(4 * w + 3, nP - 1);
+            const int mid = (grid_pos(p0 + r0, s, H, kPatch) + grid_pos(p0 + r1, s, H, kPatch)) / 2 - uy0;
+            cw[w] = min(nch - 1, max(0, mid / kChunkRows));
+        }
+        auto key = [&](int u) {
+            int k = INT_MAX;
+#pragma unroll
+            for (int w = 0; w < 4; w++) k = min(k, abs(u - cw[w]));
+            return k;
+        };
+        const int kt = key(tid);
+        int rank = 0;
+        for (int u = 0; u < nch; u++) {
+            const int ku = key(u);
+            rank += (ku < kt || (ku == kt && u < tid)) ? 1 : 0;
+        }
+        s_order[rank] = tid;
+    }
+    __syncthreads();
+
+    // builds candidate operand rows of chunk ch (thread n = candidate n) and
+    // their norms; returns the largest norm of a real candidate
+    float nbmax = 0.f;
+    auto build = [&](int ch, int par) {
+        const int n = tid;
+        const int rowl = ch * kChunkRows + (n >> 6), col = n & (kChunkCols - 1);
+        const float *src = reg + rowl * kRegStride + col;
+        float n2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < kPatch; a++) {
+            float v[8];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                v[b] = fmaf(src[a * kRegStride + b], sc, nms);
+                n2 = fmaf(v[b], v[b], n2);
+            }
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            *reinterpret_cast<uint4 *>(smem + lay.b_hi + op_off(n, a)) = hi;
+            *reinterpret_cast<uint4 *>(smem + lay.b_lo + op_off(n, a)) = lo;
+        }
+        nbs[par * kNc + n] = n2;
+        if (rowl < UH && col < UW) nbmax = fmaxf(nbmax, n2);
+    };
+    // issues the twelve MMAs of one chunk into accumulator buffer b (thread 0)
+    auto issue = [&](int b) {
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * kNc);
+        const uint32_t ah = sbase + lay.a_hi, al = sbase + lay.a_lo;
+        const uint32_t bh = sbase + lay.b_hi, bl = sbase + lay.b_lo;
+#pragma unroll
+        for (int t = 0; t < kKd / 16; t++) { // K = 16 FP16 per instruction = two K-chunks
+            mma_f16(d, smem_desc(ah + t * 256), smem_desc(bh + t * 256), t > 0 ? 1u : 0u);
+            mma_f16(d, smem_desc(ah + t * 256), smem_desc(bl + t * 256), 1u);
+            mma_f16(d, smem_desc(al + t * 256), smem_desc(bh + t * 256), 1u);
+        }
+        mma_commit(smem_u32(&mbar[b]));
+    };
+
+    // ---- selection state: this lane's window in union coordinates
+    int ky_lo = 1, ky_hi = 0;
+    unsigned colm0 = 0, colm1 = 0;
+    if (vref) {
+        ky_lo = max(0, ri - R) - uy0;
+        ky_hi = min(H - kPatch, ri + R) - uy0;
+        const int kx_lo = max(0, rj - R) - ux0, kx_hi = min(W - kPatch, rj + R) - ux0;
+        colm0 = range_mask(kx_lo, kx_hi);
+        colm1 = range_mask(kx_lo - 32, kx_hi - 32);
+    }
+    const unsigned self0 = (ix >= 0 && ix < 32) ? ~(1u << ix) : kFull;
+    const unsigned self1 = (ix >= 32 && ix < 64) ? ~(1u << (ix - 32)) : kFull;
+    int wlo = vref ? ky_lo : INT_MAX, whi = vref ? ky_hi : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wlo = min(wlo, __shfl_xor_sync(kFull, wlo, o));
+        whi = max(whi, __shfl_xor_sync(kFull, whi, o));
+    }
+    const int wc_lo = whi >= 0 ? wlo / kChunkRows : 1, wc_hi = whi >= 0 ? whi / kChunkRows : 0;
+    const float kInf = __int_as_float(0x7f800000);
+    // this lane's LP best keys so far, ascending, in registers (static indices only)
+    float lkr[LP];
+    int lir[LP];
+#pragma unroll
+    for (int t = 0; t < LP; t++) {
+        lkr[t] = kInf;
+        lir[t] = 0;
+    }
+    float thr = kInf; // the LT-th best key: larger ones can never be kept
+    int np = 0;       // pending keys of this lane (shared memory)
+
+    // merges every lane's pending keys into its list, eight at a time
+    auto flush = [&]() {
+        while (__any_sync(kFull, np > 0)) {
+            float pkr[8];
+            int pir[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const bool h = t < np;
+                pkr[t] = h ? pk[t * kM + m] : kInf;
+                pir[t] = h ? (int)pi[t * kM + m] : 0;
+            }
+#pragma unroll
+            for (int t = 8; t < kPend; t++)
+                if (t < np) {
+                    pk[(t - 8) * kM + m] = pk[t * kM + m];
+                    pi[(t - 8) * kM + m] = pi[t * kM + m];
+                }
+            np = np > 8 ? np - 8 : 0;
+            merge8<LP>(lkr, lir, pkr, pir);
+            thr = lkr[LT - 1];
+        }
+    };
+
+    // ---- pipeline: MMA(c + 1) runs while the warps select on chunk c
+    int last_issued = -1; // thread 0 only
+    if (!bad) {
+        build(s_order[0], 0);
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            issue(0);
+            last_issued = 0;
+        }
+    }
+    for (int c = 0; c < (bad ? 0 : nch); c++) {
+        const int b = c & 1;
+        const bool ok = __all_sync(kFull, mbar_wait(smem_u32(&mbar[b]), (c >> 1) & 1, s_err));
+        tc_fence_after();
+        // the product of chunk c is done: its operand tile is free for chunk c + 1
+        if (c + 1 < nch && !*s_err) build(s_order[c + 1], (c + 1) % 3);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0 && c + 1 < nch && !*s_err) {
+            issue((c + 1) & 1);
+            last_issued = c + 1;
+        }
+        // select on chunk c: 8 columns per step; the final step of the last
+        // chunk only merges what is still pending (one copy of the merge code)
+        const int ch = s_order[c];
+        const int nsteps = (ok && ch >= wc_lo && ch <= wc_hi) ? kNc / 8 : 0;
+        const int nst = nsteps + (c == nch - 1 ? 1 : 0);
+        const uint32_t tcol = tmem + (uint32_t)(b * kNc) + ((uint32_t)(warp * 32) << 16);
+        const float *nbc = nbs + (c % 3) * kNc;
+#pragma unroll 1
+        for (int st = 0; st < nst; st++) {
+            if (st < nsteps) {
+                const int g = st >> 2, j8 = (st & 3) * 8;
+                const int rowl = ch * kChunkRows + (g >> 1);
+                const int h = g & 1;
+                unsigned msk = 0u;
+                if (rowl >= ky_lo && rowl <= ky_hi) {
+                    msk = h ? colm1 : colm0;
+                    if (rowl == iy) msk &= h ? self1 : self0;
+                }
+                msk >>= j8;
+                uint32_t v[8];
+                tmem_ld8(tcol + (uint32_t)(st * 8), v);
+                const float4 nA = *reinterpret_cast<const float4 *>(nbc + st * 8);
+                const float4 nB = *reinterpret_cast<const float4 *>(nbc + st * 8 + 4);
+                const float nbv[8] = {nA.x, nA.y, nA.z, nA.w, nB.x, nB.y, nB.z, nB.w};
+                const int cbase = rowl * kChunkCols + h * 32 + j8;
+#pragma unroll
+                for (int jj = 0; jj < 8; jj++) {
+                    const float e = fmaf(-2.f, __uint_as_float(v[jj]), nbv[jj]);
+                    if (((msk >> jj) & 1u) && e < thr) {
+                        pk[np * kM + m] = e;
+                        pi[np * kM + m] = (unsigned short)(cbase + jj);
+                        np++;
+                    }
+                }
+            }
+            if (__any_sync(kFull, np >= kFlushAt || (st == nsteps && np > 0))) flush();
+        }
+        tc_fence_before();
+    }
+
+    // ---- largest candidate norm of the tile; the lists move to shared memory
+    // (over the operand tiles, whose last product has completed)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nbmax = fmaxf(nbmax, __shfl_xor_sync(kFull, nbmax, o));
+    if (lane == 0) s_red[warp] = nbmax;
+    // after a timeout the last product may still be running: let it finish
+    // before its operand tiles are overwritten and its accumulators released
+    if (tid == 0 && *s_err && last_issued >= 0)
+        mbar_wait(smem_u32(&mbar[last_issued & 1]), (last_issued >> 1) & 1, nullptr);
+    fence_async_smem();
+    __syncthreads();
+    const bool err = *s_err != 0;
+    float *lk = reinterpret_cast<float *>(smem + lay.lk); // [LT][kM] keys, then exact distances
+    int *li = reinterpret_cast<int *>(smem + lay.li);
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < LT; t++) {
+        lk[t * kM + m] = lkr[t];
+        li[t * kM + m] = lir[t];
+        cnt += lkr[t] < kInf ? 1 : 0;
+    }
+
+    if (vref) {
+        const size_t gq = ((size_t)(p0 + rr) * Bx + q0 + rc) * K;
+        bool ovf = bad || err;
+        if (!ovf && cnt == L) {
+            // certify: every key left out is provably above the (K-1)-th kept one
+            const float nbm = fmaxf(fmaxf(s_red[0], s_red[1]), fmaxf(s_red[2], s_red[3]));
+            const float na2 = na2s[m];
+            const float na = sqrtf(na2), nb = sqrtf(nbm);
+            const float d0 = 1e-4f * na * nb + 4e-6f * nbm + 1e-6f * (na + nb) + 1e-30f;
+            const float T = lk[(K - 2) * kM + m], X = lk[(L - 1) * kM + m];
+            const float hiT = T + 3e-6f * (fabsf(T) + na2) + d0;
+            const float loX = X - 3e-6f * (fabsf(X) + na2) - d0;
+            ovf = !(loX > hiT);
+        }
+        if (ovf) {
+            idx[gq] = -1; // re-matched by the direct kernel
+            atomicAdd(&g_tc_rematched, 1ull);
+        } else {
+            // exact FP32 distances, in the direct kernel's operation order
+            f2 nr[kPatch][kPatch / 2];
+#pragma unroll
+            for (int a = 0; a < kPatch; a++)
+#pragma unroll
+                for (int b = 0; b < kPatch / 2; b++)
+                    nr[a][b] = pack2(-reg[(iy + a) * kRegStride + ix + 2 * b], -reg[(iy + a) * kRegStride + ix + 2 * b + 1]);
+            for (int q = 0; q < cnt; q++) {
+                const int ci = li[q * kM + m];
+                const int ky = ci >> 6, kx = ci & (kChunkCols - 1);
+                const float *xr = reg + ky * kRegStride + kx;
+                f2 acc = 0ull;
+#pragma unroll
+                for (int a = 0; a < kPatch; a++)
+#pragma unroll
+                    for (int b = 0; b < kPatch / 2; b++)
+                        acc = sqdiff_acc2(nr[a][b], pack2(xr[a * kRegStride + 2 * b], xr[a * kRegStride + 2 * b + 1]), acc);
+                float e0, e1;
+                unpack2(acc, e0, e1);
+                lk[q * kM + m] = e0 + e1;
+                li[q * kM + m] = (uy0 + ky) * W + ux0 + kx;
+            }
+            // sort by (distance, position); the keys were already nearly in order
+            for (int a = 1; a < cnt; a++) {
+                const float dv = lk[a * kM + m];
+                const int iv = li[a * kM + m];
+                int b = a;
+                while (b > 0) {
+                    const float pd = lk[(b - 1) * kM + m];
+                    const int pv = li[(b - 1) * kM + m];
+                    if (!key_less(dv, iv, pd, pv)) break;
+                    lk[b * kM + m] = pd;
+                    li[b * kM + m] = pv;
+                    b--;
+                }
+                lk[b * kM + m] = dv;
+                li[b * kM + m] = iv;
+            }
+            idx[gq] = ri * W + rj;
+            if (dist) dist[gq] = 0.f;
+            for (int t = 0; t < K - 1; t++) {
+                const bool have = t < cnt;
+                idx[gq + 1 + t] = have ? li[t * kM + m] : INT_MAX;
+                if (dist) dist[gq + 1 + t] = have ? lk[t * kM + m] : kInf;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+} // namespace
+
+TcLayout tc_layout(int H, int s, int R, int K)
+{
+    TcLayout t{};
+    int uh = (kTileY - 1) * s + 2 * R + 1;
+    if (uh > H - kPatch + 1) uh = H - kPatch + 1;
+    if (uh < 1) uh = 1;
+    t.reg_rows = (uh + kChunkRows - 1) / kChunkRows * kChunkRows + kPatch - 1;
+    t.L = K <= 16 ? 24 : 40; // kept keys: K - 1 plus a margin of at least 8
+    int o = 0;
+    t.a_hi = o;
+    o += kOp;
+    t.a_lo = o;
+    o += kOp;
+    t.b_hi = o;
+    o += kOp;
+    t.b_lo = o;
+    o += kOp;
+    t.reg = o;
+    o += t.reg_rows * kRegStride * 4;
+    o = (o + 15) / 16 * 16;
+    t.nb = o;
+    o += 3 * kNc * 4;
+    t.na2 = o;
+    o += kM * 4;
+    t.pk = o;
+    o += kPend * kM * 4;
+    t.pi = o;
+    o += kPend * kM * 2;
+    o = (o + 15) / 16 * 16;
+    t.misc = o; // mbarriers, tensor-memory address, flags, reductions, chunk order
+    o += 128 + 4 * 128;
+    t.bytes = o;
+    t.lk = t.a_hi; // after the loop: lists over the operand tiles
+    t.li = t.lk + t.L * kM * 4;
+    return t;
+}
+
+bool match_tc_supported(int H, int W, int s, int R, int K)
+{
+    (void)W;
+    if (K < 2 || K > kMaxK) return false;
+    if ((kTileX - 1) * s + 2 * R + 1 > kChunkCols) return false; // union width must fit one chunk row
+    const TcLayout t = tc_layout(H, s, R, K);
+    if ((t.reg_rows - kPatch + 1) / kChunkRows > 128) return false; // chunk order table
+    return t.bytes <= 227 * 1024;
+}
+
+cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+                            int32_t *idx, float *dist, cudaStream_t st)
+{
+    const TcLayout lay = tc_layout(H, s, R, K);
+    // the operand tiles and pending keys alone take over a third of the SM's
+    // shared memory: at most two CTAs per SM, 2 x 256 tensor-memory columns
+    auto kern = lay.L == 24 ? k_match_tc<32, 24> : k_match_tc<64, 40>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.bytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((Bx + kTileX - 1) / kTileX, (By + kTileY - 1) / kTileY);
+    kern<<<grid, kThreads, lay.bytes, st>>>(img, H, W, pitch, By, Bx, s, R, K, lay, idx, dist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_match_fix(img, H, W, pitch, By, Bx, s, R, K, idx, dist, st);
+}
+
+cudaError_t tc_stats(unsigned long long *timeouts, unsigned long long *rematched)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(timeouts, g_tc_timeouts, sizeof *timeouts);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyFromSymbol(rematched, g_tc_rematched, sizeof *rematched);
+}
+
+} // namespace gbm3d

@@ -28,7 +28,8 @@ class Params(ctypes.Structure):
     """Mirror of gbm3d_params."""
     _fields_ = [(n, ctypes.c_int) for n in
                 ("patch", "step", "search_radius", "k1", "k2", "levels", "cycle_spins", "translations", "stages")] + \
-               [(n, ctypes.c_float) for n in ("tau_a", "tau_b", "kaiser_beta", "eps_w")]
+               [(n, ctypes.c_float) for n in ("tau_a", "tau_b", "kaiser_beta", "eps_w")] + \
+               [("match_engine", ctypes.c_int)]
 
     def replace(self, **kw) -> "Params":
         q = Params()
@@ -66,11 +67,12 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_aggregate.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp, vp]
     lib.gbm3d_denoise.argtypes = [vp, ci, ci, ci, cf, P, vp, vp, vp]
     lib.gbm3d_aggregate_noalloc.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp]
+    lib.gbm3d_match_stats.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.gbm3d_last_error_string.restype = ctypes.c_char_p
     lib.gbm3d_version.restype = ctypes.c_char_p
     for name in ("gbm3d_params_default", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
                  "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise",
-                 "gbm3d_aggregate_noalloc"):
+                 "gbm3d_aggregate_noalloc", "gbm3d_match_stats"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -130,6 +132,13 @@ def match(img: torch.Tensor, K: int, p: Params | None = None, with_dist: bool = 
     _check(load().gbm3d_match(_ptr(img), H, W, pitch, ctypes.byref(p), K, _ptr(idx), _ptr(dist), None,
                               _stream(img)))
     return idx, dist
+
+
+def match_stats():
+    """(timeouts, rematched) counters of the tensor-core matcher on the current device."""
+    t, r = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    _check(load().gbm3d_match_stats(ctypes.byref(t), ctypes.byref(r)))
+    return t.value, r.value
 
 
 def filter_ht(noisy: torch.Tensor, idx: torch.Tensor, sigma: float, p: Params | None = None,

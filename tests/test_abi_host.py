@@ -41,6 +41,7 @@ def test_presets(g):
     assert (p.patch, p.step, p.search_radius, p.k1, p.k2, p.levels, p.cycle_spins, p.translations, p.stages) == \
         (8, 3, 19, 16, 32, 3, 2, 1, 2)
     assert abs(p.tau_a - 3.6) < 1e-6 and abs(p.tau_b - 0.3) < 1e-6 and p.kaiser_beta == 2.0
+    assert p.match_engine == 0
     q = g.params_default(1)
     assert (q.step, q.search_radius, q.k1, q.translations) == (8, 16, 16, 2)
     with pytest.raises(g.Gbm3dError):
@@ -94,6 +95,14 @@ def test_validation_errors(g):
         st = lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None)
         assert st in (g.EINVAL, g.EUNSUPPORTED), bad
     assert b"" != lib.gbm3d_last_error_string()
+    # matching engine: out of range; tensor cores where the window union is too wide
+    q = p.replace(match_engine=3)
+    assert lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None) == g.EINVAL
+    q = p.replace(match_engine=2, search_radius=30)
+    assert lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None) == g.EUNSUPPORTED
+    assert lib.gbm3d_denoise(fake, 64, 64, 64, ctypes.c_float(0.1), ctypes.byref(q), ctypes.c_void_p(0x2000),
+                             ctypes.c_void_p(0x4000), None) == g.EUNSUPPORTED
+    assert lib.gbm3d_match_stats(None, None) == g.EINVAL
     # misaligned workspace
     assert lib.gbm3d_filter_ht(fake, 64, 64, 64, fake, ctypes.c_float(0.1), P, ctypes.c_void_p(0x3000), fake,
                                ctypes.c_void_p(0x1004), None) == g.EINVAL
