@@ -197,6 +197,15 @@ int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, cons
  * NULL, ECUDA if the read fails. */
 int gbm3d_match_stats(unsigned long long *timeouts, unsigned long long *rematched);
 
+/* Measurement hook.  events: NULL (off, the default) or an array of four
+ * cudaEvent_t created by the caller on the current device.  While set, each
+ * gbm3d_denoise on this host thread records events[0] / events[1] on its
+ * stream just before / after the stage-1 block-matching launch and events[2]
+ * / events[3] around the stage-2 one (with translations > 1: the last
+ * translation's), so cudaEventElapsedTime gives the matching time inside a
+ * real denoise.  The array must stay valid while set.  Always GBM3D_OK. */
+int gbm3d_set_match_events(void *events);
+
 /* Description of the last failure on this host thread ("" if none). */
 const char *gbm3d_last_error_string(void);
 

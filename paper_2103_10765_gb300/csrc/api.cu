@@ -11,6 +11,9 @@
 namespace gbm3d {
 
 static thread_local char g_err[512] = "";
+// Measurement hook (gbm3d_set_match_events): events recorded around the
+// matching launch of each stage, or null.
+static thread_local cudaEvent_t *g_match_events = nullptr;
 
 static int fail(int code, const char *fmt, ...)
 {
@@ -176,8 +179,10 @@ static int run_stage1(const float *z, int zp, int H, int W, float sigma, const g
 {
     const int K = p->k1;
     int32_t *idx = (int32_t *)(ws + S.idx);
+    if (g_match_events) cudaEventRecord(g_match_events[0], st);
     cudaError_t e = match_any(z, H, W, zp, S.By, S.Bx, p, K, idx, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "match (stage 1)");
+    if (g_match_events) cudaEventRecord(g_match_events[1], st);
     e = build_csr(idx, S.G, K, H, W, ws + S.csr, true, st);
     if (e != cudaSuccess) return cuda_fail(e, "inverted lists (stage 1)");
     const GroupOut go = planar_out(S, ws, H, W, K);
@@ -196,8 +201,10 @@ static int run_stage2(const float *z, int zp, const float *y1, int yp, int H, in
 {
     const int K = p->k2;
     int32_t *idx = (int32_t *)(ws + S.idx);
+    if (g_match_events) cudaEventRecord(g_match_events[2], st);
     cudaError_t e = match_any(y1, H, W, yp, S.By, S.Bx, p, K, idx, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "match (stage 2)");
+    if (g_match_events) cudaEventRecord(g_match_events[3], st);
     e = build_csr(idx, S.G, K, H, W, ws + S.csr, true, st);
     if (e != cudaSuccess) return cuda_fail(e, "inverted lists (stage 2)");
     const GroupOut go = planar_out(S, ws, H, W, K);
@@ -241,6 +248,12 @@ extern "C" {
 const char *gbm3d_last_error_string(void) { return g_err; }
 
 const char *gbm3d_version(void) { return "gbm3d 0.2 (sm_103a)"; }
+
+int gbm3d_set_match_events(void *events)
+{
+    g_match_events = (cudaEvent_t *)events;
+    return GBM3D_OK;
+}
 
 int gbm3d_match_stats(unsigned long long *timeouts, unsigned long long *rematched)
 {

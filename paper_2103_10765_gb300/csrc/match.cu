@@ -164,10 +164,12 @@ struct MatchArgs {
     float *dist;
 };
 
-// Matches the references q0 .. q0+kRefsPerCta-1 of grid row p: one warp per
-// reference, the CTA's region in shared memory sm.  Every thread of the CTA
-// calls it (the region load ends in a __syncthreads).
-template <int N>
+// Matches the references q0 .. q0+kRefs-1 of grid row p: one warp per
+// reference, their common search region in shared memory sm.  kRefs ==
+// kRefsPerCta: every thread of the CTA calls it (the region load ends in a
+// __syncthreads); kRefs == 1: one warp calls it for one reference, with its
+// own region (the load ends in a __syncwarp).
+template <int N, int kRefs>
 __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, float *sm)
 {
     const float *__restrict__ img = A.img;
@@ -176,7 +178,7 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
     int32_t *__restrict__ idx = A.idx;
     float *__restrict__ dist = A.dist;
     const int i = grid_pos(p, s, H, N);
-    const int qlast = min(q0 + kRefsPerCta - 1, Bx - 1);
+    const int qlast = min(q0 + kRefs - 1, Bx - 1);
     const int jf = grid_pos(q0, s, W, N), jl = grid_pos(qlast, s, W, N);
     const int ry0 = max(0, i - R), ry1 = min(H - N, i + R) + N;
     const int rx0 = max(0, jf - R), rx1 = min(W - N, jl + R) + N;
@@ -184,17 +186,21 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
     const int rhp = rh + kVB; // zero rows below absorb the last vertical block
     float *smB = sm + copy_off; // the region again, one float later: smB[e] = sm[e - 1]
     float *buf_d = sm + bufs_off;
-    int *buf_i = reinterpret_cast<int *>(buf_d + kRefsPerCta * kBuf);
-    for (int e = threadIdx.x; e < rhp * rw; e += blockDim.x) {
+    int *buf_i = reinterpret_cast<int *>(buf_d + kRefs * kBuf);
+    const int t0 = kRefs == 1 ? (threadIdx.x & 31) : threadIdx.x, nt = kRefs == 1 ? 32 : blockDim.x;
+    for (int e = t0; e < rhp * rw; e += nt) {
         const int y = e / rw, x = e - y * rw;
         const float v = (y < rh && x < rwd) ? __ldg(img + (size_t)(ry0 + y) * pitch + rx0 + x) : 0.f;
         sm[e] = v;
         smB[e + 1] = v;
     }
-    if (threadIdx.x == 0) smB[0] = 0.f;
-    __syncthreads();
+    if (t0 == 0) smB[0] = 0.f;
+    if (kRefs == 1)
+        __syncwarp();
+    else
+        __syncthreads();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = kRefs == 1 ? 0 : threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = q0 + warp;
     if (q >= Bx) return;
     const int j = grid_pos(q, s, W, N);
@@ -353,41 +359,32 @@ template <int N>
 __global__ void __launch_bounds__(kRefsPerCta * 32, 3) k_match(MatchArgs a)
 {
     extern __shared__ float sm[];
-    match_group<N>(a, blockIdx.y, blockIdx.x * kRefsPerCta, sm);
+    match_group<N, kRefsPerCta>(a, blockIdx.y, blockIdx.x * kRefsPerCta, sm);
 }
 
-// Exact re-run of the CTAs (grid row p, references q0 .. q0+7) holding a
-// reference whose slot 0 is negative: the tensor-core matcher marks that way
-// the references whose candidate list it could not certify.  Each CTA scans a
-// strided subset of the groups, gathers the marked ones in shared memory and
-// matches them as k_match does (same results, bit for bit).
+// Exact re-run of the references whose slot 0 is negative: the tensor-core
+// matcher marks that way the references whose candidate list it could not
+// certify.  One warp per CTA; warp w of nw takes the references g = w,
+// w + nw, w + 2 nw, ... (so that marked references, which cluster in smooth
+// image regions, spread over all warps), tests 32 of them per load and
+// matches each marked one exactly as k_match does, in its own region.
 template <int N>
-__global__ void __launch_bounds__(kRefsPerCta * 32, 3) k_match_fix(MatchArgs a, int By)
+__global__ void __launch_bounds__(32) k_match_fix(MatchArgs a, int G)
 {
     extern __shared__ float sm[];
-    __shared__ int s_list[kRefsPerCta * 32];
-    __shared__ int s_n;
-    const int gx = (a.Bx + kRefsPerCta - 1) / kRefsPerCta;
-    const int ngroups = By * gx;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x; base < ngroups; base += stride) {
-        if (threadIdx.x == 0) s_n = 0;
-        __syncthreads();
-        const int gid = base + threadIdx.x * gridDim.x;
-        if (gid < ngroups) {
-            const int p = gid / gx, q0 = (gid - p * gx) * kRefsPerCta;
-            bool marked = false;
-            for (int r = 0; r < kRefsPerCta && q0 + r < a.Bx; r++)
-                marked |= a.idx[((size_t)p * a.Bx + q0 + r) * a.K] < 0;
-            if (marked) s_list[atomicAdd(&s_n, 1)] = gid;
-        }
-        __syncthreads();
-        const int n = s_n;
-        for (int t = 0; t < n; t++) {
-            const int gid2 = s_list[t];
-            const int p = gid2 / gx;
-            match_group<N>(a, p, (gid2 - p * gx) * kRefsPerCta, sm);
-            __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x, w = blockIdx.x;
+    for (int b0 = 0; (long long)b0 * nw < G; b0 += 32) {
+        const long long g = w + (long long)(b0 + lane) * nw;
+        const bool marked = g < G && a.idx[g * a.K] < 0;
+        unsigned mk = __ballot_sync(0xffffffffu, marked);
+        while (mk) {
+            const int t = __ffs(mk) - 1;
+            mk &= mk - 1;
+            const int gg = (int)(w + (long long)(b0 + t) * nw);
+            const int p = gg / a.Bx;
+            match_group<N, 1>(a, p, gg - p * a.Bx, sm);
+            __syncwarp();
         }
     }
 }
@@ -397,14 +394,14 @@ struct MatchGeom {
     int copy_off, bufs_off; // floats: offset of the shifted copy, of the selection buffers
 };
 
-MatchGeom match_geom(int s, int R)
+MatchGeom match_geom(int s, int R, int nrefs = kRefsPerCta)
 {
     MatchGeom g;
     g.col_pad = (2 * R + 1 + 7) / 8 * 8;
-    // widest row a lane can touch: (l0 - rx0) <= (kRefsPerCta-1) s, plus the
+    // widest row a lane can touch: (l0 - rx0) <= (nrefs-1) s, plus the
     // padded column count, plus the block width
-    int need = (kRefsPerCta - 1) * s + g.col_pad + kPatch;
-    const int data = (kRefsPerCta - 1) * s + 2 * R + kPatch;
+    int need = (nrefs - 1) * s + g.col_pad + kPatch;
+    const int data = (nrefs - 1) * s + 2 * R + kPatch;
     if (data > need) need = data;
     g.rw = need; // kVB * rw == col_pad (mod 32)
     while ((kVB * g.rw - g.col_pad) % 32 != 0) g.rw++;
@@ -441,19 +438,19 @@ cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int 
 cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                              int32_t *idx, float *dist, cudaStream_t st)
 {
-    const MatchGeom g = match_geom(s, R);
-    const size_t smem = match_smem_bytes(s, R);
+    const MatchGeom g = match_geom(s, R, 1);
+    const size_t smem = (size_t)g.bufs_off * sizeof(float) + (size_t)kBuf * (sizeof(float) + sizeof(int));
     cudaError_t e = cudaFuncSetAttribute(k_match_fix<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int ngroups = By * ((Bx + kRefsPerCta - 1) / kRefsPerCta);
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    int blocks = 3 * nsm;
-    if (blocks > ngroups) blocks = ngroups;
+    const int G = By * Bx;
+    int blocks = 8 * nsm;
+    if (blocks > G) blocks = G;
     if (blocks < 1) blocks = 1;
     const MatchArgs a{img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, g.copy_off, g.bufs_off, idx, dist};
-    k_match_fix<kPatch><<<blocks, kRefsPerCta * 32, smem, st>>>(a, By);
+    k_match_fix<kPatch><<<blocks, 32, smem, st>>>(a, G);
     return cudaGetLastError();
 }
 

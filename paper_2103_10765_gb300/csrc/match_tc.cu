@@ -15,10 +15,10 @@
 //     two FP16 halves v = hi + lo; three products hi.hi + hi.lo + lo.hi give
 //     a.b to about 2^-21 relative.
 //  2. e~ = ||b||^2 - 2 a.b (the reference's own norm is a per-lane constant).
-//     Each lane keeps its L = K - 1 + margin (24 for K <= 16, 40 for
+//     Each lane keeps its L = K - 1 + margin (20 for K <= 16, 36 for
 //     K <= 32) smallest keys in registers; keys below its current L-th one
-//     wait in a small shared-memory queue and are merged eight at a time by
-//     a branch-free sorting network, so all 32 lanes do identical work.
+//     wait in a small shared-memory queue and are merged sixteen at a time
+//     by branch-free sorting networks, so all 32 lanes do identical work.
 //  3. A rigorous bound delta on |e~ - e*| (e* = the exact-FP32 distance minus
 //     ||a||^2) certifies the list: if every key outside it is provably larger
 //     than the (K-1)-th key inside (lo(e~_L) > hi(e~_{K-1})), the true K-1
@@ -191,6 +191,20 @@ __device__ __forceinline__ void unpack2(f2 v, float &lo, float &hi)
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // The direct kernel's step: acc += (x + nr)^2 on both halves (nr = -r).
 __device__ __forceinline__ f2 sqdiff_acc2(f2 nr, f2 x, f2 acc)
 {
@@ -242,31 +256,42 @@ __device__ __forceinline__ void cex(float &a, int &ia, float &b, int &ib)
     ib = tib;
 }
 
-// Batcher's odd-even merge sort of 8 keys (19 compare-exchanges).
-__device__ __forceinline__ void sort8(float (&k)[8], int (&v)[8])
+// Batcher's odd-even merge sort of 16 keys (63 compare-exchanges).
+__device__ __forceinline__ void sort16(float (&k)[16], int (&v)[16])
 {
 #define CX(i, j) cex(k[i], v[i], k[j], v[j])
-    CX(0, 1); CX(2, 3); CX(4, 5); CX(6, 7);
-    CX(0, 2); CX(1, 3); CX(4, 6); CX(5, 7);
-    CX(1, 2); CX(5, 6);
-    CX(0, 4); CX(1, 5); CX(2, 6); CX(3, 7);
-    CX(2, 4); CX(3, 5);
-    CX(1, 2); CX(3, 4); CX(5, 6);
+    CX(0, 1); CX(2, 3); CX(0, 2); CX(1, 3);
+    CX(1, 2); CX(4, 5); CX(6, 7); CX(4, 6);
+    CX(5, 7); CX(5, 6); CX(0, 4); CX(2, 6);
+    CX(2, 4); CX(1, 5); CX(3, 7); CX(3, 5);
+    CX(1, 2); CX(3, 4); CX(5, 6); CX(8, 9);
+    CX(10, 11); CX(8, 10); CX(9, 11); CX(9, 10);
+    CX(12, 13); CX(14, 15); CX(12, 14); CX(13, 15);
+    CX(13, 14); CX(8, 12); CX(10, 14); CX(10, 12);
+    CX(9, 13); CX(11, 15); CX(11, 13); CX(9, 10);
+    CX(11, 12); CX(13, 14); CX(0, 8); CX(4, 12);
+    CX(4, 8); CX(2, 10); CX(6, 14); CX(6, 10);
+    CX(2, 4); CX(6, 8); CX(10, 12); CX(1, 9);
+    CX(5, 13); CX(5, 9); CX(3, 11); CX(7, 15);
+    CX(7, 11); CX(3, 5); CX(7, 9); CX(11, 13);
+    CX(1, 2); CX(3, 4); CX(5, 6); CX(7, 8);
+    CX(9, 10); CX(11, 12); CX(13, 14);
 #undef CX
 }
 
-// lk (ascending, LP keys) <- the LP smallest of lk and the 8 keys pk:
-// sort pk, take min(lk[LP-8+t], pk[7-t]) (a bitonic sequence holding the LP
-// smallest), then a bitonic merge.  Branch-free, identical work in every lane.
+// lk (ascending, LP keys) <- the LP smallest of lk and the 16 keys pk:
+// sort pk, take min(lk[LP-16+t], pk[15-t]) (a bitonic sequence holding the
+// LP smallest), then a bitonic merge.  Branch-free, identical work in every
+// lane.
 template <int LP>
-__device__ __forceinline__ void merge8(float (&lk)[LP], int (&li)[LP], float (&pk)[8], int (&pi)[8])
+__device__ __forceinline__ void merge16(float (&lk)[LP], int (&li)[LP], float (&pk)[16], int (&pi)[16])
 {
-    sort8(pk, pi);
+    sort16(pk, pi);
 #pragma unroll
-    for (int t = 0; t < 8; t++) {
-        const bool sw = pk[7 - t] < lk[LP - 8 + t];
-        lk[LP - 8 + t] = sw ? pk[7 - t] : lk[LP - 8 + t];
-        li[LP - 8 + t] = sw ? pi[7 - t] : li[LP - 8 + t];
+    for (int t = 0; t < 16; t++) {
+        const bool sw = pk[15 - t] < lk[LP - 16 + t];
+        lk[LP - 16 + t] = sw ? pk[15 - t] : lk[LP - 16 + t];
+        li[LP - 16 + t] = sw ? pi[15 - t] : li[LP - 16 + t];
     }
 #pragma unroll
     for (int st = LP / 2; st > 0; st >>= 1)
@@ -280,7 +305,7 @@ __device__ __forceinline__ void merge8(float (&lk)[LP], int (&li)[LP], float (&p
 // Shared-memory layout of one tile (byte offsets from the 1024-aligned base).
 struct TcLayout {
     int reg_rows, L;
-    int a_hi, a_lo, b_hi, b_lo, reg, nb, na2, pk, pi, misc, bytes;
+    int a_hi, a_lo, b_hi, b_lo, reg, nb, nbm, ntb, pk, pi, misc, bytes;
     int lk, li; // after the main loop the lists reuse the operand tiles
 };
 
@@ -307,8 +332,10 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     const int rrows = nch * kChunkRows + kPatch - 1; // region rows read by the chunks (<= lay.reg_rows)
 
     float *reg = reinterpret_cast<float *>(smem + lay.reg);
-    float *nbs = reinterpret_cast<float *>(smem + lay.nb);   // [2][kNc] candidate norms, by chunk parity
-    float *na2s = reinterpret_cast<float *>(smem + lay.na2); // [kM] reference norms
+    // per candidate of the last three chunks: centred norm, -8 mean, -(8 mean + sum / 4)
+    float *nbs = reinterpret_cast<float *>(smem + lay.nb);  // [3][kNc]
+    float *nbm = reinterpret_cast<float *>(smem + lay.nbm); // [3][kNc]
+    float *ntb = reinterpret_cast<float *>(smem + lay.ntb); // [3][kNc]
     float *pk = reinterpret_cast<float *>(smem + lay.pk);    // [kPend][kM] pending keys
     unsigned short *pi = reinterpret_cast<unsigned short *>(smem + lay.pi); // their candidate numbers
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + lay.misc);        // [2]
@@ -360,8 +387,10 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     for (int w = 0; w < kThreads / 32; w++) maxabs = fmaxf(maxabs, s_red[w]);
     int ex = 0;
     frexpf(maxabs, &ex);
-    // power-of-two scale: largest centred magnitude in [2^13, 2^14), inside FP16 range
-    const float sc = maxabs > 0.f ? ldexpf(1.f, 14 - ex) : 1.f;
+    // power-of-two scale: the largest tile-centred magnitude in [2^12, 2^13),
+    // so block-centred values stay below 2^14, inside FP16 range
+    const float sc = maxabs > 0.f ? ldexpf(1.f, 13 - ex) : 1.f;
+    const float vt = maxabs * sc * 1.0001f; // bound on every tile-centred scaled value
     const bool bad = !isfinite(mu) || !isfinite(maxabs) || ex > 100 || ex < -100 || !(fabsf(mu) * sc < 1e30f);
     const float nms = -mu * sc; // fma(x, sc, nms) = (x - mu) sc, rounded once
 
@@ -373,23 +402,66 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     const int rj = vref ? grid_pos(q0 + rc, s, W, kPatch) : 0;
     const int iy = ri - uy0, ix = rj - ux0;
 
-    // ---- reference operand A (thread m builds reference m) and the chunk order
-    if (!bad) {
-        float n2 = 0.f;
+    // One block (src: its top-left in the region) -> tile-centred scaled
+    // values v = (x - mu) sc, their mean m, and the block-centred values
+    // v - m, written as FP16 halves into row n of the operand tiles at
+    // (off_hi, off_lo); returns their sum of squares and their sum.  The
+    // distance splits exactly as |a - b|^2 = |a~ - b~|^2 + 2 (m_a - m_b)
+    // (S_a - S_b) + 64 (m_a - m_b)^2 (a~ = a - m_a, S_a = sum of a~), so the
+    // product only sees the small within-block parts.
+    // src must address an in-bounds block even when valid is false.
+    auto centre = [&](const float *src, bool valid, int off_hi, int off_lo, int n, float &n2, float &mean,
+                      float &ssum) {
+        const f2 sc2 = pack2(sc, sc), nms2 = valid ? pack2(nms, nms) : 0ull;
+        const f2 scv = valid ? sc2 : 0ull; // an invalid block is all zeros
+        // pass 1: row sums of v (two columns per packed operation)
+        f2 acc = 0ull;
 #pragma unroll
         for (int a = 0; a < kPatch; a++) {
-            float v[8];
+            const float *r = src + a * kRegStride;
+            f2 rs = fma2(pack2(r[0], r[1]), scv, nms2);
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                v[b] = vref ? fmaf(reg[(iy + a) * kRegStride + ix + b], sc, nms) : 0.f;
-                n2 = fmaf(v[b], v[b], n2);
+            for (int b = 2; b < kPatch; b += 2) rs = add2(rs, fma2(pack2(r[b], r[b + 1]), scv, nms2));
+            acc = add2(acc, rs);
+        }
+        float s0, s1;
+        unpack2(acc, s0, s1);
+        mean = (s0 + s1) * (1.f / kKd);
+        // pass 2: the same v again, centred, split, summed
+        const f2 nm2 = pack2(-mean, -mean);
+        f2 q2 = 0ull, sq = 0ull;
+#pragma unroll
+        for (int a = 0; a < kPatch; a++) {
+            const float *r = src + a * kRegStride;
+            float t[8];
+#pragma unroll
+            for (int b = 0; b < kPatch; b += 2) {
+                const f2 tv = add2(fma2(pack2(r[b], r[b + 1]), scv, nms2), nm2);
+                q2 = fma2(tv, tv, q2);
+                sq = add2(sq, tv);
+                unpack2(tv, t[b], t[b + 1]);
             }
             uint4 hi, lo;
-            split8(v, hi, lo);
-            *reinterpret_cast<uint4 *>(smem + lay.a_hi + op_off(m, a)) = hi;
-            *reinterpret_cast<uint4 *>(smem + lay.a_lo + op_off(m, a)) = lo;
+            split8(t, hi, lo);
+            *reinterpret_cast<uint4 *>(smem + off_hi + op_off(n, a)) = hi;
+            *reinterpret_cast<uint4 *>(smem + off_lo + op_off(n, a)) = lo;
         }
-        na2s[m] = n2;
+        float q0, q1;
+        unpack2(q2, q0, q1);
+        n2 = q0 + q1;
+        unpack2(sq, q0, q1);
+        ssum = q0 + q1;
+    };
+
+    // ---- reference operand A (thread m builds reference m) and the chunk order
+    float ra2 = 0.f, a8 = 0.f, ta = 0.f; // reference: centred norm, 8 m_a, 8 m_a + S_a / 4
+    if (!bad) {
+        float mean, ssum;
+        // a padding lane (no reference) reads the region's first block, which
+        // is in bounds, and zeroes it
+        centre(vref ? reg + iy * kRegStride + ix : reg, vref, lay.a_hi, lay.a_lo, m, ra2, mean, ssum);
+        a8 = 8.f * mean;
+        ta = a8 + 0.25f * ssum;
     }
     // chunk order: each chunk's rank is its distance (in chunks) to the
     // nearest warp's own reference rows, so that every warp meets the
@@ -419,29 +491,16 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     }
     __syncthreads();
 
-    // builds candidate operand rows of chunk ch (thread n = candidate n) and
-    // their norms; returns the largest norm of a real candidate
-    float nbmax = 0.f;
+    // builds the candidate operand rows of chunk ch (thread n = candidate n)
+    // and their per-candidate terms into buffer par
     auto build = [&](int ch, int par) {
         const int n = tid;
         const int rowl = ch * kChunkRows + (n >> 6), col = n & (kChunkCols - 1);
-        const float *src = reg + rowl * kRegStride + col;
-        float n2 = 0.f;
-#pragma unroll
-        for (int a = 0; a < kPatch; a++) {
-            float v[8];
-#pragma unroll
-            for (int b = 0; b < 8; b++) {
-                v[b] = fmaf(src[a * kRegStride + b], sc, nms);
-                n2 = fmaf(v[b], v[b], n2);
-            }
-            uint4 hi, lo;
-            split8(v, hi, lo);
-            *reinterpret_cast<uint4 *>(smem + lay.b_hi + op_off(n, a)) = hi;
-            *reinterpret_cast<uint4 *>(smem + lay.b_lo + op_off(n, a)) = lo;
-        }
+        float n2, mean, ssum;
+        centre(reg + rowl * kRegStride + col, true, lay.b_hi, lay.b_lo, n, n2, mean, ssum);
         nbs[par * kNc + n] = n2;
-        if (rowl < UH && col < UW) nbmax = fmaxf(nbmax, n2);
+        nbm[par * kNc + n] = -8.f * mean;
+        ntb[par * kNc + n] = -(8.f * mean + 0.25f * ssum);
     };
     // issues the twelve MMAs of one chunk into accumulator buffer b (thread 0)
     auto issue = [&](int b) {
@@ -489,25 +548,25 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     float thr = kInf; // the LT-th best key: larger ones can never be kept
     int np = 0;       // pending keys of this lane (shared memory)
 
-    // merges every lane's pending keys into its list, eight at a time
+    // merges every lane's pending keys into its list, sixteen at a time
     auto flush = [&]() {
         while (__any_sync(kFull, np > 0)) {
-            float pkr[8];
-            int pir[8];
+            float pkr[16];
+            int pir[16];
 #pragma unroll
-            for (int t = 0; t < 8; t++) {
+            for (int t = 0; t < 16; t++) {
                 const bool h = t < np;
                 pkr[t] = h ? pk[t * kM + m] : kInf;
                 pir[t] = h ? (int)pi[t * kM + m] : 0;
             }
 #pragma unroll
-            for (int t = 8; t < kPend; t++)
+            for (int t = 16; t < kPend; t++)
                 if (t < np) {
-                    pk[(t - 8) * kM + m] = pk[t * kM + m];
-                    pi[(t - 8) * kM + m] = pi[t * kM + m];
+                    pk[(t - 16) * kM + m] = pk[t * kM + m];
+                    pi[(t - 16) * kM + m] = pi[t * kM + m];
                 }
-            np = np > 8 ? np - 8 : 0;
-            merge8<LP>(lkr, lir, pkr, pir);
+            np = np > 16 ? np - 16 : 0;
+            merge16<LP>(lkr, lir, pkr, pir);
             thr = lkr[LT - 1];
         }
     };
@@ -542,7 +601,8 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         const int nsteps = (ok && ch >= wc_lo && ch <= wc_hi) ? kNc / 8 : 0;
         const int nst = nsteps + (c == nch - 1 ? 1 : 0);
         const uint32_t tcol = tmem + (uint32_t)(b * kNc) + ((uint32_t)(warp * 32) << 16);
-        const float *nbc = nbs + (c % 3) * kNc;
+        const int pb = (c % 3) * kNc;
+        const f2 a8x2 = pack2(a8, a8), tax2 = pack2(ta, ta), m2x2 = pack2(-2.f, -2.f);
 #pragma unroll 1
         for (int st = 0; st < nst; st++) {
             if (st < nsteps) {
@@ -557,13 +617,26 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
                 msk >>= j8;
                 uint32_t v[8];
                 tmem_ld8(tcol + (uint32_t)(st * 8), v);
-                const float4 nA = *reinterpret_cast<const float4 *>(nbc + st * 8);
-                const float4 nB = *reinterpret_cast<const float4 *>(nbc + st * 8 + 4);
-                const float nbv[8] = {nA.x, nA.y, nA.z, nA.w, nB.x, nB.y, nB.z, nB.w};
+                // e = |b~|^2 + d (d + (S_a - S_b) / 4) - 2 a~.b~ with d = 8 (m_a - m_b):
+                // the block-centred key, two columns per packed FP32 operation
+                const ulonglong2 *qn = reinterpret_cast<const ulonglong2 *>(nbs + pb + st * 8);
+                const ulonglong2 *qm = reinterpret_cast<const ulonglong2 *>(nbm + pb + st * 8);
+                const ulonglong2 *qt = reinterpret_cast<const ulonglong2 *>(ntb + pb + st * 8);
+                const ulonglong2 n0 = qn[0], n1 = qn[1], m0 = qm[0], m1 = qm[1], t0 = qt[0], t1 = qt[1];
+                const f2 nn[4] = {n0.x, n0.y, n1.x, n1.y}, mm[4] = {m0.x, m0.y, m1.x, m1.y};
+                const f2 tt[4] = {t0.x, t0.y, t1.x, t1.y};
+                float ev[8];
+#pragma unroll
+                for (int jp = 0; jp < 4; jp++) {
+                    const f2 dd = add2(a8x2, mm[jp]);
+                    const f2 bb = fma2(dd, add2(tax2, tt[jp]), nn[jp]);
+                    const f2 ee = fma2(pack2(__uint_as_float(v[2 * jp]), __uint_as_float(v[2 * jp + 1])), m2x2, bb);
+                    unpack2(ee, ev[2 * jp], ev[2 * jp + 1]);
+                }
                 const int cbase = rowl * kChunkCols + h * 32 + j8;
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
-                    const float e = fmaf(-2.f, __uint_as_float(v[jj]), nbv[jj]);
+                    const float e = ev[jj];
                     if (((msk >> jj) & 1u) && e < thr) {
                         pk[np * kM + m] = e;
                         pi[np * kM + m] = (unsigned short)(cbase + jj);
@@ -576,12 +649,8 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         tc_fence_before();
     }
 
-    // ---- largest candidate norm of the tile; the lists move to shared memory
-    // (over the operand tiles, whose last product has completed)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nbmax = fmaxf(nbmax, __shfl_xor_sync(kFull, nbmax, o));
-    if (lane == 0) s_red[warp] = nbmax;
-    // after a timeout the last product may still be running: let it finish
+    // ---- the lists move to shared memory (over the operand tiles, whose last
+    // product has completed); after a timeout the last product may still be running: let it finish
     // before its operand tiles are overwritten and its accumulators released
     if (tid == 0 && *s_err && last_issued >= 0)
         mbar_wait(smem_u32(&mbar[last_issued & 1]), (last_issued >> 1) & 1, nullptr);
@@ -602,15 +671,18 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         const size_t gq = ((size_t)(p0 + rr) * Bx + q0 + rc) * K;
         bool ovf = bad || err;
         if (!ovf && cnt == L) {
-            // certify: every key left out is provably above the (K-1)-th kept one
-            const float nbm = fmaxf(fmaxf(s_red[0], s_red[1]), fmaxf(s_red[2], s_red[3]));
-            const float na2 = na2s[m];
-            const float na = sqrtf(na2), nb = sqrtf(nbm);
-            const float d0 = 1e-4f * na * nb + 4e-6f * nbm + 1e-6f * (na + nb) + 1e-30f;
+            // certify: every key left out is provably above the (K-1)-th kept
+            // one.  delta(x) bounds |key - (exact FP32 distance - |a~|^2)| for a
+            // key x (scaled units): product rounding and accumulation, the
+            // centring and mean roundings, the norm sums and the direct sum's
+            // own rounding, each bounded through |a~|^2 and x + |a~|^2
+            const float na = sqrtf(ra2);
+            auto delta = [&](float x) {
+                const float dd = fabsf(x) + ra2, r = sqrtf(dd + 1.f);
+                return 1.2e-4f * ra2 + 7e-5f * dd + 4e-6f * vt * r + 3e-6f * (na + r) + 1e-30f;
+            };
             const float T = lk[(K - 2) * kM + m], X = lk[(L - 1) * kM + m];
-            const float hiT = T + 3e-6f * (fabsf(T) + na2) + d0;
-            const float loX = X - 3e-6f * (fabsf(X) + na2) - d0;
-            ovf = !(loX > hiT);
+            ovf = !(X - delta(X) > T + delta(T));
         }
         if (ovf) {
             idx[gq] = -1; // re-matched by the direct kernel
@@ -680,7 +752,7 @@ TcLayout tc_layout(int H, int s, int R, int K)
     if (uh > H - kPatch + 1) uh = H - kPatch + 1;
     if (uh < 1) uh = 1;
     t.reg_rows = (uh + kChunkRows - 1) / kChunkRows * kChunkRows + kPatch - 1;
-    t.L = K <= 16 ? 24 : 40; // kept keys: K - 1 plus a margin of at least 8
+    t.L = K <= 16 ? 20 : 36; // kept keys: K - 1 plus a margin of at least 4
     int o = 0;
     t.a_hi = o;
     o += kOp;
@@ -695,8 +767,10 @@ TcLayout tc_layout(int H, int s, int R, int K)
     o = (o + 15) / 16 * 16;
     t.nb = o;
     o += 3 * kNc * 4;
-    t.na2 = o;
-    o += kM * 4;
+    t.nbm = o;
+    o += 3 * kNc * 4;
+    t.ntb = o;
+    o += 3 * kNc * 4;
     t.pk = o;
     o += kPend * kM * 4;
     t.pi = o;
@@ -726,7 +800,7 @@ cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, i
     const TcLayout lay = tc_layout(H, s, R, K);
     // the operand tiles and pending keys alone take over a third of the SM's
     // shared memory: at most two CTAs per SM, 2 x 256 tensor-memory columns
-    auto kern = lay.L == 24 ? k_match_tc<32, 24> : k_match_tc<64, 40>;
+    auto kern = lay.L == 20 ? k_match_tc<32, 20> : k_match_tc<64, 36>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.bytes);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kTileX - 1) / kTileX, (By + kTileY - 1) / kTileY);

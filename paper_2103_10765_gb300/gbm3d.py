@@ -67,12 +67,13 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_aggregate.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp, vp]
     lib.gbm3d_denoise.argtypes = [vp, ci, ci, ci, cf, P, vp, vp, vp]
     lib.gbm3d_aggregate_noalloc.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp]
+    lib.gbm3d_set_match_events.argtypes = [vp]
     lib.gbm3d_match_stats.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.gbm3d_last_error_string.restype = ctypes.c_char_p
     lib.gbm3d_version.restype = ctypes.c_char_p
     for name in ("gbm3d_params_default", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
                  "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise",
-                 "gbm3d_aggregate_noalloc", "gbm3d_match_stats"):
+                 "gbm3d_aggregate_noalloc", "gbm3d_match_stats", "gbm3d_set_match_events"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -132,6 +133,25 @@ def match(img: torch.Tensor, K: int, p: Params | None = None, with_dist: bool = 
     _check(load().gbm3d_match(_ptr(img), H, W, pitch, ctypes.byref(p), K, _ptr(idx), _ptr(dist), None,
                               _stream(img)))
     return idx, dist
+
+
+_match_events_keep = None
+
+
+def set_match_events(events=None):
+    """Record 4 torch.cuda.Events around the two matching launches of every
+    gbm3d_denoise on this thread (None: off).  events[0..1] bracket stage 1,
+    events[2..3] stage 2."""
+    global _match_events_keep
+    if events is None:
+        _match_events_keep = None
+        _check(load().gbm3d_set_match_events(None))
+        return
+    if len(events) != 4:
+        raise ValueError("need 4 events")
+    arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _match_events_keep = (arr, events)
+    _check(load().gbm3d_set_match_events(ctypes.cast(arr, ctypes.c_void_p)))
 
 
 def match_stats():

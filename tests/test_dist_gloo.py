@@ -54,3 +54,12 @@ def test_single_rank_helpers():
     assert bench.candidate_pairs(64, 64, R=3) == sum(
         (min(56, i + 3) - max(0, i - 3) + 1) * (min(56, j + 3) - max(0, j - 3) + 1) - 1
         for i in sorted(set(min(p * 3, 56) for p in range(20))) for j in sorted(set(min(q * 3, 56) for q in range(20))))
+
+
+def test_tc_executed_flop_closed_form():
+    # 1024^2, s = 3, R = 19: 340 grid rows in tiles of 16; the union of a tile's
+    # windows spans 65 rows for the first tile, 84 inside, 76 for tile 20 and
+    # 28 for the 4-row last tile -> 33 + 19 x 42 + 38 + 14 = 883 two-row
+    # chunks per tile column, 43 tile columns, 3 x 2 x 128 x 128 x 64 FLOP each
+    import bench
+    assert bench.tc_executed_flop(1024, 1024) == 883 * 43 * 3 * 2 * 128 * 128 * 64
