@@ -11,18 +11,21 @@
 // Exactness.  The product only ranks; the returned list is the exact one of
 // the direct FP32 sum (match.cu), bit for bit:
 //  1. Pixels are centred on the tile mean and scaled by a power of two so the
-//     largest magnitude lies in [2^13, 2^14) (exact scaling), then split into
-//     two FP16 halves v = hi + lo; three products hi.hi + hi.lo + lo.hi give
-//     a.b to about 2^-21 relative.
-//  2. e~ = ||b||^2 - 2 a.b (the reference's own norm is a per-lane constant).
-//     Each lane keeps its L = K - 1 + margin (20 for K <= 16, 36 for
-//     K <= 32) smallest keys in registers; keys below its current L-th one
-//     wait in a small shared-memory queue and are merged sixteen at a time
-//     by branch-free sorting networks, so all 32 lanes do identical work.
-//  3. A rigorous bound delta on |e~ - e*| (e* = the exact-FP32 distance minus
-//     ||a||^2) certifies the list: if every key outside it is provably larger
-//     than the (K-1)-th key inside (lo(e~_L) > hi(e~_{K-1})), the true K-1
-//     best are inside.  Their exact FP32 distances (same operation order as
+//     largest magnitude lies in [2^12, 2^13) (exact scaling), each block is
+//     then centred on its own mean (values below 2^14) and split into two
+//     FP16 halves v = hi + lo; three products hi.hi + hi.lo + lo.hi give the
+//     product to about 2^-21 relative.
+//  2. The mean terms of the distance are added per pair in FP32, and each
+//     lane keeps its L (16 for
+//     K <= 16, 32 for K <= 32) smallest keys in registers.  Keys below its
+//     L-th key plus a margin wait in a small shared-memory queue and are
+//     merged sixteen at a time by branch-free sorting networks (identical
+//     work in all 32 lanes); merges also record the two smallest keys they
+//     drop, the first of which joins the exact re-rank.
+//  3. A rigorous bound delta on |key - e*| (e* = the exact-FP32 distance
+//     minus the reference's centred norm) certifies the list: if every key
+//     left out is provably larger than the (K-1)-th key kept, the true K-1
+//     best are kept.  Their exact FP32 distances (same operation order as
 //     match.cu) are then recomputed and sorted by (distance, k*W + l).
 //  4. A reference that fails the test (near-ties wider than the margin,
 //     non-finite input, a timed-out wait) is marked by slot 0 = -1 and
@@ -281,17 +284,27 @@ __device__ __forceinline__ void sort16(float (&k)[16], int (&v)[16])
 
 // lk (ascending, LP keys) <- the LP smallest of lk and the 16 keys pk:
 // sort pk, take min(lk[LP-16+t], pk[15-t]) (a bitonic sequence holding the
-// LP smallest), then a bitonic merge.  Branch-free, identical work in every
-// lane.
+// LP smallest), then a bitonic merge.  (x1, i1) and x2 track the smallest
+// key ever dropped (with its candidate) and the second smallest.
+// Branch-free, identical work in every lane.
 template <int LP>
-__device__ __forceinline__ void merge16(float (&lk)[LP], int (&li)[LP], float (&pk)[16], int (&pi)[16])
+__device__ __forceinline__ void merge16(float (&lk)[LP], int (&li)[LP], float (&pk)[16], int (&pi)[16],
+                                        float &x1, int &i1, float &x2)
 {
     sort16(pk, pi);
 #pragma unroll
     for (int t = 0; t < 16; t++) {
-        const bool sw = pk[15 - t] < lk[LP - 16 + t];
-        lk[LP - 16 + t] = sw ? pk[15 - t] : lk[LP - 16 + t];
-        li[LP - 16 + t] = sw ? pi[15 - t] : li[LP - 16 + t];
+        const float a = lk[LP - 16 + t], b = pk[15 - t];
+        const int ia = li[LP - 16 + t], ib = pi[15 - t];
+        const bool sw = b < a;
+        lk[LP - 16 + t] = sw ? b : a;
+        li[LP - 16 + t] = sw ? ib : ia;
+        const float d = sw ? a : b; // dropped
+        const int id = sw ? ia : ib;
+        const bool lt = d < x1;
+        x2 = lt ? x1 : fminf(x2, d);
+        i1 = lt ? id : i1;
+        x1 = lt ? d : x1;
     }
 #pragma unroll
     for (int st = LP / 2; st > 0; st >>= 1)
@@ -545,8 +558,21 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         lkr[t] = kInf;
         lir[t] = 0;
     }
-    float thr = kInf; // the LT-th best key: larger ones can never be kept
-    int np = 0;       // pending keys of this lane (shared memory)
+    // delta(x) bounds |key - (exact FP32 distance - |a~|^2)| for a key x
+    // (scaled units): product rounding and accumulation, the centring and
+    // mean roundings, the norm sums and the direct sum's own rounding, each
+    // bounded through |a~|^2 and x + |a~|^2
+    const float na = sqrtf(ra2);
+    auto delta = [&](float x) {
+        const float dd = fabsf(x) + ra2, r = sqrtf(dd + 1.f);
+        return 1.2e-4f * ra2 + 7e-5f * dd + 4e-6f * vt * r + 3e-6f * (na + r) + 1e-30f;
+    };
+    float thr = kInf;   // the LT-th best key so far
+    float thr_q = kInf; // keys below thr + 2.5 delta(thr) are queued: every key never
+                        // queued is above the final one of these
+    float x1 = kInf, x2 = kInf; // the two smallest keys merges have dropped
+    int i1 = 0;                 // the candidate of x1
+    int np = 0;         // pending keys of this lane (shared memory)
 
     // merges every lane's pending keys into its list, sixteen at a time
     auto flush = [&]() {
@@ -566,8 +592,9 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
                     pi[(t - 16) * kM + m] = pi[t * kM + m];
                 }
             np = np > 16 ? np - 16 : 0;
-            merge16<LP>(lkr, lir, pkr, pir);
+            merge16<LP>(lkr, lir, pkr, pir, x1, i1, x2);
             thr = lkr[LT - 1];
+            thr_q = thr < kInf ? thr + 2.5f * delta(thr) : kInf;
         }
     };
 
@@ -637,7 +664,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
                     const float e = ev[jj];
-                    if (((msk >> jj) & 1u) && e < thr) {
+                    if (((msk >> jj) & 1u) && e < thr_q) {
                         pk[np * kM + m] = e;
                         pi[np * kM + m] = (unsigned short)(cbase + jj);
                         np++;
@@ -666,22 +693,22 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         li[t * kM + m] = lir[t];
         cnt += lkr[t] < kInf ? 1 : 0;
     }
+    // the smallest dropped key joins the exact re-rank (slot LT; it is not
+    // below any kept key: the list only ever takes smaller keys)
+    if (x1 < kInf) {
+        lk[LT * kM + m] = x1;
+        li[LT * kM + m] = i1;
+        cnt++;
+    }
 
     if (vref) {
         const size_t gq = ((size_t)(p0 + rr) * Bx + q0 + rc) * K;
         bool ovf = bad || err;
-        if (!ovf && cnt == L) {
-            // certify: every key left out is provably above the (K-1)-th kept
-            // one.  delta(x) bounds |key - (exact FP32 distance - |a~|^2)| for a
-            // key x (scaled units): product rounding and accumulation, the
-            // centring and mean roundings, the norm sums and the direct sum's
-            // own rounding, each bounded through |a~|^2 and x + |a~|^2
-            const float na = sqrtf(ra2);
-            auto delta = [&](float x) {
-                const float dd = fabsf(x) + ra2, r = sqrtf(dd + 1.f);
-                return 1.2e-4f * ra2 + 7e-5f * dd + 4e-6f * vt * r + 3e-6f * (na + r) + 1e-30f;
-            };
-            const float T = lk[(K - 2) * kM + m], X = lk[(L - 1) * kM + m];
+        if (!ovf && cnt >= L) {
+            // certify: every key left out (dropped by a merge and not x1: >= x2;
+            // never queued: >= thr_q, which only decreased) is provably above
+            // the (K-1)-th kept one.  (A list that never filled left nothing out.)
+            const float T = lk[(K - 2) * kM + m], X = fminf(x2, thr_q);
             ovf = !(X - delta(X) > T + delta(T));
         }
         if (ovf) {
@@ -752,7 +779,7 @@ TcLayout tc_layout(int H, int s, int R, int K)
     if (uh > H - kPatch + 1) uh = H - kPatch + 1;
     if (uh < 1) uh = 1;
     t.reg_rows = (uh + kChunkRows - 1) / kChunkRows * kChunkRows + kPatch - 1;
-    t.L = K <= 16 ? 20 : 36; // kept keys: K - 1 plus a margin of at least 4
+    t.L = K <= 16 ? 16 : 32; // kept keys (K - 1 of them are returned)
     int o = 0;
     t.a_hi = o;
     o += kOp;
@@ -779,8 +806,8 @@ TcLayout tc_layout(int H, int s, int R, int K)
     t.misc = o; // mbarriers, tensor-memory address, flags, reductions, chunk order
     o += 128 + 4 * 128;
     t.bytes = o;
-    t.lk = t.a_hi; // after the loop: lists over the operand tiles
-    t.li = t.lk + t.L * kM * 4;
+    t.lk = t.a_hi; // after the loop: lists (L kept + 1 dropped) over the operand tiles
+    t.li = t.lk + (t.L + 1) * kM * 4;
     return t;
 }
 
@@ -800,7 +827,7 @@ cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, i
     const TcLayout lay = tc_layout(H, s, R, K);
     // the operand tiles and pending keys alone take over a third of the SM's
     // shared memory: at most two CTAs per SM, 2 x 256 tensor-memory columns
-    auto kern = lay.L == 20 ? k_match_tc<32, 20> : k_match_tc<64, 36>;
+    auto kern = lay.L == 16 ? k_match_tc<16, 16> : k_match_tc<32, 32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.bytes);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kTileX - 1) / kTileX, (By + kTileY - 1) / kTileY);
