@@ -84,6 +84,10 @@ def _declare(lib):
     lib.orc_aggregate.argtypes = [_f64p, _f64p, _i32p, c_int, c_int, c_int, c_int, c_int, c_double, _f64p]
     lib.orc_denoise.argtypes = [_f64p, c_int, c_int, c_double, ctypes.POINTER(_Params), _f64p, vp, c_int]
     lib.orc_max_threads.argtypes = []
+    lib.orc_opp.argtypes = [_f64p, ctypes.c_size_t, c_int, _f64p]
+    lib.orc_opp_sigma_scale.argtypes = [c_int]
+    lib.orc_opp_sigma_scale.restype = c_double
+    lib.orc_denoise_color.argtypes = [_f64p, c_int, c_int, c_double, ctypes.POINTER(_Params), _f64p, c_int]
 
 
 class OracleError(RuntimeError):
@@ -275,6 +279,30 @@ def denoise(Z, sigma, params: Params | None = None, nthreads=1, return_y1=False)
     _check(_get().orc_denoise(Z, H, W, float(sigma), ctypes.byref(p), out, y1.ctypes.data_as(ctypes.c_void_p),
                               nthreads), "orc_denoise")
     return (out, y1) if return_y1 else out
+
+
+def opp(x, inverse=False):
+    """Opponent colour transform of a (3, H, W) array (reading C1), or its inverse."""
+    x = _f64(x)
+    y = np.zeros_like(x)
+    _check(_get().orc_opp(x, x[0].size, int(inverse), y), "orc_opp")
+    return y
+
+
+def opp_sigma_scale(c: int) -> float:
+    """Noise deviation of opponent channel c per unit deviation in R, G, B (reading C2)."""
+    return float(_get().orc_opp_sigma_scale(c))
+
+
+def denoise_color(Z, sigma, params: Params | None = None, nthreads=1):
+    """Colour G-BM3D of a (3, H, W) RGB array (readings C1-C4)."""
+    params = params or Params()
+    Z = _f64(Z)
+    _, H, W = Z.shape
+    out = np.zeros_like(Z)
+    p = params.c()
+    _check(_get().orc_denoise_color(Z, H, W, float(sigma), ctypes.byref(p), out, nthreads), "orc_denoise_color")
+    return out
 
 
 def psnr(x, ref) -> float:

@@ -753,6 +753,110 @@ int orc_denoise(const double *Z, int H, int W, double sigma, const orc_params *p
     return st;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Colour extension.  The paper is grayscale only; this is the usual colour
+ * use of BM3D (reading C1-C4):
+ *   C1 opponent transform per pixel: Y = (R+G+B)/3, U = (R-B)/2,
+ *      V = (R-2G+B)/4 (rows orthogonal, so independent channel noise stays
+ *      independent), inverse R = Y+U+2V/3, G = Y-4V/3, B = Y-U+2V/3;
+ *   C2 channel c carries noise sigma_c = sigma |row_c| (sigma/sqrt3,
+ *      sigma/sqrt2, sigma sqrt(3/8)) for i.i.d. noise of deviation sigma in
+ *      R, G, B;
+ *   C3 each stage matches once, on Y (stage 2: on the Y of the stage-1
+ *      estimate), and every channel is filtered through those groups with
+ *      its own sigma_c, its own weights and its own aggregation;
+ *   C4 translations as in orc_denoise, applied to all channels together. */
+static const double ORC_OPP_F[3][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {0.5, 0.0, -0.5}, {0.25, -0.5, 0.25}};
+static const double ORC_OPP_I[3][3] = {{1.0, 1.0, 2.0 / 3}, {1.0, 0.0, -4.0 / 3}, {1.0, -1.0, 2.0 / 3}};
+
+/* x (3 planes of n values, plane c at x + c n) -> y = M x per pixel
+ * (inverse = 0: forward opponent transform, 1: its inverse). */
+int orc_opp(const double *x, size_t n, int inverse, double *y)
+{
+    if (!x || !y) return ORC_EINVAL;
+    const double (*M)[3] = inverse ? ORC_OPP_I : ORC_OPP_F;
+    for (size_t e = 0; e < n; e++) {
+        const double a = x[e], b = x[n + e], c = x[2 * n + e];
+        for (int r = 0; r < 3; r++) y[r * n + e] = M[r][0] * a + M[r][1] * b + M[r][2] * c;
+    }
+    return ORC_OK;
+}
+
+/* sigma_c / sigma = |row c of the forward transform| (reading C2). */
+double orc_opp_sigma_scale(int c)
+{
+    if (c < 0 || c > 2) return 0.0;
+    const double *r = ORC_OPP_F[c];
+    return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+}
+
+/* One colour stage on (possibly shifted) opponent planes Zo: matching on the
+ * guide plane (Zo[0] in stage 1, Y1o[0] in stage 2), then per channel the
+ * stage's filter and aggregation into out (3 planes). */
+static int stage_color(const double *Zo, const double *Y1o, int H, int W, double sigma, const orc_params *p,
+                       double *out, int nt)
+{
+    const int N = p->patch, K = Y1o ? p->k2 : p->k1;
+    const int By = orc_grid(H, N, p->step, NULL), Bx = orc_grid(W, N, p->step, NULL);
+    const size_t G = (size_t)By * Bx, n = (size_t)H * W;
+    int32_t *idx = malloc(sizeof(int32_t) * G * K);
+    double *gr = malloc(sizeof(double) * G * K * N * N), *w = malloc(sizeof(double) * G);
+    int st = (idx && gr && w) ? ORC_OK : ORC_ENOMEM;
+    if (st == ORC_OK) st = orc_match(Y1o ? Y1o : Zo, H, W, N, p->step, p->search_radius, K, idx, NULL, nt);
+    for (int c = 0; c < 3 && st == ORC_OK; c++) {
+        const double sc = sigma * orc_opp_sigma_scale(c);
+        if (!Y1o) {
+            st = orc_filter_ht(Zo + c * n, H, W, idx, By, Bx, N, K, sc, p->levels, p->cycle_spins, p->tau_a,
+                               p->tau_b, p->eps_w, gr, w);
+            if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, 0.0, out + c * n);
+        } else {
+            st = orc_filter_wiener(Zo + c * n, Y1o + c * n, H, W, idx, (int)G, N, K, sc, p->eps_w, gr, w, nt);
+            if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, p->kaiser_beta, out + c * n);
+        }
+    }
+    free(idx); free(gr); free(w);
+    return st;
+}
+
+/* Colour denoising of Z (3 planes R, G, B of H x W) into out (3 planes). */
+int orc_denoise_color(const double *Z, int H, int W, double sigma, const orc_params *p, double *out, int nthreads)
+{
+    if (!Z || !p || !out || H < p->patch || W < p->patch || p->translations < 1 || p->translations > 3 ||
+        p->stages < 1 || p->stages > 2 || sigma < 0)
+        return ORC_EINVAL;
+    const size_t n = (size_t)H * W;
+    const int hs[3] = {0, p->patch / 4, p->patch / 2};
+    double *zo = malloc(sizeof(double) * 3 * n), *zs = malloc(sizeof(double) * 3 * n);
+    double *o = malloc(sizeof(double) * 3 * n), *os = malloc(sizeof(double) * 3 * n);
+    double *y1 = calloc(3 * n, sizeof(double)), *y1s = malloc(sizeof(double) * 3 * n);
+    double *acc = calloc(3 * n, sizeof(double));
+    int st = (zo && zs && o && os && y1 && y1s && acc) ? ORC_OK : ORC_ENOMEM;
+    if (st == ORC_OK) st = orc_opp(Z, n, 0, zo);
+    for (int t = 0; t < p->translations && st == ORC_OK; t++) {
+        for (int c = 0; c < 3; c++) shift2(zo + c * n, zs + c * n, H, W, hs[t]);
+        st = stage_color(zs, NULL, H, W, sigma, p, o, nthreads);
+        for (int c = 0; c < 3 && st == ORC_OK; c++) {
+            shift2(o + c * n, os + c * n, H, W, -hs[t]);
+            for (size_t e = 0; e < n; e++) y1[c * n + e] += os[c * n + e] / p->translations;
+        }
+    }
+    if (st == ORC_OK && p->stages == 1) memcpy(acc, y1, sizeof(double) * 3 * n);
+    for (int t = 0; p->stages == 2 && t < p->translations && st == ORC_OK; t++) {
+        for (int c = 0; c < 3; c++) {
+            shift2(zo + c * n, zs + c * n, H, W, hs[t]);
+            shift2(y1 + c * n, y1s + c * n, H, W, hs[t]);
+        }
+        st = stage_color(zs, y1s, H, W, sigma, p, o, nthreads);
+        for (int c = 0; c < 3 && st == ORC_OK; c++) {
+            shift2(o + c * n, os + c * n, H, W, -hs[t]);
+            for (size_t e = 0; e < n; e++) acc[c * n + e] += os[c * n + e] / p->translations;
+        }
+    }
+    if (st == ORC_OK) st = orc_opp(acc, n, 1, out);
+    free(zo); free(zs); free(o); free(os); free(y1); free(y1s); free(acc);
+    return st;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -131,5 +131,17 @@ def make_pair(H: int, W: int, sigma: float, scene_seed: int = 1):
     return clean, add_noise(clean, sigma, 1000 + scene_seed)
 
 
+def make_color_pair(H: int, W: int, sigma: float, scene_seed: int = 1):
+    """(clean, noisy) float32 RGB images of shape (3, H, W): two independent
+    scenes A (seed s) and B (seed s + 50) give R = A, G = (A + B) / 2, B = B,
+    so the channels are correlated as in natural images; noise is i.i.d. per
+    channel with seeds 1000 + s, 2000 + s, 3000 + s."""
+    a = clean_scene(H, W, scene_seed).astype(np.float64)
+    b = clean_scene(H, W, scene_seed + 50).astype(np.float64)
+    clean = np.stack([a, 0.5 * (a + b), b]).astype(np.float32)
+    noisy = np.stack([add_noise(clean[c], sigma, 1000 * (c + 1) + scene_seed) for c in range(3)])
+    return clean, noisy
+
+
 def constant_image(H: int, W: int, value: float = 0.5) -> np.ndarray:
     return np.full((H, W), value, dtype=np.float32)

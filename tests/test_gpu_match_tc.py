@@ -95,6 +95,13 @@ def test_engines_identical_full_size(g, K):
     _assert_same(*_both(g, _noisy(1024, 1024, 25 / 255), K))
 
 
+@pytest.mark.parametrize("K", [16, 32])
+def test_engines_identical_4096(g, K):
+    # the 4096^2 grayscale configuration: all 1,860,496 lists
+    img = _noisy(4096, 4096, 25 / 255, seed=4) if K == 16 else _clean(4096, 4096, seed=4)
+    _assert_same(*_both(g, img, K))
+
+
 def test_engines_identical_full_size_smooth(g):
     # a stage-2-like input (smooth estimate) at full size
     _assert_same(*_both(g, _clean(1024, 1024, seed=2), 32))

@@ -93,7 +93,8 @@ def test_match_exact_ties_flat_image(orc):
     np.testing.assert_array_equal(gidx.cpu().numpy(), oidx)
 
 
-@pytest.mark.parametrize("H,W,K", [(1024, 1024, 16), (1024, 1024, 32), (2048, 2048, 16)])
+@pytest.mark.parametrize("H,W,K", [(1024, 1024, 16), (1024, 1024, 32), (2048, 2048, 16), (4096, 4096, 16),
+                                   (4096, 4096, 32)])
 def test_match_parity_full_size_sampled(orc, H, W, K):
     """Full-size launch (as the benchmark runs it); oracle on a sample of references."""
     _, X = synth.make_pair(H, W, 25 / 255, 1)
@@ -230,3 +231,15 @@ def test_pitched_input_matches_contiguous():
     a = gbm3d.denoise(gpu(X), 0.1)
     b = gbm3d.denoise(view, 0.1, out=torch.zeros((64, 96), device=DEV)[:, :70])
     assert torch.equal(a, b)
+
+
+def test_denoise_4096_runs():
+    """The 4096 x 4096 grayscale configuration end to end (33 GB workspace):
+    finite output, and far closer to the clean scene than the noisy input."""
+    clean, X = synth.make_pair(4096, 4096, 25 / 255, 3)
+    out = gbm3d.denoise(gpu(X), 25 / 255).cpu().numpy().astype(np.float64)
+    assert np.isfinite(out).all()
+    c = clean.astype(np.float64)
+    p_noisy = 10 * np.log10(1 / np.mean((X.astype(np.float64) - c) ** 2))
+    p_out = 10 * np.log10(1 / np.mean((out - c) ** 2))
+    assert p_out > p_noisy + 8, (p_noisy, p_out)
