@@ -38,12 +38,47 @@ sys.path.insert(0, ROOT)
 from paper_2103_10765_gb300 import synth  # noqa: E402
 
 METRIC = "denoised MPix/s per GB300 (2-stage) at ≤0.01 dB PSNR gap to FP64 oracle"
-H = W = 1024
 SIGMA = 25 / 255
-WORKLOAD = ("two-stage G-BM3D, 1024x1024 grayscale fp32, sigma 25/255, N=8 s=3 R=19 (39x39 offsets), "
-            "K1=16 K2=32, 3 levels bior1.5/Haar, 2 cycle spins, 1 translation")
+_PARAMS = "N=8 s=3 R=19 (39x39 offsets), K1=16 K2=32, 3 levels bior1.5/Haar, 2 cycle spins, 1 translation"
+# --workload: gray1024 is the metric's configuration (the default); the other
+# two are the larger tensor-core matching configurations
+WORKLOADS = {
+    "gray1024": dict(H=1024, W=1024, C=1, cpu_crop=512, ref_crop=256,
+                     desc="two-stage G-BM3D, 1024x1024 grayscale fp32, sigma 25/255, " + _PARAMS),
+    "gray4096": dict(H=4096, W=4096, C=1, cpu_crop=512, ref_crop=256,
+                     desc="two-stage G-BM3D, 4096x4096 grayscale fp32, sigma 25/255, " + _PARAMS),
+    "color2048": dict(H=2048, W=2048, C=3, cpu_crop=256, ref_crop=128,
+                      desc="two-stage colour G-BM3D, 2048x2048x3 RGB fp32 (opponent transform, matching on luma, "
+                           "per-channel sigma), sigma 25/255, " + _PARAMS),
+}
+H = W = 1024
+C = 1                   # channels
+WORKLOAD = WORKLOADS["gray1024"]["desc"]
 CPU_CROP = 512          # cpu_baseline sample: top-left crop of the workload image
 REF_CROP = 256          # --impl reference: crop per step
+
+
+def set_workload(name: str):
+    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP
+    w = WORKLOADS[name]
+    H, W, C, WORKLOAD, CPU_CROP, REF_CROP = w["H"], w["W"], w["C"], w["desc"], w["cpu_crop"], w["ref_crop"]
+
+
+def make_inputs(seed: int):
+    """(clean, noisy) of the workload: (H, W) grayscale or (3, H, W) RGB."""
+    return synth.make_pair(H, W, SIGMA, seed) if C == 1 else synth.make_color_pair(H, W, SIGMA, seed)
+
+
+def launches_per_denoise(p, channels: int, tc: bool = True) -> int:
+    """Kernel launches of one denoise (translations = 1): per stage the
+    matching (+ the exact re-match pass of the tensor-core engine) and the 7
+    launches of the inverted lists; stage 1 per channel the offset table, one
+    analysis and one synthesis per level and cycle spin, TV, gather; stage 2
+    per channel Wiener and gather; colour adds the two opponent transforms."""
+    m = 2 if tc else 1
+    s1 = m + 7 + channels * (1 + 2 * p.cycle_spins * p.levels + 1 + 1)
+    s2 = m + 7 + channels * 2
+    return s1 + (s2 if p.stages == 2 else 0) + (2 if channels == 3 else 0)
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES = 152, 128
 
@@ -179,7 +214,10 @@ class ClockSampler:
 def run_cpu_oracle(noisy_crop, nthreads):
     import oracle
     t0 = time.perf_counter()
-    out = oracle.denoise(noisy_crop, SIGMA, nthreads=nthreads)
+    if noisy_crop.ndim == 3:
+        out = oracle.denoise_color(noisy_crop, SIGMA, nthreads=nthreads)
+    else:
+        out = oracle.denoise(noisy_crop, SIGMA, nthreads=nthreads)
     return out, time.perf_counter() - t0
 
 
@@ -190,7 +228,7 @@ def reference_arm(args, rank, world):
     import oracle
     oracle.build()
     nt = os.cpu_count() or 1
-    imgs = [synth.make_pair(H, W, SIGMA, s)[1][:REF_CROP, :REF_CROP] for s in (1, 2, 3)]
+    imgs = [np.ascontiguousarray(make_inputs(s)[1][..., :REF_CROP, :REF_CROP]) for s in (1, 2, 3)]
     for i in range(args.warmup):
         run_cpu_oracle(imgs[i % 3], nt)
     times = [run_cpu_oracle(imgs[i % 3], nt)[1] for i in range(args.steps)]
@@ -201,7 +239,8 @@ def reference_arm(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": mpix, "unit": "MPix/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "image": [H, W], "sigma": SIGMA, "parallelism": "replicas"},
+        "config": {"workload": WORKLOAD, "image": [H, W], "channels": C, "sigma": SIGMA,
+                   "parallelism": "replicas"},
         "cpu_baseline": {"value": mpix, "unit": "MPix/s", "cores": nt, "kind": "oracle", "sample": sample},
         "e2e": {"value": mpix, "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -215,7 +254,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="gray1024", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    set_workload(args.workload)
     args.warmup = max(args.warmup, 1)
     rank, world, local = dist_env()
 
@@ -235,10 +276,15 @@ def main():
     dev = torch.device("cuda", local)
     p = gbm3d.params_default()
     seeds = rank_seeds(rank)
-    pairs = [synth.make_pair(H, W, SIGMA, s) for s in seeds]
+    pairs = [make_inputs(s) for s in seeds]
     noisy = [torch.from_numpy(n).to(dev) for _, n in pairs]
-    out = torch.empty((H, W), dtype=torch.float32, device=dev)
-    ws = gbm3d.workspace(H, W, p, dev)
+    out = torch.empty_like(noisy[0])
+    if C == 1:
+        ws = gbm3d.workspace(H, W, p, dev)
+        run = lambda x, o=out: gbm3d.denoise(x, SIGMA, p, ws, o)  # noqa: E731
+    else:
+        ws = torch.empty(gbm3d.workspace_bytes_color(H, W, p), dtype=torch.uint8, device=dev)
+        run = lambda x, o=out: gbm3d.denoise_color(x, SIGMA, p, ws, o)  # noqa: E731
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -248,7 +294,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     for i in range(args.warmup):
-        gbm3d.denoise(noisy[i % 3], SIGMA, p, ws, out)
+        run(noisy[i % 3])
     barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     # the dominant kernel (block matching, both stages) timed live inside every
@@ -263,7 +309,7 @@ def main():
             flush.zero_()
             gbm3d.set_match_events(mev[i])
             ev[i][0].record(stream)
-            gbm3d.denoise(noisy[i % 3], SIGMA, p, ws, out)
+            run(noisy[i % 3])
             ev[i][1].record(stream)
         barrier()
     gbm3d.set_match_events(None)
@@ -273,14 +319,14 @@ def main():
     mpix = job_mpix(world, args.steps, total_ms)
 
     # output quality on this step's image (PSNR vs the clean scene)
-    gbm3d.denoise(noisy[0], SIGMA, p, ws, out)
+    run(noisy[0])
     psnr = float(10 * math.log10(1.0 / float(((out.cpu().double() - torch.from_numpy(pairs[0][0]).double())
                                                 ** 2).mean())))
 
     # e2e: pinned host in -> denoise -> host out, per step
     e2e = None
     if not args.no_e2e:
-        hd = gbm3d.HostDenoiser(H, W, p, dev)
+        hd = gbm3d.HostDenoiser(H, W, p, dev, channels=C)
         host_in = [torch.from_numpy(n).pin_memory() for _, n in pairs]
         for i in range(args.warmup):
             hd(host_in[i % 3], SIGMA)
@@ -324,29 +370,33 @@ def main():
                                    f"peak = measured dense BF16 cuBLAS rate ({peak_kind}), FP16 nominal ratio 1"}}
     tr = match_traffic()
     if tr:
-        roofline["traffic"] = 0.5 * (tr.get("dram_bytes_K16", 0.0) + tr.get("dram_bytes_K32", 0.0))
-        roofline["traffic_note"] = "dram read+write bytes per launch, ncu capture of this kernel source"
+        # captured at 1024^2; the launch reads its (luma) image once, so the
+        # traffic scales with the pixel count
+        roofline["traffic"] = 0.5 * (tr.get("dram_bytes_K16", 0.0) + tr.get("dram_bytes_K32", 0.0)) * H * W / 1024 ** 2
+        roofline["traffic_note"] = ("dram read+write bytes per launch, ncu capture of this kernel source at 1024x1024"
+                                    + ("" if H * W == 1024 ** 2 else ", scaled by the pixel count"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nt = os.cpu_count() or 1
-        crop = pairs[0][1][:CPU_CROP, :CPU_CROP]
+        crop = np.ascontiguousarray(pairs[0][1][..., :CPU_CROP, :CPU_CROP])
         ref, secs = run_cpu_oracle(crop, nt)
-        g = gbm3d.denoise(torch.from_numpy(np.ascontiguousarray(crop)).to(dev), SIGMA, p).cpu().numpy()
-        clean = pairs[0][0][:CPU_CROP, :CPU_CROP].astype(np.float64)
+        gin = torch.from_numpy(crop).to(dev)
+        g = (gbm3d.denoise(gin, SIGMA, p) if C == 1 else gbm3d.denoise_color(gin, SIGMA, p)).cpu().numpy()
+        clean = pairs[0][0][..., :CPU_CROP, :CPU_CROP].astype(np.float64)
         pg = 10 * math.log10(1 / np.mean((g - clean) ** 2))
         po = 10 * math.log10(1 / np.mean((ref - clean) ** 2))
         cpu = {"value": CPU_CROP * CPU_CROP / secs / 1e6, "unit": "MPix/s", "cores": nt, "kind": "oracle",
                "sample": f"two-stage FP64 oracle on the top-left {CPU_CROP}x{CPU_CROP} crop of the workload image",
                "seconds": secs, "psnr_gap_db_on_sample": abs(pg - po)}
 
-    launches = 2 + 2 * p.cycle_spins * p.levels + 1 + 7 + 1 + 7  # per denoise (T = 1)
+    launches = launches_per_denoise(p, C)
     if rank == 0:
         line = {
             "metric": METRIC, "value": mpix, "unit": "MPix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "image": [H, W], "sigma": SIGMA, "parallelism": "replicas",
+            "config": {"workload": WORKLOAD, "image": [H, W], "channels": C, "sigma": SIGMA, "parallelism": "replicas",
                        "l2": "flushed between steps (256 MiB write outside the timed events)"},
             "psnr_db": psnr, "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk.summary(),

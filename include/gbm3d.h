@@ -185,6 +185,23 @@ int gbm3d_aggregate_noalloc(const float *groups, const float *w, const int32_t *
 int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, const gbm3d_params *p,
                   float *out, void *ws, gbm3d_stream_t stream);
 
+/* Colour denoising, an extension (the paper is grayscale only): the RGB
+ * planes are mapped per pixel to opponent planes Y = (R+G+B)/3,
+ * U = (R-B)/2, V = (R-2G+B)/4 (orthogonal rows: independent channel noise of
+ * deviation sigma becomes sigma/sqrt(3), sigma/sqrt(2), sigma sqrt(3/8));
+ * each stage matches once, on Y (stage 2: on the Y of the stage-1 estimate),
+ * and filters every channel through those groups with its own sigma, weights
+ * and aggregation; the result is mapped back (R = Y+U+2V/3, G = Y-4V/3,
+ * B = Y-U+2V/3).  translations must be 1 (else GBM3D_EUNSUPPORTED).
+ *   noisy : planes R, G, B of H x W with row pitch `pitch`; plane c starts at
+ *           noisy + c * plane_stride (elements, >= (H-1) pitch + W).
+ *   out   : same layout; must not overlap noisy.
+ *   ws    : scratch, gbm3d_workspace_bytes_color (the grayscale workspace
+ *           plus six H x W planes). */
+int gbm3d_workspace_bytes_color(int H, int W, const gbm3d_params *p, size_t *bytes);
+int gbm3d_denoise_color(const float *noisy, int H, int W, int pitch, long long plane_stride, float sigma,
+                        const gbm3d_params *p, float *out, void *ws, gbm3d_stream_t stream);
+
 /* Counters of the tensor-core matcher on the current device, cumulative since
  * the library was loaded:
  *   timeouts  : bounded device-side waits that gave up (0 when healthy; the

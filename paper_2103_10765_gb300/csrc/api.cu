@@ -239,6 +239,81 @@ cudaError_t launch_shift(const float *src, int spitch, float *dst, int dpitch, i
     return cudaGetLastError();
 }
 
+// ---- colour (an extension: the paper is grayscale) --------------------------
+// Opponent transform per pixel, src planes -> dst planes (inverse: back to RGB):
+//   Y = (R+G+B)/3, U = (R-B)/2, V = (R-2G+B)/4;  R = Y+U+2V/3, G = Y-4V/3, B = Y-U+2V/3.
+__global__ void k_opp(const float *__restrict__ src, int sp, long long splane, float *dst, int dp, long long dplane,
+                      int H, int W, int inverse)
+{
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= W || y >= H) return;
+    const size_t si = (size_t)y * sp + x, di = (size_t)y * dp + x;
+    const float a = src[si], b = src[si + splane], c = src[si + 2 * splane];
+    float o0, o1, o2;
+    if (!inverse) {
+        o0 = (a + b + c) * (1.f / 3.f);
+        o1 = (a - c) * 0.5f;
+        o2 = (a - 2.f * b + c) * 0.25f;
+    } else {
+        o0 = a + b + c * (2.f / 3.f);
+        o1 = a - c * (4.f / 3.f);
+        o2 = a - b + c * (2.f / 3.f);
+    }
+    dst[di] = o0;
+    dst[di + dplane] = o1;
+    dst[di + 2 * dplane] = o2;
+}
+
+static cudaError_t launch_opp(const float *src, int sp, long long splane, float *dst, int dp, long long dplane, int H,
+                              int W, int inverse, cudaStream_t st)
+{
+    dim3 grid((W + 31) / 32, (H + 7) / 8);
+    k_opp<<<grid, 256, 0, st>>>(src, sp, splane, dst, dp, dplane, H, W, inverse);
+    return cudaGetLastError();
+}
+
+// Noise deviation of opponent channel c per unit deviation in R, G, B: the
+// norm of row c of the forward transform (the rows are orthogonal).
+static double opp_scale(int c)
+{
+    static const double sq[3] = {1.0 / 3.0, 0.5, 3.0 / 8.0};
+    return sqrt(sq[c]);
+}
+
+// One colour stage on opponent planes zo (pitch W, plane stride n): match
+// once on the guide plane (zo[0] in stage 1, y1o[0] in stage 2), build the
+// inverted lists once, then filter and aggregate each channel with its own
+// sigma into out plane c (pitch op, plane stride oplane).
+static int run_stage_color(const float *zo, const float *y1o, long long n, int H, int W, float sigma,
+                           const gbm3d_params *p, const Sizes &S, char *ws, float *out, int op, long long oplane,
+                           cudaStream_t st)
+{
+    const bool s2 = y1o != nullptr;
+    const int K = s2 ? p->k2 : p->k1;
+    int32_t *idx = (int32_t *)(ws + S.idx);
+    if (g_match_events) cudaEventRecord(g_match_events[s2 ? 2 : 0], st);
+    cudaError_t e = match_any(s2 ? y1o : zo, H, W, W, S.By, S.Bx, p, K, idx, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, s2 ? "match (stage 2)" : "match (stage 1)");
+    if (g_match_events) cudaEventRecord(g_match_events[s2 ? 3 : 1], st);
+    e = build_csr(idx, S.G, K, H, W, ws + S.csr, true, st);
+    if (e != cudaSuccess) return cuda_fail(e, "inverted lists");
+    const GroupOut go = planar_out(S, ws, H, W, K);
+    float win[8];
+    kaiser8(s2 ? p->kaiser_beta : 0.f, win);
+    for (int c = 0; c < 3; c++) {
+        const float sc = (float)((double)sigma * opp_scale(c));
+        if (s2)
+            e = launch_filter_wiener(zo + c * n, W, y1o + c * n, W, H, W, idx, S.G, K, sc, p->eps_w, go, st);
+        else
+            e = launch_filter_ht(zo + c * n, H, W, W, idx, S.ht, sc, p->tau_a, p->tau_b, p->cycle_spins, p->eps_w, go,
+                                 ws + S.ht_off, st);
+        if (e != cudaSuccess) return cuda_fail(e, s2 ? "filter_wiener" : "filter_ht");
+        e = launch_aggregate_planar(go.base, go.w, S.G * K, H, W, op, win, out + c * oplane, ws + S.csr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "aggregate");
+    }
+    return GBM3D_OK;
+}
+
 } // namespace gbm3d
 
 using namespace gbm3d;
@@ -289,6 +364,21 @@ int gbm3d_params_default(gbm3d_params *p, int preset)
         p->translations = 2;
     }
     g_err[0] = 0;
+    return GBM3D_OK;
+}
+
+// Colour workspace: the grayscale layout, then the opponent planes of the
+// input and of the stage-1 estimate (3 + 3 images, pitch W).
+static size_t color_extra(int H, int W) { return 6 * align_up((size_t)H * W * sizeof(float)); }
+
+int gbm3d_workspace_bytes_color(int H, int W, const gbm3d_params *p, size_t *bytes)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if (!bytes) return fail(GBM3D_EINVAL, "bytes is NULL");
+    if ((st = check_image(H, W, W))) return st;
+    if (p->translations != 1) return fail(GBM3D_EUNSUPPORTED, "colour: translations must be 1");
+    *bytes = sizes(H, W, p).total + color_extra(H, W);
     return GBM3D_OK;
 }
 
@@ -453,6 +543,41 @@ int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, cons
         if (e != cudaSuccess) return cuda_fail(e, "shift");
     }
     return GBM3D_OK;
+}
+
+int gbm3d_denoise_color(const float *noisy, int H, int W, int pitch, long long plane_stride, float sigma,
+                        const gbm3d_params *p, float *out, void *ws, gbm3d_stream_t stream)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if ((st = check_image(H, W, pitch))) return st;
+    if (!noisy || !out || !ws) return fail(GBM3D_EINVAL, "null pointer argument");
+    if (plane_stride < (long long)(H - 1) * pitch + W)
+        return fail(GBM3D_EINVAL, "plane_stride %lld: planes would overlap", plane_stride);
+    const long long span = 2 * plane_stride + (long long)(H - 1) * pitch + W; // elements of the 3 planes
+    if (out < noisy + span && noisy < out + span) return fail(GBM3D_EINVAL, "out must not overlap noisy");
+    if (!(sigma >= 0.f) || !isfinite(sigma)) return fail(GBM3D_EINVAL, "sigma must be finite and >= 0");
+    if (!aligned(ws, kAlign)) return fail(GBM3D_EINVAL, "ws must be 256-byte aligned");
+    if (p->translations != 1) return fail(GBM3D_EUNSUPPORTED, "colour: translations must be 1");
+    if ((st = check_window(H, W, p->search_radius, p->k1 > p->k2 ? p->k1 : p->k2))) return st;
+    if ((st = check_engine(H, W, p, p->k1))) return st;
+    if (p->stages == 2 && (st = check_engine(H, W, p, p->k2))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Sizes S = sizes(H, W, p);
+    char *base = (char *)ws;
+    const long long n = (long long)(align_up((size_t)H * W * sizeof(float)) / sizeof(float));
+    float *zo = (float *)(base + S.total), *y1o = zo + 3 * n;
+    cudaError_t e = launch_opp(noisy, pitch, plane_stride, zo, W, n, H, W, 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "opponent transform");
+    if ((st = run_stage_color(zo, nullptr, n, H, W, sigma, p, S, base, y1o, W, n, s))) return st;
+    if (p->stages == 2) {
+        // stage 2 writes the opponent planes of the result into out, then back to RGB in place
+        if ((st = run_stage_color(zo, y1o, n, H, W, sigma, p, S, base, out, pitch, plane_stride, s))) return st;
+        e = launch_opp(out, pitch, plane_stride, out, pitch, plane_stride, H, W, 1, s);
+    } else {
+        e = launch_opp(y1o, W, n, out, pitch, plane_stride, H, W, 1, s);
+    }
+    return e == cudaSuccess ? GBM3D_OK : cuda_fail(e, "inverse opponent transform");
 }
 
 } // extern "C"

@@ -68,12 +68,15 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_denoise.argtypes = [vp, ci, ci, ci, cf, P, vp, vp, vp]
     lib.gbm3d_aggregate_noalloc.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp]
     lib.gbm3d_set_match_events.argtypes = [vp]
+    lib.gbm3d_workspace_bytes_color.argtypes = [ci, ci, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.gbm3d_denoise_color.argtypes = [vp, ci, ci, ci, ctypes.c_longlong, cf, P, vp, vp, vp]
     lib.gbm3d_match_stats.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.gbm3d_last_error_string.restype = ctypes.c_char_p
     lib.gbm3d_version.restype = ctypes.c_char_p
     for name in ("gbm3d_params_default", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
                  "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise",
-                 "gbm3d_aggregate_noalloc", "gbm3d_match_stats", "gbm3d_set_match_events"):
+                 "gbm3d_aggregate_noalloc", "gbm3d_match_stats", "gbm3d_set_match_events",
+                 "gbm3d_workspace_bytes_color", "gbm3d_denoise_color"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -133,6 +136,60 @@ def match(img: torch.Tensor, K: int, p: Params | None = None, with_dist: bool = 
     _check(load().gbm3d_match(_ptr(img), H, W, pitch, ctypes.byref(p), K, _ptr(idx), _ptr(dist), None,
                               _stream(img)))
     return idx, dist
+
+
+def workspace_bytes_color(H: int, W: int, p: Params | None = None) -> int:
+    p = p or params_default()
+    n = ctypes.c_size_t()
+    _check(load().gbm3d_workspace_bytes_color(H, W, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def denoise_color(noisy: torch.Tensor, sigma: float, p: Params | None = None, ws: torch.Tensor | None = None,
+                  out: torch.Tensor | None = None) -> torch.Tensor:
+    """Colour G-BM3D of a (3, H, W) float32 CUDA tensor of R, G, B planes
+    (rows contiguous; any row pitch and plane stride)."""
+    p = p or params_default()
+    if not (noisy.is_cuda and noisy.dtype == torch.float32 and noisy.dim() == 3 and noisy.shape[0] == 3
+            and noisy.stride(2) == 1):
+        raise ValueError("noisy must be a (3, H, W) float32 CUDA tensor with unit column stride")
+    _, H, W = noisy.shape
+    if ws is None:
+        ws = torch.empty(max(workspace_bytes_color(H, W, p), 1), dtype=torch.uint8, device=noisy.device)
+    if out is None:  # the same row pitch and plane stride as noisy (one pair for both in the ABI)
+        out = torch.empty_strided(noisy.shape, noisy.stride(), dtype=torch.float32, device=noisy.device)
+    if out.stride() != noisy.stride() or out.shape != noisy.shape:
+        raise ValueError("out must have the shape and strides of noisy")
+    _check(load().gbm3d_denoise_color(_ptr(noisy), H, W, noisy.stride(1), noisy.stride(0), float(sigma),
+                                      ctypes.byref(p), _ptr(out), _ptr(ws), _stream(noisy)))
+    return out
+
+
+def workspace_bytes_color(H: int, W: int, p: Params | None = None) -> int:
+    p = p or params_default()
+    n = ctypes.c_size_t()
+    _check(load().gbm3d_workspace_bytes_color(H, W, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def denoise_color(noisy: torch.Tensor, sigma: float, p: Params | None = None, ws: torch.Tensor | None = None,
+                  out: torch.Tensor | None = None) -> torch.Tensor:
+    """Colour G-BM3D of a (3, H, W) float32 CUDA tensor of R, G, B planes
+    (rows contiguous; any row pitch and plane stride)."""
+    p = p or params_default()
+    if not (noisy.is_cuda and noisy.dtype == torch.float32 and noisy.dim() == 3 and noisy.shape[0] == 3
+            and noisy.stride(2) == 1):
+        raise ValueError("noisy must be a (3, H, W) float32 CUDA tensor with unit column stride")
+    _, H, W = noisy.shape
+    if ws is None:
+        ws = torch.empty(max(workspace_bytes_color(H, W, p), 1), dtype=torch.uint8, device=noisy.device)
+    if out is None:  # the same row pitch and plane stride as noisy (one pair for both in the ABI)
+        out = torch.empty_strided(noisy.shape, noisy.stride(), dtype=torch.float32, device=noisy.device)
+    if out.stride() != noisy.stride() or out.shape != noisy.shape:
+        raise ValueError("out must have the shape and strides of noisy")
+    _check(load().gbm3d_denoise_color(_ptr(noisy), H, W, noisy.stride(1), noisy.stride(0), float(sigma),
+                                      ctypes.byref(p), _ptr(out), _ptr(ws), _stream(noisy)))
+    return out
 
 
 _match_events_keep = None
@@ -231,25 +288,34 @@ def denoise(noisy: torch.Tensor, sigma: float, p: Params | None = None, ws: torc
 
 class HostDenoiser:
     """End-to-end use from host memory: pinned host -> device copy, denoise,
-    device -> host copy, on one stream.  Buffers are allocated once per shape."""
+    device -> host copy, on one stream.  Buffers are allocated once per shape.
+    channels = 3: colour (R, G, B planes, gbm3d_denoise_color)."""
 
-    def __init__(self, H: int, W: int, p: Params | None = None, device="cuda"):
+    def __init__(self, H: int, W: int, p: Params | None = None, device="cuda", channels: int = 1):
         self.p = p or params_default()
-        self.H, self.W = H, W
-        self.dev_in = torch.empty((H, W), dtype=torch.float32, device=device)
-        self.dev_out = torch.empty((H, W), dtype=torch.float32, device=device)
-        self.host_out = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
-        self.ws = workspace(H, W, self.p, device)
+        self.H, self.W, self.C = H, W, channels
+        shape = (H, W) if channels == 1 else (channels, H, W)
+        self.dev_in = torch.empty(shape, dtype=torch.float32, device=device)
+        self.dev_out = torch.empty(shape, dtype=torch.float32, device=device)
+        self.host_out = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+        if channels == 1:
+            self.ws = workspace(H, W, self.p, device)
+        else:
+            n = workspace_bytes_color(H, W, self.p)
+            self.ws = torch.empty(max(n, 1), dtype=torch.uint8, device=device)
 
     @property
     def h2d_bytes(self) -> int:
-        return self.H * self.W * 4
+        return self.C * self.H * self.W * 4
 
     d2h_bytes = h2d_bytes
 
     def __call__(self, host_noisy: torch.Tensor, sigma: float) -> torch.Tensor:
         self.dev_in.copy_(host_noisy, non_blocking=True)
-        denoise(self.dev_in, sigma, self.p, self.ws, self.dev_out)
+        if self.C == 1:
+            denoise(self.dev_in, sigma, self.p, self.ws, self.dev_out)
+        else:
+            denoise_color(self.dev_in, sigma, self.p, self.ws, self.dev_out)
         self.host_out.copy_(self.dev_out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return self.host_out

@@ -111,6 +111,26 @@ def test_validation_errors(g):
                                None) == g.EUNSUPPORTED
 
 
+def test_color_validation(g):
+    lib = g.load()
+    p = g.params_default()
+    P = ctypes.byref(p)
+    fake, fake2, ws = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x900000), ctypes.c_void_p(0x2000000)
+    sig = ctypes.c_float(0.1)
+    # planes overlapping (plane stride below one plane)
+    assert lib.gbm3d_denoise_color(fake, 64, 64, 64, 64 * 63, sig, P, fake2, ws, None) == g.EINVAL
+    # out overlapping noisy
+    assert lib.gbm3d_denoise_color(fake, 64, 64, 64, 64 * 64, sig, P, ctypes.c_void_p(0x100000 + 4 * 64 * 64),
+                                   ws, None) == g.EINVAL
+    # translations other than 1
+    q = p.replace(translations=2)
+    assert lib.gbm3d_denoise_color(fake, 64, 64, 64, 64 * 64, sig, ctypes.byref(q), fake2, ws, None) == g.EUNSUPPORTED
+    n = ctypes.c_size_t()
+    assert lib.gbm3d_workspace_bytes_color(64, 64, ctypes.byref(q), ctypes.byref(n)) == g.EUNSUPPORTED
+    # the colour workspace is the grayscale one plus six planes
+    assert g.workspace_bytes_color(256, 256) == g.workspace_bytes(256, 256) + 6 * 256 * 256 * 4
+
+
 def test_empty_image_rejected(g):
     lib = g.load()
     p = g.params_default()

@@ -63,3 +63,14 @@ def test_tc_executed_flop_closed_form():
     # chunks per tile column, 43 tile columns, 3 x 2 x 128 x 128 x 64 FLOP each
     import bench
     assert bench.tc_executed_flop(1024, 1024) == 883 * 43 * 3 * 2 * 128 * 128 * 64
+
+
+def test_launch_count_matches_launch_list():
+    # one 1024^2 grayscale denoise launched 35 kernels in the ncu launch list
+    # (profiles/launches_denoise_1024.md: 142 launches over 4 denoises, 2 of
+    # them the bench's L2-flush fill)
+    import bench
+    from types import SimpleNamespace
+    p = SimpleNamespace(cycle_spins=2, levels=3, stages=2)
+    assert bench.launches_per_denoise(p, 1) == 35 == (142 - 2) // 4
+    assert bench.launches_per_denoise(p, 3) == 71
