@@ -2,12 +2,14 @@
 // 2-D DCT on the blocks, 1-D Haar along the group, Wiener shrinkage against
 // the pilot, inverse, group weight).
 //
-// One CTA per group, K*8 threads: thread (r, a) owns row a of block r while
-// the 8-point DCTs run (even/odd butterfly of the orthonormal DCT-II), then
-// one thread per coefficient position runs the full-depth Haar along the K
-// blocks in registers.  Both groups (noisy and pilot) are gathered straight
-// from the images; the filtered group is written once, coalesced, in the
-// group-major layout [g][r][a][b].
+// One CTA per group, K*8 threads.  Thread (r, c) reads column c of block r of
+// both groups (noisy and pilot) straight from the images -- 8 lanes cover one
+// 32-byte block row per load -- and runs the column DCT in registers (even/odd
+// butterfly of the orthonormal DCT-II); the row DCTs go through a
+// bank-conflict-free shared layout, one thread per coefficient position runs
+// the full-depth Haar along the K blocks in registers, and the inverse ends
+// with the column pass writing the filtered group straight out, again 8 lanes
+// per block row.
 #include "internal.cuh"
 
 namespace gbm3d {
@@ -123,27 +125,7 @@ __device__ __forceinline__ void haar_inv_lanes(float *v, int q)
     haar_inv<8>(v);
 }
 
-// Row a of a block: the 8 floats at rowp[l .. l+7].  VEC: three aligned float4
-// loads (the third only when l is not 4-aligned) and a shift by l & 3.
-template <bool VEC>
-__device__ __forceinline__ void load_row8(const float *__restrict__ rowp, int l, float *v)
-{
-    if (VEC) {
-        const float4 *q = reinterpret_cast<const float4 *>(rowp + (l & ~3));
-        const int sft = l & 3;
-        const float4 A = __ldg(q), B = __ldg(q + 1);
-        const float4 C = sft ? __ldg(q + 2) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float w[12] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, C.x, C.y, C.z, C.w};
-#pragma unroll
-        for (int b = 0; b < 8; b++)
-            v[b] = sft == 0 ? w[b] : sft == 1 ? w[b + 1] : sft == 2 ? w[b + 2] : w[b + 3];
-    } else {
-#pragma unroll
-        for (int b = 0; b < 8; b++) v[b] = __ldg(rowp + l + b);
-    }
-}
-
-template <int K, bool VEC>
+template <int K>
 __global__ void __launch_bounds__(K * 8)
 k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ pilot, int ppitch, int H, int W,
          const int32_t *__restrict__ idx, float sigma2, float eps_w, GroupOut out)
@@ -152,36 +134,50 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
     __shared__ float sp[SZ];
     __shared__ float sq[SZ];
     __shared__ float red[NT / 32];
+    __shared__ long long s_zoff[K], s_poff[K]; // block r's top-left in the noisy and the pilot image
+    __shared__ long long s_slot[K];      // block r's slot in the output
     const int g = blockIdx.x, t = threadIdx.x;
     const int r = t >> 3, a = t & 7; // row and column passes: (block r, row/column a)
-    {
+    if (t < K) {
         int k, l;
-        block_kl(__ldg(idx + (size_t)g * K + r), H, W, k, l);
+        block_kl(__ldg(idx + (size_t)g * K + t), H, W, k, l);
+        s_zoff[t] = (long long)k * npitch + l;
+        s_poff[t] = (long long)k * ppitch + l;
+        s_slot[t] = out.slot((long long)g * K + t);
+    }
+    __syncthreads();
+    const int cb = a; // in the column phases thread (r, a) owns column a of block r
+    { // columns first, straight from global: 8 lanes read one 32-byte block row
+        // per load; the column DCT runs in registers
+        const float *zc = noisy + s_zoff[r] + cb, *pc = pilot + s_poff[r] + cb;
         float xz[8], xy[8];
-        load_row8<VEC>(noisy + (size_t)(k + a) * npitch, l, xz);
-        load_row8<VEC>(pilot + (size_t)(k + a) * ppitch, l, xy);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            xz[u] = __ldg(zc + (long long)u * npitch);
+            xy[u] = __ldg(pc + (long long)u * ppitch);
+        }
+        dct8(xz);
+        dct8(xy);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            sq[sidx(r, u, cb)] = xz[u];
+            sp[sidx(r, u, cb)] = xy[u];
+        }
+    }
+    __syncthreads();
+    { // rows: thread (r, a)
+        float xz[8], xy[8];
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            xz[b] = sq[sidx(r, a, b)];
+            xy[b] = sp[sidx(r, a, b)];
+        }
         dct8(xz);
         dct8(xy);
 #pragma unroll
         for (int b = 0; b < 8; b++) {
             sq[sidx(r, a, b)] = xz[b];
             sp[sidx(r, a, b)] = xy[b];
-        }
-    }
-    __syncthreads();
-    { // columns: thread (r, b = a)
-        float xz[8], xy[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            xz[u] = sq[sidx(r, u, a)];
-            xy[u] = sp[sidx(r, u, a)];
-        }
-        dct8(xz);
-        dct8(xy);
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            sq[sidx(r, u, a)] = xz[u];
-            sp[sidx(r, u, a)] = xy[u];
         }
     }
     __syncthreads();
@@ -217,39 +213,36 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
         float s = 0.f;
         for (int i = 0; i < NT / 32; i++) s += red[i];
         const float wv = 1.f / fmaxf(sigma2 * s, eps_w);
-        if (out.per_slot) out.w[out.slot((long long)g * K + t)] = wv;
+        if (out.per_slot) out.w[s_slot[t]] = wv;
         else if (t == 0) out.w[g] = wv;
     }
-    { // inverse columns
-        float x[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) x[u] = sq[sidx(r, u, a)];
-        idct8(x);
-#pragma unroll
-        for (int u = 0; u < 8; u++) sq[sidx(r, u, a)] = x[u];
-    }
-    __syncthreads();
-    {
+    { // inverse rows
         float x[8];
 #pragma unroll
         for (int b = 0; b < 8; b++) x[b] = sq[sidx(r, a, b)];
         idct8(x);
-        float4 *o = reinterpret_cast<float4 *>(out.row((long long)g * K + r, a));
-        o[0] = make_float4(x[0], x[1], x[2], x[3]);
-        o[1] = make_float4(x[4], x[5], x[6], x[7]);
+#pragma unroll
+        for (int b = 0; b < 8; b++) sq[sidx(r, a, b)] = x[b];
+    }
+    __syncthreads();
+    { // inverse columns, written straight out: 8 lanes per 32-byte block row
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) x[u] = sq[sidx(r, u, cb)];
+        idct8(x);
+        float *o = out.base + s_slot[r] * out.s_slot + cb;
+#pragma unroll
+        for (int u = 0; u < 8; u++) o[u * out.s_row] = x[u];
     }
 }
 
 } // namespace
 
 template <int K>
-static void wiener_k(bool vec, int G, const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
+static void wiener_k(int G, const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
                      const int32_t *idx, float s2, float eps_w, const GroupOut &out, cudaStream_t st)
 {
-    if (vec)
-        k_wiener<K, true><<<G, K * 8, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out);
-    else
-        k_wiener<K, false><<<G, K * 8, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out);
+    k_wiener<K><<<G, K * 8, 0, st>>>(noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out);
 }
 
 cudaError_t launch_filter_wiener(const float *noisy, int npitch, const float *pilot, int ppitch, int H, int W,
@@ -257,14 +250,10 @@ cudaError_t launch_filter_wiener(const float *noisy, int npitch, const float *pi
                                  cudaStream_t st)
 {
     const float s2 = sigma * sigma;
-    // Vector row loads read up to 3 floats past a block row, inside the same
-    // 4-aligned span: safe when W, both pitches and both bases are 4-aligned.
-    const bool vec = (W % 4 == 0) && (npitch % 4 == 0) && (ppitch % 4 == 0) && ((uintptr_t)noisy % 16 == 0) &&
-                     ((uintptr_t)pilot % 16 == 0);
     switch (K) {
-    case 8: wiener_k<8>(vec, G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
-    case 16: wiener_k<16>(vec, G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
-    case 32: wiener_k<32>(vec, G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
+    case 8: wiener_k<8>(G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
+    case 16: wiener_k<16>(G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
+    case 32: wiener_k<32>(G, noisy, npitch, pilot, ppitch, H, W, idx, s2, eps_w, out, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
