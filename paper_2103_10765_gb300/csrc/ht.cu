@@ -298,21 +298,47 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
         z0 = pwrap(2 * m - shift, Zo);
         z1 = pwrap(2 * m + 1 - shift, Zo);
     }
-    for (int orow = tid >> 6; orow < 2 * TY; orow += 4) {
-        const int ys = 2 * y0 + orow;
-        if (ys >= Yo) break;
-        const float L = s_o[0][orow][col], Hh = s_o[1][orow][col];
-        const float v0 = (L + Hh) * kS, v1 = (L - Hh) * kS;
-        if (SCATTER) {
-            const int y = pwrap(ys - shift, Yo);
-            const long long g = (long long)(y >> 3) * Bx + gx;
-            float *p0 = out.row(g * Zo + z0, y & 7) + bx;
-            float *p1 = out.row(g * Zo + z1, y & 7) + bx;
-            *p0 = accumulate ? (*p0 + scale * v0) : scale * v0;
-            *p1 = accumulate ? (*p1 + scale * v1) : scale * v1;
-        } else {
-            dst[((size_t)(2 * m) * Yo + ys) * Xo + xo] = v0;
-            dst[((size_t)(2 * m + 1) * Yo + ys) * Xo + xo] = v1;
+    if (SCATTER) {
+        // this thread's 8 output rows: every destination and, when averaging
+        // spins, every previous value first (16 loads in flight), then the stores
+        constexpr int NRO = 2 * TY / 4;
+        float *p0[NRO], *p1[NRO];
+        float o0[NRO], o1[NRO];
+#pragma unroll
+        for (int i = 0; i < NRO; i++) {
+            const int orow = (tid >> 6) + 4 * i, ys = 2 * y0 + orow;
+            p0[i] = p1[i] = nullptr;
+            if (ys < Yo) {
+                const int y = pwrap(ys - shift, Yo);
+                const long long g = (long long)(y >> 3) * Bx + gx;
+                p0[i] = out.row(g * Zo + z0, y & 7) + bx;
+                p1[i] = out.row(g * Zo + z1, y & 7) + bx;
+            }
+            o0[i] = o1[i] = 0.f;
+        }
+        if (accumulate) {
+#pragma unroll
+            for (int i = 0; i < NRO; i++)
+                if (p0[i]) {
+                    o0[i] = *p0[i];
+                    o1[i] = *p1[i];
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < NRO; i++)
+            if (p0[i]) {
+                const int orow = (tid >> 6) + 4 * i;
+                const float L = s_o[0][orow][col], Hh = s_o[1][orow][col];
+                *p0[i] = o0[i] + scale * ((L + Hh) * kS);
+                *p1[i] = o1[i] + scale * ((L - Hh) * kS);
+            }
+    } else {
+        for (int orow = tid >> 6; orow < 2 * TY; orow += 4) {
+            const int ys = 2 * y0 + orow;
+            if (ys >= Yo) break;
+            const float L = s_o[0][orow][col], Hh = s_o[1][orow][col];
+            dst[((size_t)(2 * m) * Yo + ys) * Xo + xo] = (L + Hh) * kS;
+            dst[((size_t)(2 * m + 1) * Yo + ys) * Xo + xo] = (L - Hh) * kS;
         }
     }
 }
