@@ -200,9 +200,10 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
 
 // The same sums over the planar, position-sorted layout: row a of slot j is
 // the 8 floats at planes + a * plane_stride + 8 j, its weight w_slot[j], its
-// block column lpos[j].  For one block row k the slots of positions
-// k*W + la .. k*W + lb are one contiguous range, walked in order (= columns
-// ascending, entries ascending: the same per-pixel order as k_gather), so
+// block column lpos[j].  For one block row k the slots of the blocks
+// covering pixel x (positions k*W + x-7 .. k*W + x) are one contiguous range,
+// walked in order (= columns ascending, entries ascending: the same
+// per-pixel order as k_gather), so each lane visits only its own blocks and
 // the reads stream through memory.
 __global__ void __launch_bounds__(256)
 k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_slot, const int *__restrict__ off,
@@ -223,26 +224,30 @@ k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_sl
     const bool xin = x < W;
     float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
     const int ka = max(0, y - 7), kb = min(y, H - 8);
-    const int la = max(0, x0 - 7), lb = min(x0 + 7, W - 8);
+    // the blocks of block row k covering pixel x have columns lo .. hi, and
+    // their slots are one contiguous range (positions in order, entries in
+    // order within a position): each lane walks exactly its own range
+    const int lo = max(0, x - 7), hi = min(x, W - 8);
+    const bool any = xin && lo <= hi;
     for (int k = ka; k <= kb; k++) {
         const int a = y - k;
         const float wa = sw[a];
         const float *plane = planes + a * plane_stride;
-        const int s0 = __ldg(off + k * W + la), s1 = __ldg(off + k * W + lb + 1);
+        const int s0 = any ? __ldg(off + k * W + lo) : 0, s1 = any ? __ldg(off + k * W + hi + 1) : 0;
         for (int e0 = s0; e0 < s1; e0 += 8) { // chunks of 8 slots, loads issued before use
             int bq[8];
 #pragma unroll
-            for (int q = 0; q < 8; q++) bq[q] = e0 + q < s1 ? x - __ldg(lpos + e0 + q) : -1;
+            for (int q = 0; q < 8; q++) bq[q] = e0 + q < s1 ? x - __ldg(lpos + e0 + q) : 0;
             float wq[8], vq[8];
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                const bool ok = xin && bq[q] >= 0 && bq[q] < 8;
+                const bool ok = e0 + q < s1;
                 wq[q] = ok ? __ldg(w_slot + e0 + q) : 0.f;
                 vq[q] = ok ? __ldg(plane + (size_t)(e0 + q) * 8 + bq[q]) : 0.f;
             }
 #pragma unroll
             for (int q = 0; q < 8; q++)
-                if (xin && bq[q] >= 0 && bq[q] < 8) {
+                if (e0 + q < s1) {
                     const float wt = wq[q] * wa * sw[bq[q]];
                     kahan_add(num, cn, wt * vq[q]);
                     kahan_add(den, cd, wt);

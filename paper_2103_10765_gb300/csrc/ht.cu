@@ -384,13 +384,14 @@ __global__ void __launch_bounds__(kTvWarps * 32) k_tv(const float *__restrict__ 
         if (lane == 0) out.w[g] = wv;
         return;
     }
+    // two lanes per block row q = 8 r + a, one float4 each: every 32-byte row
+    // (one sector) is written whole by one instruction, 16 rows per instruction
+    const int h = lane & 1;
 #pragma unroll
-    for (int i = 0; i < K * 8 / 32; i++) { // block row q = 8 r + a
-        const int q = lane + 32 * i;
+    for (int i = 0; i < K * 8 / 16; i++) {
+        const int q = (lane >> 1) + 16 * i;
         const float4 *s = reinterpret_cast<const float4 *>(u + q * 8);
-        float4 *d = reinterpret_cast<float4 *>(out.row((long long)g * K + (q >> 3), q & 7));
-        d[0] = s[0];
-        d[1] = s[1];
+        reinterpret_cast<float4 *>(out.row((long long)g * K + (q >> 3), q & 7))[h] = s[h];
     }
     if (lane < K) out.w[out.slot((long long)g * K + lane)] = wv;
 }
