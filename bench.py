@@ -164,33 +164,63 @@ def candidate_pairs(Hh, Ww, N=8, s=3, R=19):
 
 
 class ClockSampler:
+    """nvidia-smi clock/throttle sampler.  Samples are read by a thread and stamped on
+    arrival; only those taken while the timed region runs (between mark_start() and
+    mark_end()) enter the summary.  __enter__ waits for the first sample so the sampler
+    is already running when the timed region starts."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.stamped = []
+        self.t0 = self.t1 = None
+
+    def _reader(self):
+        for ln in self.proc.stdout:
+            if ln.strip():
+                self.stamped.append((time.monotonic(), ln))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._reader, daemon=True)
+        self.thread.start()
+        deadline = time.monotonic() + 5.0
+        while not self.stamped and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
+        # one more period so the sample covering the end of the region arrives
+        time.sleep(self.PERIOD_MS / 1000.0 * 1.5)
 
     def __exit__(self, *a):
         self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+                self.proc.wait()
+            self.thread.join(timeout=5)
+            t0 = self.t0 if self.t0 is not None else -math.inf
+            t1 = (self.t1 if self.t1 is not None else math.inf) + self.PERIOD_MS / 1000.0
+            self.lines = [ln for t, ln in self.stamped if t0 <= t <= t1]
 
     def summary(self):
         mhz, mx, reasons = [], None, set()
@@ -249,7 +279,7 @@ def reference_arm(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
@@ -305,6 +335,7 @@ def main():
             e.record(stream)  # creates the underlying CUDA event
     barrier()
     with ClockSampler(local) as clk:
+        clk.mark_start()
         for i in range(args.steps):
             flush.zero_()
             gbm3d.set_match_events(mev[i])
@@ -312,6 +343,7 @@ def main():
             run(noisy[i % 3])
             ev[i][1].record(stream)
         barrier()
+        clk.mark_end()
     gbm3d.set_match_events(None)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     match_ms = [[e4[0].elapsed_time(e4[1]) for e4 in mev], [e4[2].elapsed_time(e4[3]) for e4 in mev]]

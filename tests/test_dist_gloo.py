@@ -74,3 +74,34 @@ def test_launch_count_matches_launch_list():
     p = SimpleNamespace(cycle_spins=2, levels=3, stages=2)
     assert bench.launches_per_denoise(p, 1) == 35 == (142 - 2) // 4
     assert bench.launches_per_denoise(p, 3) == 71
+
+
+def test_clock_sampler_keeps_only_timed_window(tmp_path, monkeypatch):
+    """The bench's clock record holds the samples taken while the timed region ran:
+    a fake nvidia-smi reports 1000 MHz before the region and 2070 MHz with
+    sw_power_cap during it."""
+    import time
+
+    import bench
+    flag = tmp_path / "in_region"
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    f"while true; do if [ -e {flag} ]; then "
+                    "echo '0, 2070, 2070, 900.0, Not Active, Not Active, Not Active, Active'; "
+                    "else echo '0, 1000, 2070, 100.0, Not Active, Not Active, Not Active, Not Active'; fi; "
+                    "sleep 0.05; done\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    with bench.ClockSampler(0) as clk:
+        assert clk.stamped, "sampler did not start"
+        flag.touch()
+        time.sleep(0.12)
+        clk.mark_start()
+        time.sleep(0.4)
+        clk.mark_end()
+        flag.unlink()
+        time.sleep(0.15)
+    s = clk.summary()
+    assert s["samples"] >= 4
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
