@@ -53,7 +53,8 @@ _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("patch", "step", "search_radius", "k1", "k2", "levels", "cycle_spins", "translations", "stages")] + \
-               [(n, ctypes.c_double) for n in ("tau_a", "tau_b", "kaiser_beta", "eps_w")]
+               [(n, ctypes.c_double) for n in ("tau_a", "tau_b", "kaiser_beta", "eps_w")] + \
+               [(n, ctypes.c_int) for n in ("patch2", "step2")]
 
 
 def _declare(lib):
@@ -115,10 +116,20 @@ class Params:
     tau_b: float = 0.3
     kaiser_beta: float = 2.0
     eps_w: float = 1e-8
+    patch2: int = 0  # stage-2 block side (0: patch)
+    step2: int = 0   # stage-2 grid stride (0: step)
+
+    @classmethod
+    def paper(cls) -> "Params":
+        """The Sec. 5 parameter list: N = 16 tiling blocks in stage 1, N = 8 in
+        stage 2 (s = N in both), a 32-pixel search window read as R = 16,
+        K = 16 in both stages, 3 levels, 2 cycle spins, 2 translations."""
+        return cls(patch=16, step=16, search_radius=16, k1=16, k2=16, translations=2, patch2=8, step2=8)
 
     def c(self):
         return _Params(self.patch, self.step, self.search_radius, self.k1, self.k2, self.levels, self.cycle_spins,
-                       self.translations, self.stages, self.tau_a, self.tau_b, self.kaiser_beta, self.eps_w)
+                       self.translations, self.stages, self.tau_a, self.tau_b, self.kaiser_beta, self.eps_w,
+                       self.patch2, self.step2)
 
 
 def max_threads() -> int:

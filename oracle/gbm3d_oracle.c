@@ -668,10 +668,35 @@ int orc_aggregate(const double *groups, const double *w, const int32_t *idx, int
  * Reading: stage 2 matches on the stage-1 estimate (Sec. 1.1) and filters the
  * noisy image with the stage-1 estimate as pilot (Sec. 4); both images are
  * translated together. */
+/* patch / step: block side N and grid stride of stage 1; patch2 / step2 those
+ * of stage 2 (0 = the stage-1 value).  Sec. 5 uses N = 16 in stage 1 and
+ * N = 8 in stage 2, each grid tiling the image (s = N). */
 typedef struct {
     int patch, step, search_radius, k1, k2, levels, cycle_spins, translations, stages;
     double tau_a, tau_b, kaiser_beta, eps_w;
+    int patch2, step2;
 } orc_params;
+
+static int stage_patch(const orc_params *p, int stage)
+{
+    return (stage == 2 && p->patch2 > 0) ? p->patch2 : p->patch;
+}
+
+static int stage_step(const orc_params *p, int stage)
+{
+    return (stage == 2 && p->step2 > 0) ? p->step2 : p->step;
+}
+
+/* Reading: the translations h in {0, N/4, N/2} of eq. firstEst use the block
+ * side N of the stage they wrap (stage 2 repeats the strategy "just as in the
+ * first step", Sec. 4, with its own N). */
+static void stage_shifts(const orc_params *p, int stage, int hs[3])
+{
+    const int N = stage_patch(p, stage);
+    hs[0] = 0;
+    hs[1] = N / 4;
+    hs[2] = N / 2;
+}
 
 static void shift2(const double *src, double *dst, int H, int W, int h)
 {
@@ -702,14 +727,14 @@ static int stage1(const double *Z, int H, int W, double sigma, const orc_params 
 static int stage2(const double *Z, const double *Y1, int H, int W, double sigma, const orc_params *p,
                   double *out, int nt)
 {
-    int N = p->patch, K = p->k2;
-    int By = orc_grid(H, N, p->step, NULL), Bx = orc_grid(W, N, p->step, NULL);
+    int N = stage_patch(p, 2), K = p->k2, s = stage_step(p, 2);
+    int By = orc_grid(H, N, s, NULL), Bx = orc_grid(W, N, s, NULL);
     size_t G = (size_t)By * Bx;
     int32_t *idx = malloc(sizeof(int32_t) * G * K);
     double *gr = malloc(sizeof(double) * G * K * N * N), *w = malloc(sizeof(double) * G);
     int st = ORC_ENOMEM;
     if (idx && gr && w) {
-        st = orc_match(Y1, H, W, N, p->step, p->search_radius, K, idx, NULL, nt);
+        st = orc_match(Y1, H, W, N, s, p->search_radius, K, idx, NULL, nt);
         if (st == ORC_OK) st = orc_filter_wiener(Z, Y1, H, W, idx, (int)G, N, K, sigma, p->eps_w, gr, w, nt);
         if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, p->kaiser_beta, out);
     }
@@ -720,11 +745,13 @@ static int stage2(const double *Z, const double *Y1, int H, int W, double sigma,
 int orc_denoise(const double *Z, int H, int W, double sigma, const orc_params *p, double *out,
                 double *y1_out, int nthreads)
 {
-    if (!Z || !p || !out || H < p->patch || W < p->patch || p->translations < 1 || p->translations > 3 ||
-        p->stages < 1 || p->stages > 2 || sigma < 0)
+    if (!Z || !p || !out || H < p->patch || W < p->patch || H < stage_patch(p, 2) || W < stage_patch(p, 2) ||
+        p->translations < 1 || p->translations > 3 || p->stages < 1 || p->stages > 2 || sigma < 0)
         return ORC_EINVAL;
     size_t n = (size_t)H * W;
-    int hs[3] = {0, p->patch / 4, p->patch / 2};
+    int hs[3], hs2[3];
+    stage_shifts(p, 1, hs);
+    stage_shifts(p, 2, hs2);
     double *zs = malloc(sizeof(double) * n), *ys = malloc(sizeof(double) * n);
     double *o = malloc(sizeof(double) * n), *y1 = calloc(n, sizeof(double));
     int st = (zs && ys && o && y1) ? ORC_OK : ORC_ENOMEM;
@@ -740,10 +767,10 @@ int orc_denoise(const double *Z, int H, int W, double sigma, const orc_params *p
         double *y2 = calloc(n, sizeof(double)), *y1s = malloc(sizeof(double) * n);
         if (!y2 || !y1s) st = ORC_ENOMEM;
         for (int t = 0; t < p->translations && st == ORC_OK; t++) {
-            shift2(Z, zs, H, W, hs[t]);
-            shift2(y1, y1s, H, W, hs[t]);
+            shift2(Z, zs, H, W, hs2[t]);
+            shift2(y1, y1s, H, W, hs2[t]);
             st = stage2(zs, y1s, H, W, sigma, p, o, nthreads);
-            shift2(o, ys, H, W, -hs[t]);
+            shift2(o, ys, H, W, -hs2[t]);
             for (size_t e = 0; e < n; e++) y2[e] += ys[e] / p->translations;
         }
         if (st == ORC_OK) memcpy(out, y2, sizeof(double) * n);
@@ -796,13 +823,14 @@ double orc_opp_sigma_scale(int c)
 static int stage_color(const double *Zo, const double *Y1o, int H, int W, double sigma, const orc_params *p,
                        double *out, int nt)
 {
-    const int N = p->patch, K = Y1o ? p->k2 : p->k1;
-    const int By = orc_grid(H, N, p->step, NULL), Bx = orc_grid(W, N, p->step, NULL);
+    const int sg = Y1o ? 2 : 1;
+    const int N = stage_patch(p, sg), K = Y1o ? p->k2 : p->k1, s = stage_step(p, sg);
+    const int By = orc_grid(H, N, s, NULL), Bx = orc_grid(W, N, s, NULL);
     const size_t G = (size_t)By * Bx, n = (size_t)H * W;
     int32_t *idx = malloc(sizeof(int32_t) * G * K);
     double *gr = malloc(sizeof(double) * G * K * N * N), *w = malloc(sizeof(double) * G);
     int st = (idx && gr && w) ? ORC_OK : ORC_ENOMEM;
-    if (st == ORC_OK) st = orc_match(Y1o ? Y1o : Zo, H, W, N, p->step, p->search_radius, K, idx, NULL, nt);
+    if (st == ORC_OK) st = orc_match(Y1o ? Y1o : Zo, H, W, N, s, p->search_radius, K, idx, NULL, nt);
     for (int c = 0; c < 3 && st == ORC_OK; c++) {
         const double sc = sigma * orc_opp_sigma_scale(c);
         if (!Y1o) {
@@ -821,11 +849,13 @@ static int stage_color(const double *Zo, const double *Y1o, int H, int W, double
 /* Colour denoising of Z (3 planes R, G, B of H x W) into out (3 planes). */
 int orc_denoise_color(const double *Z, int H, int W, double sigma, const orc_params *p, double *out, int nthreads)
 {
-    if (!Z || !p || !out || H < p->patch || W < p->patch || p->translations < 1 || p->translations > 3 ||
-        p->stages < 1 || p->stages > 2 || sigma < 0)
+    if (!Z || !p || !out || H < p->patch || W < p->patch || H < stage_patch(p, 2) || W < stage_patch(p, 2) ||
+        p->translations < 1 || p->translations > 3 || p->stages < 1 || p->stages > 2 || sigma < 0)
         return ORC_EINVAL;
     const size_t n = (size_t)H * W;
-    const int hs[3] = {0, p->patch / 4, p->patch / 2};
+    int hs[3], hs2[3];
+    stage_shifts(p, 1, hs);
+    stage_shifts(p, 2, hs2);
     double *zo = malloc(sizeof(double) * 3 * n), *zs = malloc(sizeof(double) * 3 * n);
     double *o = malloc(sizeof(double) * 3 * n), *os = malloc(sizeof(double) * 3 * n);
     double *y1 = calloc(3 * n, sizeof(double)), *y1s = malloc(sizeof(double) * 3 * n);
@@ -843,12 +873,12 @@ int orc_denoise_color(const double *Z, int H, int W, double sigma, const orc_par
     if (st == ORC_OK && p->stages == 1) memcpy(acc, y1, sizeof(double) * 3 * n);
     for (int t = 0; p->stages == 2 && t < p->translations && st == ORC_OK; t++) {
         for (int c = 0; c < 3; c++) {
-            shift2(zo + c * n, zs + c * n, H, W, hs[t]);
-            shift2(y1 + c * n, y1s + c * n, H, W, hs[t]);
+            shift2(zo + c * n, zs + c * n, H, W, hs2[t]);
+            shift2(y1 + c * n, y1s + c * n, H, W, hs2[t]);
         }
         st = stage_color(zs, y1s, H, W, sigma, p, o, nthreads);
         for (int c = 0; c < 3 && st == ORC_OK; c++) {
-            shift2(o + c * n, os + c * n, H, W, -hs[t]);
+            shift2(o + c * n, os + c * n, H, W, -hs2[t]);
             for (size_t e = 0; e < n; e++) acc[c * n + e] += os[c * n + e] / p->translations;
         }
     }

@@ -33,7 +33,8 @@ def test_grid_closed_form(orc):
             assert np.all(np.diff(g) > 0) and np.all(np.diff(g)[:-1] == s)
 
 
-@pytest.mark.parametrize("H,W,N,R,K", [(16, 16, 4, 3, 5), (20, 13, 4, 3, 8), (24, 24, 8, 19, 16), (17, 30, 8, 5, 32)])
+@pytest.mark.parametrize("H,W,N,R,K", [(16, 16, 4, 3, 5), (20, 13, 4, 3, 8), (24, 24, 8, 19, 16), (17, 30, 8, 5, 32),
+                                       (37, 29, 16, 6, 16)])
 def test_match_brute_force(orc, rng, H, W, N, R, K):
     X = rng.random((H, W))
     idx, dist = orc.match(X, N=N, s=3, R=R, K=K)

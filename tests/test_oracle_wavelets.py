@@ -141,13 +141,17 @@ def _dense_ht(V, sigma, L, C, tau_a, tau_b):
     return U
 
 
-@pytest.mark.parametrize("C", [1, 2])
-def test_filter_ht_matches_dense_evaluation(orc, C):
+@pytest.mark.parametrize("C,N,s,R,H,W", [(1, 8, 3, 19, 16, 22), (2, 8, 3, 19, 16, 22),
+                                          (2, 16, 16, 16, 32, 40)])
+def test_filter_ht_matches_dense_evaluation(orc, C, N, s, R, H, W):
+    """Sec. 3.1 eq. BM3DHT with cycle spinning, evaluated with dense per-axis
+    matrices; the last case is the Sec. 5 stage-1 geometry (16 x 16 blocks
+    tiling the image)."""
     from paper_2103_10765_gb300 import synth
-    clean, Zimg = synth.make_pair(16, 22, 25 / 255, 3)
-    N, K, sigma = 8, 16, 25 / 255
-    idx, _ = orc.match(Zimg, N=N, s=3, R=19, K=K)
-    gy, gx = orc.grid(16, N, 3), orc.grid(22, N, 3)
+    clean, Zimg = synth.make_pair(H, W, 25 / 255, 3)
+    K, sigma = 16, 25 / 255
+    idx, _ = orc.match(Zimg, N=N, s=s, R=R, K=K)
+    gy, gx = orc.grid(H, N, s), orc.grid(W, N, s)
     By, Bx = len(gy), len(gx)
     groups, w = orc.filter_ht(Zimg, idx, sigma, By, Bx, N=N, K=K, L=3, C=C)
     # volume V[pN+a, qN+b, r] = Z[k_r + a, l_r + b]
@@ -157,7 +161,7 @@ def test_filter_ht_matches_dense_evaluation(orc, C):
         for q in range(Bx):
             for r in range(K):
                 v = idx[p * Bx + q, r]
-                i, j = divmod(int(v), 22)
+                i, j = divmod(int(v), W)
                 V[p * N:(p + 1) * N, q * N:(q + 1) * N, r] = Zd[i:i + N, j:j + N]
     U = _dense_ht(V, sigma, 3, C, 3.6, 0.3)
     for p in range(By):

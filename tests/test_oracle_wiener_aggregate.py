@@ -108,16 +108,17 @@ def _brute_aggregate(groups, w, idx, H, W, N, kap):
     return num / den
 
 
-@pytest.mark.parametrize("beta", [0.0, 2.0])
-def test_aggregate_brute_force(orc, rng, beta):
-    _, Z = synth.make_pair(30, 27, 0.1, 1)
-    idx, _ = orc.match(Z, K=16)
+@pytest.mark.parametrize("beta,N,s", [(0.0, 8, 3), (2.0, 8, 3), (0.0, 16, 16), (2.0, 16, 5)])
+def test_aggregate_brute_force(orc, rng, beta, N, s):
+    _, Z = synth.make_pair(30 + N, 27 + N, 0.1, 1)
+    H, W = Z.shape
+    idx, _ = orc.match(Z, N=N, s=s, R=7, K=16)
     G = len(idx)
-    groups = rng.standard_normal((G, 16, 8, 8))
+    groups = rng.standard_normal((G, 16, N, N))
     w = rng.random(G) + 0.1
-    out = orc.aggregate(groups, w, idx, 30, 27, beta=beta)
-    kap = np.kaiser(8, beta) if beta > 0 else np.ones(8)
-    np.testing.assert_allclose(out, _brute_aggregate(groups, w, idx, 30, 27, 8, kap), atol=1e-12)
+    out = orc.aggregate(groups, w, idx, H, W, N=N, beta=beta)
+    kap = np.kaiser(N, beta) if beta > 0 else np.ones(N)
+    np.testing.assert_allclose(out, _brute_aggregate(groups, w, idx, H, W, N, kap), atol=1e-12)
 
 
 def test_aggregate_invariants(orc, rng):
