@@ -50,18 +50,31 @@ WORKLOADS = {
     "color2048": dict(H=2048, W=2048, C=3, cpu_crop=256, ref_crop=128,
                       desc="two-stage colour G-BM3D, 2048x2048x3 RGB fp32 (opponent transform, matching on luma, "
                            "per-channel sigma), sigma 25/255, " + _PARAMS),
+    # the Sec. 5 parameter list (library preset 1): tiling reference grids
+    "paper1024": dict(H=1024, W=1024, C=1, cpu_crop=512, ref_crop=256, preset=1,
+                      desc="two-stage G-BM3D, 1024x1024 grayscale fp32, sigma 25/255, Sec. 5 parameters: stage 1 "
+                           "N=16 s=16, stage 2 N=8 s=8, R=16, K1=K2=16, 3 levels bior1.5/Haar, 2 cycle spins, "
+                           "2 translations"),
 }
 H = W = 1024
 C = 1                   # channels
+PRESET = 0              # library parameter preset of the workload
 WORKLOAD = WORKLOADS["gray1024"]["desc"]
 CPU_CROP = 512          # cpu_baseline sample: top-left crop of the workload image
 REF_CROP = 256          # --impl reference: crop per step
 
 
 def set_workload(name: str):
-    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP
+    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP, PRESET
     w = WORKLOADS[name]
     H, W, C, WORKLOAD, CPU_CROP, REF_CROP = w["H"], w["W"], w["C"], w["desc"], w["cpu_crop"], w["ref_crop"]
+    PRESET = w.get("preset", 0)
+
+
+def oracle_params():
+    """The oracle's parameters for the workload's library preset."""
+    import oracle
+    return oracle.Params.paper() if PRESET == 1 else oracle.Params()
 
 
 def make_inputs(seed: int):
@@ -69,16 +82,25 @@ def make_inputs(seed: int):
     return synth.make_pair(H, W, SIGMA, seed) if C == 1 else synth.make_color_pair(H, W, SIGMA, seed)
 
 
-def launches_per_denoise(p, channels: int, tc: bool = True) -> int:
-    """Kernel launches of one denoise (translations = 1): per stage the
-    matching (+ the exact re-match pass of the tensor-core engine) and the 7
+def launches_per_denoise(p, channels: int, tc=(True, True)) -> int:
+    """Kernel launches of one denoise: per stage and translation the matching
+    (+ the exact re-match pass of the tensor-core engine, tc[stage]) and the 7
     launches of the inverted lists; stage 1 per channel the offset table, one
     analysis and one synthesis per level and cycle spin, TV, gather; stage 2
-    per channel Wiener and gather; colour adds the two opponent transforms."""
-    m = 2 if tc else 1
-    s1 = m + 7 + channels * (1 + 2 * p.cycle_spins * p.levels + 1 + 1)
-    s2 = m + 7 + channels * 2
-    return s1 + (s2 if p.stages == 2 else 0) + (2 if channels == 3 else 0)
+    per channel Wiener and gather; with translations the image shifts (stage 1:
+    input and accumulation, stage 2: input, pilot and accumulation); colour
+    adds the two opponent transforms."""
+    T = p.translations
+    s1 = (2 if tc[0] else 1) + 7 + channels * (1 + 2 * p.cycle_spins * p.levels + 1 + 1) + (2 if T > 1 else 0)
+    s2 = (2 if tc[1] else 1) + 7 + channels * 2 + (3 if T > 1 else 0)
+    return T * s1 + (T * s2 if p.stages == 2 else 0) + (2 if channels == 3 else 0)
+
+
+def tc_supported(Hh, Ww, N, s, R, K):
+    """Whether the library's automatic engine choice takes the tensor-core
+    matcher for this stage geometry (block side 8, the union of 8 grid
+    columns' windows within one 64-column chunk, K <= 32)."""
+    return N == 8 and 2 <= K <= 32 and 7 * s + 2 * R + 1 <= 64
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES = 152, 128
 
@@ -245,9 +267,9 @@ def run_cpu_oracle(noisy_crop, nthreads):
     import oracle
     t0 = time.perf_counter()
     if noisy_crop.ndim == 3:
-        out = oracle.denoise_color(noisy_crop, SIGMA, nthreads=nthreads)
+        out = oracle.denoise_color(noisy_crop, SIGMA, oracle_params(), nthreads=nthreads)
     else:
-        out = oracle.denoise(noisy_crop, SIGMA, nthreads=nthreads)
+        out = oracle.denoise(noisy_crop, SIGMA, oracle_params(), nthreads=nthreads)
     return out, time.perf_counter() - t0
 
 
@@ -304,7 +326,7 @@ def main():
     from paper_2103_10765_gb300 import gbm3d
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = gbm3d.params_default()
+    p = gbm3d.params_default(PRESET)
     seeds = rank_seeds(rank)
     pairs = [make_inputs(s) for s in seeds]
     noisy = [torch.from_numpy(n).to(dev) for _, n in pairs]
@@ -375,38 +397,48 @@ def main():
         e2e = {"value": job_mpix(world, args.steps, e2e_ms), "unit": "MPix/s",
                "h2d_bytes_per_step": hd.h2d_bytes, "d2h_bytes_per_step": hd.d2h_bytes}
 
-    # roofline of the dominant kernel, the tensor-core block matcher
+    # roofline of the dominant kernel, the block matcher (both stages' launches)
     mt = [float(np.mean(x)) for x in match_ms]
-    npairs = candidate_pairs(H, W)
-    flops_launch = 2 * 64 * npairs  # 2 N^2 FLOP per (reference, candidate)
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    achieved = flops_launch / (np.mean(mt) / 1e3) / 1e12
-    tc_flop = tc_executed_flop(H, W)
-    f16_peak = float(peaks.get("bf16_tflops", 1900.0))  # FP16 and BF16 share the nominal dense rate
-    tc_achieved = tc_flop / (np.mean(mt) / 1e3) / 1e12
-    roofline = {"kernel": "k_match_tc (block matching: tcgen05 split-FP16 Theorem-1 product, register top-L, "
-                          "certified exact FP32 re-rank)", "bound": "alu",
-                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "traffic": None, "launch_ms": {"stage1_K16": mt[0], "stage2_K32": mt[1]},
+    geo = [gbm3d.params_stage(p, 1), gbm3d.params_stage(p, 2)]
+    Ks = (p.k1, p.k2)
+    tc = [tc_supported(H, W, g.patch, g.step, p.search_radius, k) for g, k in zip(geo, Ks)]
+    # 2 N^2 FLOP per (reference, candidate), the Theorem-1 inner-product count
+    flops = [2 * g.patch ** 2 * candidate_pairs(H, W, g.patch, g.step, p.search_radius) for g in geo]
+    achieved = sum(flops) / (sum(mt) / 1e3) / 1e12
+    names = ["k_match_tc" if t else f"k_match<{g.patch}>" for t, g in zip(tc, geo)]
+    roofline = {"kernel": (names[0] if names[0] == names[1] else " + ".join(names)) + " (block matching, both "
+                "stages: " + ("tcgen05 split-FP16 Theorem-1 product, register top-L, certified exact FP32 re-rank"
+                              if all(tc) else "direct FP32 sum of squared differences") + ")",
+                "bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "launch_ms": {f"stage1_K{p.k1}": mt[0], f"stage2_K{p.k2}": mt[1]},
                 "launch_timing": "CUDA events recorded by the library around both matching launches of every "
-                                 "timed step (same stream), averaged over the timed steps",
-                "flop_per_launch": flops_launch,
+                                 "timed step (same stream; with translations the last one's), averaged over the "
+                                 "timed steps",
+                "flop_per_launch": {"stage1": flops[0], "stage2": flops[1]},
                 "peak_note": f"FP32 ALU: {N_SM} SMs x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz "
-                             f"(SM clock from MEASURED_PEAKS.json, {peak_kind}); the binding resource is "
-                             "the issue of the per-reference selection (tensor pipe mostly idle)",
-                "tensor": {"executed_flop_per_launch": tc_flop, "achieved": tc_achieved, "peak": f16_peak,
-                           "unit": "TFLOP/s", "frac": tc_achieved / f16_peak,
-                           "note": "three FP16 products over each 128-reference tile's window union; "
-                                   f"peak = measured dense BF16 cuBLAS rate ({peak_kind}), FP16 nominal ratio 1"}}
-    tr = match_traffic()
-    if tr:
-        # captured at 1024^2; the launch reads its (luma) image once, so the
-        # traffic scales with the pixel count
-        roofline["traffic"] = 0.5 * (tr.get("dram_bytes_K16", 0.0) + tr.get("dram_bytes_K32", 0.0)) * H * W / 1024 ** 2
-        roofline["traffic_note"] = ("dram read+write bytes per launch, ncu capture of this kernel source at 1024x1024"
-                                    + ("" if H * W == 1024 ** 2 else ", scaled by the pixel count"))
+                             f"(SM clock from MEASURED_PEAKS.json, {peak_kind})"}
+    if all(tc):
+        tc_flop = sum(tc_executed_flop(H, W, g.patch, g.step, p.search_radius) for g in geo) / 2
+        f16_peak = float(peaks.get("bf16_tflops", 1900.0))  # FP16 and BF16 share the nominal dense rate
+        tc_achieved = 2 * tc_flop / (sum(mt) / 1e3) / 1e12
+        roofline["peak_note"] += ("; the binding resource is the issue of the per-reference selection (tensor "
+                                  "pipe mostly idle)")
+        roofline["tensor"] = {"executed_flop_per_launch": tc_flop, "achieved": tc_achieved, "peak": f16_peak,
+                              "unit": "TFLOP/s", "frac": tc_achieved / f16_peak,
+                              "note": "three FP16 products over each 128-reference tile's window union; "
+                                      f"peak = measured dense BF16 cuBLAS rate ({peak_kind}), FP16 nominal ratio 1"}
+        tr = match_traffic()
+        if tr:
+            # captured at 1024^2; the launch reads its (luma) image once, so
+            # the traffic scales with the pixel count
+            roofline["traffic"] = (0.5 * (tr.get("dram_bytes_K16", 0.0) + tr.get("dram_bytes_K32", 0.0))
+                                   * H * W / 1024 ** 2)
+            roofline["traffic_note"] = ("dram read+write bytes per launch, ncu capture of this kernel source at "
+                                        "1024x1024" + ("" if H * W == 1024 ** 2 else ", scaled by the pixel count"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -422,7 +454,7 @@ def main():
                "sample": f"two-stage FP64 oracle on the top-left {CPU_CROP}x{CPU_CROP} crop of the workload image",
                "seconds": secs, "psnr_gap_db_on_sample": abs(pg - po)}
 
-    launches = launches_per_denoise(p, C)
+    launches = launches_per_denoise(p, C, tc)
     if rank == 0:
         line = {
             "metric": METRIC, "value": mpix, "unit": "MPix/s", "n_gpus": world, "steps": args.steps,

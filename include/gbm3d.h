@@ -57,8 +57,9 @@ enum {
 
 /* Method parameters (Sec. 5 parameter list; see gbm3d_params_default). */
 typedef struct {
-    int patch;          /* N: block side, both stages                         */
-    int step;           /* s: reference-grid stride                           */
+    int patch;          /* N: block side (stage 1; both stages if patch2 = 0): */
+                        /* 8 or 16                                            */
+    int step;           /* s: reference-grid stride (stage 1; see step2)      */
     int search_radius;  /* R: candidates with |k-i| <= R and |l-j| <= R       */
     int k1;             /* K: blocks per group, stage 1 (Sec. 3: K = 16)      */
     int k2;             /* K: blocks per group, stage 2                       */
@@ -76,18 +77,31 @@ typedef struct {
                         /* bit: the tensor-core engine ranks with the norm    */
                         /* expansion of Theorem 1 and re-ranks its certified  */
                         /* survivors with the exact direct sum.               */
+    int patch2;         /* stage-2 block side; 0 = patch.  The Wiener filter  */
+                        /* is built for 8 (Sec. 5: N = 16 in stage 1, 8 in 2) */
+    int step2;          /* stage-2 grid stride; 0 = step                      */
 } gbm3d_params;
 
-/* Fill *p with a preset.  preset 0: N=8, s=3, R=19 (39x39 candidate offsets),
- * K1=16, K2=32, 3 levels, 2 cycle spins, 1 translation, 2 stages,
- * tau = sigma (3.6 - 0.3 l), Kaiser beta 2, eps_w 1e-8.  preset 1 (the
- * paper's Sec. 5 list where this build supports it): N=8, s=8, R=16, K1=K2=16,
- * 3 levels, 2 cycle spins, 2 translations.  Returns GBM3D_EINVAL for other
- * presets or p == NULL. */
+/* Fill *p with a preset.  preset 0: N=8, s=3 in both stages, R=19 (39x39
+ * candidate offsets), K1=16, K2=32, 3 levels, 2 cycle spins, 1 translation,
+ * 2 stages, tau = sigma (3.6 - 0.3 l), Kaiser beta 2, eps_w 1e-8.  preset 1
+ * (the Sec. 5 parameter list): stage 1 with 16 x 16 blocks tiling the image
+ * (N = s = 16), stage 2 with 8 x 8 blocks tiling it (N = s = 8), R = 16 (the
+ * 32-pixel search window), K1 = K2 = 16, 3 levels, 2 cycle spins,
+ * 2 translations.  Translations shift by h in {0, N/4, N/2}, N the block side
+ * of the stage being averaged.  Returns GBM3D_EINVAL for other presets or
+ * p == NULL. */
 int gbm3d_params_default(gbm3d_params *p, int preset);
 
-/* Reference-grid size for an H x W image: By = |G_y|, Bx = |G_x|.  Host-only,
- * launches nothing. */
+/* The parameters that the block-level calls below (grid_dims, match,
+ * filter_ht, filter_wiener, aggregate) take for stage `stage` (1 or 2) of the
+ * whole method: a copy of *p whose patch / step are that stage's block side
+ * and stride (patch2 / step2 for stage 2 where set) and whose patch2 / step2
+ * are 0.  Host-only.  EINVAL for a NULL pointer or another stage. */
+int gbm3d_params_stage(const gbm3d_params *p, int stage, gbm3d_params *out);
+
+/* Reference-grid size for an H x W image with block side p->patch and stride
+ * p->step: By = |G_y|, Bx = |G_x|.  Host-only, launches nothing. */
 int gbm3d_grid_dims(int H, int W, const gbm3d_params *p, int *By, int *Bx);
 
 /* Bytes of device scratch `ws` needed by any call below for an H x W image
@@ -100,7 +114,8 @@ int gbm3d_workspace_bytes(int H, int W, const gbm3d_params *p, size_t *bytes);
  * ||z^{ij} - z^{kl}||^2 (FP32, direct sum of squared differences) to every
  * candidate top-left (k,l) with |k-i| <= R, |l-j| <= R inside [0,H-N]x[0,W-N];
  * slot 0 = the reference itself, slots 1..K-1 = the K-1 nearest other blocks
- * ordered by (distance, k, l).
+ * ordered by (distance, k, l).  Blocks are N x N with N = p->patch (8 or 16)
+ * on the grid of stride p->step; the tensor-core engine serves N = 8.
  *   img  : H x W image, pitch elements per row.
  *   idx  : out, int32 [By*Bx][K].
  *   dist : out, float [By*Bx][K] (nullable); slot 0 holds 0.
@@ -116,7 +131,7 @@ int gbm3d_match(const float *img, int H, int W, int pitch, const gbm3d_params *p
  * periodic, Mallat), every detail coefficient of level l is hard-thresholded
  * at sigma (tau_a - tau_b l), the transform is inverted; this is repeated for
  * cycle spins h = 0..C-1 (circular shift by h along all three axes) and
- * averaged.
+ * averaged.  N = p->patch (8 or 16), grid of stride p->step.
  *   noisy  : H x W noisy image Z, pitch elements per row.
  *   idx    : int32 [By*Bx][K1] from gbm3d_match with K = k1.
  *   groups : out, float [By*Bx][K1][N][N] = filtered blocks U.
@@ -129,7 +144,8 @@ int gbm3d_filter_ht(const float *noisy, int H, int W, int pitch, const int32_t *
  * G_y (pilot) blocks, transform T = orthonormal 8x8 DCT-II per block then
  * full-depth orthonormal Haar along the K2 blocks; omega = P^2/(P^2+sigma^2)
  * with P = T(G_y); filtered group T^-1(omega . T(G_z)); weight
- * 1 / max(sigma^2 sum omega^2, eps_w).
+ * 1 / max(sigma^2 sum omega^2, eps_w).  p->patch must be 8 (else
+ * GBM3D_EUNSUPPORTED); grid of stride p->step.
  *   noisy, pilot : H x W images sharing `pitch`.
  *   idx    : int32 [By*Bx][K2] (matching done on the pilot).
  *   groups : out, float [By*Bx][K2][N][N];  w : out, float [By*Bx].
@@ -145,7 +161,7 @@ int gbm3d_filter_wiener(const float *noisy, const float *pilot, int H, int W, in
  * order with Kahan-compensated FP32 numerator and denominator, so the result
  * is deterministic.
  *   groups : float [G][K][N][N];  w : float [G];  idx : int32 [G][K], with
- *            G = By*Bx of the grid for H x W.
+ *            N = p->patch and G = By*Bx of its grid (stride p->step) for H x W.
  *   out    : out, H x W, pitch elements per row.
  *   ws     : scratch, gbm3d_workspace_bytes.
  * Every pixel must be covered by some block (true for grid-reference slot 0). */

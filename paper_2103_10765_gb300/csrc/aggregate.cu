@@ -4,7 +4,7 @@
 // Deterministic owner-computes design: the match lists are inverted into a
 // CSR index (block top-left position -> the (group, slot) entries placed
 // there; counting sort, then each bucket sorted), and one thread per output
-// pixel walks the N x N top-left positions that cover it, in a fixed order,
+// pixel walks the N x N top-left positions that cover it (N = 8 or 16), in a fixed order,
 // summing numerator and denominator with Kahan compensation.  No floating-
 // point atomics: the result does not depend on scheduling.
 #include <mutex>
@@ -23,12 +23,12 @@ constexpr int kScanBlock = 1024; // elements per scan block (256 threads x 4)
 
 // Entries that are not valid block positions are skipped (never counted,
 // never placed), so a bad caller-supplied list cannot write out of bounds.
-__global__ void k_count(const int32_t *__restrict__ idx, int n, int H, int W, int *__restrict__ cnt)
+__global__ void k_count(const int32_t *__restrict__ idx, int n, int H, int W, int N, int *__restrict__ cnt)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int pos = idx[e];
-    if (block_ok(pos, H, W)) atomicAdd(cnt + pos, 1);
+    if (block_ok(pos, H, W, N)) atomicAdd(cnt + pos, 1);
 }
 
 // Exclusive scan, phase 1: per-block scan of 1024 elements, block totals out.
@@ -96,13 +96,13 @@ __global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__
     if (e < n) out[e] += bsum[e / kScanBlock];
 }
 
-__global__ void k_fill(const int32_t *__restrict__ idx, int n, int H, int W, const int *__restrict__ off,
+__global__ void k_fill(const int32_t *__restrict__ idx, int n, int H, int W, int N, const int *__restrict__ off,
                        int *__restrict__ cursor, int *__restrict__ list)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int pos = idx[e];
-    if (!block_ok(pos, H, W)) return;
+    if (!block_ok(pos, H, W, N)) return;
     const int slot = atomicAdd(cursor + pos, 1);
     list[off[pos] + slot] = e;
 }
@@ -136,8 +136,8 @@ __global__ void k_slots(const int *__restrict__ list, const int *__restrict__ to
     lpos[j] = idx[e] % W;
 }
 
-struct Win8 {
-    float v[8];
+struct Win {
+    float v[kMaxPatch];
 };
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
@@ -150,20 +150,21 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 
 // One thread per output pixel, eight lanes per 8-pixel row segment: the lanes
 // of a segment walk the same block positions and entries together, so each
-// patch-row read is one 32-byte sector shared by the 8 lanes (lanes the block
+// patch-row read is a 32-byte sector shared by the 8 lanes (lanes the block
 // does not cover sit the entry out).  Per pixel the order is fixed -- block
 // rows k ascending, columns l ascending, entries ascending -- and numerator
 // and denominator are Kahan-compensated FP32 sums.
 constexpr int kSegX = 8, kSegRows = 4; // CTA: 8 segments (64 px) x 4 rows
 
+template <int N>
 __global__ void __launch_bounds__(256)
 k_gather(const float *__restrict__ groups, const float *__restrict__ w, const int *__restrict__ off,
-         const int *__restrict__ list, int log2K, int H, int W, int pitch, Win8 win, float *__restrict__ out)
+         const int *__restrict__ list, int log2K, int H, int W, int pitch, Win win, float *__restrict__ out)
 {
-    __shared__ float sw[8];
+    __shared__ float sw[N];
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; i++) sw[i] = win.v[i];
+        for (int i = 0; i < N; i++) sw[i] = win.v[i];
     }
     __syncthreads();
     const int j = threadIdx.x & 7;
@@ -172,15 +173,15 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
     if (x0 >= W || y >= H) return; // whole segment
     const int x = x0 + j;
     float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
-    const int ka = max(0, y - 7), kb = min(y, H - 8);
-    const int la = max(0, x0 - 7), lb = min(x0 + 7, W - 8);
+    const int ka = max(0, y - (N - 1)), kb = min(y, H - N);
+    const int la = max(0, x0 - (N - 1)), lb = min(x0 + 7, W - N);
     for (int k = ka; k <= kb; k++) {
         const int a = y - k;
         const float wa = sw[a];
-        const float *grow = groups + a * 8;
+        const float *grow = groups + a * N;
         for (int l = la; l <= lb; l++) {
             const int b = x - l;
-            const bool inb = b >= 0 && b < 8 && x < W;
+            const bool inb = b >= 0 && b < N && x < W;
             const float wab = inb ? wa * sw[b] : 0.f;
             const int pos = k * W + l;
             const int e0 = __ldg(off + pos), e1 = __ldg(off + pos + 1);
@@ -188,7 +189,7 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
                 const int ent = __ldg(list + e);
                 if (inb) {
                     const float wt = __ldg(w + (ent >> log2K)) * wab;
-                    const float v = __ldg(grow + (size_t)ent * 64 + b);
+                    const float v = __ldg(grow + (size_t)ent * (N * N) + b);
                     kahan_add(num, cn, wt * v);
                     kahan_add(den, cd, wt);
                 }
@@ -199,21 +200,22 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
 }
 
 // The same sums over the planar, position-sorted layout: row a of slot j is
-// the 8 floats at planes + a * plane_stride + 8 j, its weight w_slot[j], its
+// the N floats at planes + a * plane_stride + N j, its weight w_slot[j], its
 // block column lpos[j].  For one block row k the slots of the blocks
-// covering pixel x (positions k*W + x-7 .. k*W + x) are one contiguous range,
+// covering pixel x (positions k*W + x-N+1 .. k*W + x) are one contiguous range,
 // walked in order (= columns ascending, entries ascending: the same
 // per-pixel order as k_gather), so each lane visits only its own blocks and
 // the reads stream through memory.
+template <int N>
 __global__ void __launch_bounds__(256)
 k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_slot, const int *__restrict__ off,
-                const int *__restrict__ lpos, long long plane_stride, int H, int W, int pitch, Win8 win,
+                const int *__restrict__ lpos, long long plane_stride, int H, int W, int pitch, Win win,
                 float *__restrict__ out)
 {
-    __shared__ float sw[8];
+    __shared__ float sw[N];
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; i++) sw[i] = win.v[i];
+        for (int i = 0; i < N; i++) sw[i] = win.v[i];
     }
     __syncthreads();
     const int j = threadIdx.x & 7;
@@ -223,11 +225,11 @@ k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_sl
     const int x = x0 + j;
     const bool xin = x < W;
     float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
-    const int ka = max(0, y - 7), kb = min(y, H - 8);
+    const int ka = max(0, y - (N - 1)), kb = min(y, H - N);
     // the blocks of block row k covering pixel x have columns lo .. hi, and
     // their slots are one contiguous range (positions in order, entries in
     // order within a position): each lane walks exactly its own range
-    const int lo = max(0, x - 7), hi = min(x, W - 8);
+    const int lo = max(0, x - (N - 1)), hi = min(x, W - N);
     const bool any = xin && lo <= hi;
     for (int k = ka; k <= kb; k++) {
         const int a = y - k;
@@ -243,7 +245,7 @@ k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_sl
             for (int q = 0; q < 8; q++) {
                 const bool ok = e0 + q < s1;
                 wq[q] = ok ? __ldg(w_slot + e0 + q) : 0.f;
-                vq[q] = ok ? __ldg(plane + (size_t)(e0 + q) * 8 + bq[q]) : 0.f;
+                vq[q] = ok ? __ldg(plane + (size_t)(e0 + q) * N + bq[q]) : 0.f;
             }
 #pragma unroll
             for (int q = 0; q < 8; q++)
@@ -308,7 +310,8 @@ AggLayout agg_layout(int H, int W, int G, int K, bool with_slots)
     return L;
 }
 
-cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, void *agg_ws, bool with_slots, cudaStream_t st)
+cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, int N, void *agg_ws, bool with_slots,
+                      cudaStream_t st)
 {
     const AggLayout L = agg_layout(H, W, G, K, with_slots);
     char *base = (char *)agg_ws;
@@ -319,48 +322,52 @@ cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, void *agg_
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(cursor, 0, (size_t)nscan * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_count<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, cnt);
+    k_count<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, N, cnt);
     k_scan_local<<<L.nblk, 256, 0, st>>>(cnt, nscan, off, bsum);
     k_scan_bsum<<<1, 1024, 0, st>>>(bsum, L.nblk);
     k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(off, nscan, bsum);
-    k_fill<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, off, cursor, list);
+    k_fill<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, N, off, cursor, list);
     k_sort<<<(L.npos + 255) / 256, 256, 0, st>>>(off, L.npos, list);
     if (with_slots)
         k_slots<<<(n + 255) / 256, 256, 0, st>>>(list, off + L.npos, idx, W, slot_of, (int *)(base + L.lpos));
     return cudaGetLastError();
 }
 
-static Win8 make_win(const float *window8)
+static Win make_win(const float *window, int N)
 {
-    Win8 win;
-    for (int i = 0; i < 8; i++) win.v[i] = window8[i];
+    Win win{};
+    for (int i = 0; i < N; i++) win.v[i] = window[i];
     return win;
 }
 
 cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t *idx, int G, int K, int H, int W,
-                             int pitch, const float *window8, float *out, void *agg_ws, cudaStream_t st)
+                             int N, int pitch, const float *window, float *out, void *agg_ws, cudaStream_t st)
 {
-    cudaError_t e = build_csr(idx, G, K, H, W, agg_ws, false, st);
+    if (N != 8 && N != 16) return cudaErrorInvalidValue;
+    cudaError_t e = build_csr(idx, G, K, H, W, N, agg_ws, false, st);
     if (e != cudaSuccess) return e;
     const AggLayout L = agg_layout(H, W, G, K, false);
     const char *base = (const char *)agg_ws;
     int log2K = 0;
     while ((1 << log2K) < K) log2K++;
     dim3 grid((W + 8 * kSegX - 1) / (8 * kSegX), (H + kSegRows - 1) / kSegRows);
-    k_gather<<<grid, 256, 0, st>>>(groups, w, (const int *)(base + L.off), (const int *)(base + L.list), log2K, H, W,
-                                   pitch, make_win(window8), out);
+    auto kern = N == 8 ? k_gather<8> : k_gather<16>;
+    kern<<<grid, 256, 0, st>>>(groups, w, (const int *)(base + L.off), (const int *)(base + L.list), log2K, H, W,
+                               pitch, make_win(window, N), out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, int n_entries, int H, int W,
-                                    int pitch, const float *window8, float *out, const void *agg_ws, cudaStream_t st)
+cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, int n_entries, int H, int W, int N,
+                                    int pitch, const float *window, float *out, const void *agg_ws, cudaStream_t st)
 {
+    if (N != 8 && N != 16) return cudaErrorInvalidValue;
     const AggLayout L = agg_layout(H, W, n_entries, 1, true);
     const int *off = (const int *)((const char *)agg_ws + L.off);
     const int *lpos = (const int *)((const char *)agg_ws + L.lpos);
     dim3 grid((W + 8 * kSegX - 1) / (8 * kSegX), (H + kSegRows - 1) / kSegRows);
-    k_gather_planar<<<grid, 256, 0, st>>>(planes, w_slot, off, lpos, (long long)n_entries * 8, H, W, pitch,
-                                          make_win(window8), out);
+    auto kern = N == 8 ? k_gather_planar<8> : k_gather_planar<16>;
+    kern<<<grid, 256, 0, st>>>(planes, w_slot, off, lpos, (long long)n_entries * N, H, W, pitch, make_win(window, N),
+                               out);
     return cudaGetLastError();
 }
 

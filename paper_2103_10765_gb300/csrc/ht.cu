@@ -54,12 +54,13 @@ __device__ __forceinline__ int pwrap(int i, int n)
 
 // Pixel offset k*pitch + l of every match-list entry (once per call, so the
 // gathers need no division).
-__global__ void k_offsets(const int32_t *__restrict__ idx, int n, int H, int W, int pitch, int *__restrict__ ofs)
+__global__ void k_offsets(const int32_t *__restrict__ idx, int n, int H, int W, int N, int pitch,
+                          int *__restrict__ ofs)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     int k, l;
-    block_kl(idx[e], H, W, k, l);
+    block_kl(idx[e], H, W, N, k, l);
     ofs[e] = k * pitch + l;
 }
 
@@ -70,10 +71,11 @@ __device__ __forceinline__ float lift_u(float dm2, float dm1, float dp1, float d
 }
 
 // Level analysis: input (Z, Y, X) -> 8 bands [band][Z/2][Y/2][X/2], band =
-// 4 hz + 2 hy + hx.  GATHER: the input is the cycle-spun mosaic read from the
-// image through the pixel offsets of the match list (level 1); otherwise a
-// [Z][Y][X] plane stack.  vec: X/2 is a multiple of 4 (float4 stores).
-template <bool GATHER>
+// 4 hz + 2 hy + hx.  GATHER: the input is the cycle-spun mosaic of blocks of
+// side 2^LN read from the image through the pixel offsets of the match list
+// (level 1); otherwise a [Z][Y][X] plane stack.  vec: X/2 is a multiple of 4
+// (float4 stores).
+template <bool GATHER, int LN>
 __global__ void __launch_bounds__(256)
 k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitch, const int *__restrict__ ofs,
           int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst, float tau, int vec)
@@ -86,19 +88,22 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // load (one warp per tile row) + Haar along z.  Gather: the tile's input
-    // rows and columns span at most 6 x 10 blocks of the mosaic (an 8-aligned
-    // block wraps as a whole), whose pixel offsets for the two slices are
-    // staged in shared memory first; every voxel is then one image load.
-    __shared__ int s_ofs[6][10][2];
+    // rows and columns span at most OY x OX blocks of the mosaic (6 x 10 for
+    // N = 8, 4 x 6 for N = 16; an N-aligned block wraps as a whole), whose
+    // pixel offsets for the two slices are staged in shared memory first;
+    // every voxel is then one image load.
+    constexpr int NB = 1 << LN;
+    constexpr int OY = ((NB + IY - 2) >> LN) + 1, OX = ((NB + IX - 2) >> LN) + 1;
+    __shared__ int s_ofs[OY][OX][2];
     int z0 = 2 * m, z1 = 2 * m + 1;
     const int uy0 = iy0 - shift, ux0 = ix0 - shift;
-    const int ybase = (uy0 >> 3) << 3, xbase = (ux0 >> 3) << 3; // floor to a block
+    const int ybase = (uy0 >> LN) << LN, xbase = (ux0 >> LN) << LN; // floor to a block
     if (GATHER) {
         z0 = pwrap(z0 - shift, Z);
         z1 = pwrap(z1 - shift, Z);
-        for (int e = tid; e < 6 * 10 * 2; e += blockDim.x) {
-            const int ry = e / 20, rem = e - ry * 20, rx = rem >> 1, zz = rem & 1;
-            const int gy = pwrap(ybase + 8 * ry, Y) >> 3, gx = pwrap(xbase + 8 * rx, X) >> 3;
+        for (int e = tid; e < OY * OX * 2; e += blockDim.x) {
+            const int ry = e / (2 * OX), rem = e - ry * (2 * OX), rx = rem >> 1, zz = rem & 1;
+            const int gy = pwrap(ybase + NB * ry, Y) >> LN, gx = pwrap(xbase + NB * rx, X) >> LN;
             s_ofs[ry][rx][zz] = __ldg(ofs + (size_t)(gy * Bx + gx) * Z + (zz ? z1 : z0));
         }
         __syncthreads();
@@ -110,17 +115,17 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
         for (int j = 0; j < NR; j++) {
             const int yy = warp + 8 * j;
             if (GATHER) {
-                const int dy = uy0 + yy - ybase, ry = dy >> 3;
-                const float *rowimg = img + (size_t)(dy & 7) * pitch;
+                const int dy = uy0 + yy - ybase, ry = dy >> LN;
+                const float *rowimg = img + (size_t)(dy & (NB - 1)) * pitch;
 #pragma unroll
                 for (int h = 0; h < NH; h++) {
                     const int xx = lane + 32 * h;
                     v0[j][h] = v1[j][h] = 0.f;
                     if (xx < IX) {
                         const int dx = ux0 + xx - xbase;
-                        const float *b = rowimg + (dx & 7);
-                        v0[j][h] = __ldg(b + s_ofs[ry][dx >> 3][0]);
-                        v1[j][h] = __ldg(b + s_ofs[ry][dx >> 3][1]);
+                        const float *b = rowimg + (dx & (NB - 1));
+                        v0[j][h] = __ldg(b + s_ofs[ry][dx >> LN][0]);
+                        v1[j][h] = __ldg(b + s_ofs[ry][dx >> LN][1]);
                     }
                 }
             } else {
@@ -214,9 +219,9 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
 // Level synthesis: 8 bands [band][Zc][Yc][Xc] -> (2Zc, 2Yc, 2Xc) for one tile
 // of 16 x 32 coefficient positions and one slice pair.  SCATTER (level 1):
 // the voxel at spun position (z,y,x) belongs to mosaic position
-// (z,y,x) - shift, i.e. block r = z of group (y/8, x/8) at (y%8, x%8); it is
-// written (or added) scaled through the GroupOut.
-template <bool SCATTER>
+// (z,y,x) - shift, i.e. block r = z of group (y/N, x/N) at (y%N, x%N), with
+// N = 2^LN; it is written (or added) scaled through the GroupOut.
+template <bool SCATTER, int LN>
 __global__ void __launch_bounds__(256)
 k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restrict__ dst, GroupOut out, int Bx,
           int shift, float scale, int accumulate)
@@ -293,8 +298,8 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
     long long gx = 0;
     if (SCATTER) {
         const int x = pwrap(xo - shift, Xo);
-        gx = x >> 3;
-        bx = x & 7;
+        gx = x >> LN;
+        bx = x & ((1 << LN) - 1);
         z0 = pwrap(2 * m - shift, Zo);
         z1 = pwrap(2 * m + 1 - shift, Zo);
     }
@@ -310,9 +315,9 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
             p0[i] = p1[i] = nullptr;
             if (ys < Yo) {
                 const int y = pwrap(ys - shift, Yo);
-                const long long g = (long long)(y >> 3) * Bx + gx;
-                p0[i] = out.row(g * Zo + z0, y & 7) + bx;
-                p1[i] = out.row(g * Zo + z1, y & 7) + bx;
+                const long long g = (long long)(y >> LN) * Bx + gx;
+                p0[i] = out.row(g * Zo + z0, y & ((1 << LN) - 1)) + bx;
+                p1[i] = out.row(g * Zo + z1, y & ((1 << LN) - 1)) + bx;
             }
             o0[i] = o1[i] = 0.f;
         }
@@ -348,34 +353,45 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
 // N x N x K block (no wrap).  One warp per group reads the group-major block
 // gm[g][r][a][b] (contiguous, float4), stages it in shared memory, sums the
 // differences and writes w; with permute it also copies each block row to
-// out.row(g*K + r, a) and w to each of the group's slots.
-constexpr int kTvWarps = 4;
-
-template <int K>
-__global__ void __launch_bounds__(kTvWarps * 32) k_tv(const float *__restrict__ gm, int G, float eps, GroupOut out,
-                                                      int permute)
+// out.row(g*K + r, a) and w to each of the group's slots.  Warps per CTA:
+// as many as keep the staged blocks within 32 KB of shared memory (<= 4).
+template <int K, int NB>
+__host__ __device__ constexpr int tv_warps()
 {
-    constexpr int NV = K * 16 / 32; // float4 per lane
-    __shared__ __align__(16) float su[kTvWarps][K * 64];
+    return 8192 / (K * NB * NB) >= 4 ? 4 : (8192 / (K * NB * NB) >= 1 ? 8192 / (K * NB * NB) : 1);
+}
+
+template <int K, int NB>
+__global__ void __launch_bounds__(tv_warps<K, NB>() * 32)
+k_tv(const float *__restrict__ gm, int G, float eps, GroupOut out, int permute)
+{
+    constexpr int NW = tv_warps<K, NB>(), E = K * NB * NB; // floats per group
+    constexpr int NV = E / 4 / 32;                         // float4 per lane
+    constexpr int NL = NB == 8 ? 3 : 4;                    // log2 NB
+    __shared__ __align__(16) float su[NW][E];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x * kTvWarps + warp;
+    const int g = blockIdx.x * NW + warp;
     if (g >= G) return;
     float *u = su[warp];
-    const float4 *src = reinterpret_cast<const float4 *>(gm + (size_t)g * K * 64);
-    float4 v[NV];
+    const float4 *src = reinterpret_cast<const float4 *>(gm + (size_t)g * E);
+    constexpr int CH = NV < 8 ? NV : 8; // float4 loads in flight per lane
+#pragma unroll 1
+    for (int i0 = 0; i0 < NV; i0 += CH) {
+        float4 v[CH];
 #pragma unroll
-    for (int i = 0; i < NV; i++) v[i] = __ldg(src + lane + 32 * i);
+        for (int i = 0; i < CH; i++) v[i] = __ldg(src + lane + 32 * (i0 + i));
 #pragma unroll
-    for (int i = 0; i < NV; i++) reinterpret_cast<float4 *>(u)[lane + 32 * i] = v[i];
+        for (int i = 0; i < CH; i++) reinterpret_cast<float4 *>(u)[lane + 32 * (i0 + i)] = v[i];
+    }
     __syncwarp();
     float tv = 0.f;
 #pragma unroll 4
-    for (int e = lane; e < K * 64; e += 32) {
-        const int r = e >> 6, a = (e >> 3) & 7, b = e & 7;
+    for (int e = lane; e < E; e += 32) {
+        const int r = e >> (2 * NL), a = (e >> NL) & (NB - 1), b = e & (NB - 1);
         const float c = u[e];
-        if (a < 7) tv += fabsf(u[e + 8] - c);
-        if (b < 7) tv += fabsf(u[e + 1] - c);
-        if (r < K - 1) tv += fabsf(u[e + 64] - c);
+        if (a < NB - 1) tv += fabsf(u[e + NB] - c);
+        if (b < NB - 1) tv += fabsf(u[e + 1] - c);
+        if (r < K - 1) tv += fabsf(u[e + NB * NB] - c);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tv += __shfl_xor_sync(0xffffffffu, tv, o);
@@ -384,28 +400,67 @@ __global__ void __launch_bounds__(kTvWarps * 32) k_tv(const float *__restrict__ 
         if (lane == 0) out.w[g] = wv;
         return;
     }
-    // two lanes per block row q = 8 r + a, one float4 each: every 32-byte row
-    // (one sector) is written whole by one instruction, 16 rows per instruction
-    const int h = lane & 1;
-#pragma unroll
-    for (int i = 0; i < K * 8 / 16; i++) {
-        const int q = (lane >> 1) + 16 * i;
-        const float4 *s = reinterpret_cast<const float4 *>(u + q * 8);
-        reinterpret_cast<float4 *>(out.row((long long)g * K + (q >> 3), q & 7))[h] = s[h];
+    // NB / 4 lanes per block row q = NB r + a, one float4 each: every row
+    // (32 or 64 bytes, whole sectors) is written by one instruction
+    constexpr int LPR = NB / 4, RPI = 32 / LPR; // lanes per row, rows per instruction
+    const int h = lane % LPR;
+#pragma unroll 8
+    for (int i = 0; i < K * NB / RPI; i++) {
+        const int q = lane / LPR + RPI * i;
+        const float4 *s = reinterpret_cast<const float4 *>(u + q * NB);
+        reinterpret_cast<float4 *>(out.row((long long)g * K + (q >> NL), q & (NB - 1)))[h] = s[h];
     }
     if (lane < K) out.w[out.slot((long long)g * K + lane)] = wv;
 }
 
+template <int K, int NB>
+void launch_tv(const float *gm, int G, float eps, const GroupOut &out, int permute, cudaStream_t st)
+{
+    constexpr int NW = tv_warps<K, NB>();
+    k_tv<K, NB><<<(G + NW - 1) / NW, NW * 32, 0, st>>>(gm, G, eps, out, permute);
+}
+
+template <int LN>
+void launch_levels(const HtGeom &g, const float *img, int pitch, const int *ofs, float *const C[4], float sigma,
+                   float tau_a, float tau_b, int cycle_spins, const GroupOut &gm_out, cudaStream_t st)
+{
+    const float inv_c = 1.f / (float)cycle_spins;
+    for (int c = 0; c < cycle_spins; c++) {
+        for (int l = 1; l <= g.levels; l++) { // analysis
+            const int Y = g.Yd >> (l - 1), X = g.Xd >> (l - 1), Z = g.K >> (l - 1);
+            const float tau = sigma * (tau_a - tau_b * (float)l);
+            const int vec = ((X >> 1) % 4) == 0;
+            dim3 grid((X / 2 + TX - 1) / TX, (Y / 2 + TY - 1) / TY, Z / 2);
+            if (l == 1)
+                k_dwt_ana<true, LN><<<grid, 256, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
+            else
+                k_dwt_ana<false, 3><<<grid, 256, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau,
+                                                          vec);
+        }
+        // synthesis, levels L..1; level l writes the approximation of level
+        // l-1, i.e. band 0 of C[l-1] (or the blocks for l = 1)
+        for (int l = g.levels; l >= 1; l--) {
+            const int Yc = g.Yd >> l, Xc = g.Xd >> l, Zc = g.K >> l;
+            dim3 grid((Xc + TX - 1) / TX, (Yc + TY - 1) / TY, Zc);
+            if (l == 1)
+                k_dwt_syn<true, LN><<<grid, 256, 0, st>>>(C[1], Yc, Xc, Zc, nullptr, gm_out, g.Bx, c, inv_c, c > 0);
+            else
+                k_dwt_syn<false, 3><<<grid, 256, 0, st>>>(C[l], Yc, Xc, Zc, C[l - 1], gm_out, 0, 0, 0.f, 0);
+        }
+    }
+}
+
 } // namespace
 
-HtGeom ht_geom(int By, int Bx, int K, int levels)
+HtGeom ht_geom(int By, int Bx, int K, int levels, int N)
 {
     HtGeom g{};
+    g.N = N;
     g.By = By;
     g.Bx = Bx;
     g.K = K;
-    g.Yd = By * kPatch;
-    g.Xd = Bx * kPatch;
+    g.Yd = By * N;
+    g.Xd = Bx * N;
     g.levels = levels;
     size_t off = 0;
     for (int l = 1; l <= levels; l++) {
@@ -417,7 +472,7 @@ HtGeom ht_geom(int By, int Bx, int K, int levels)
     g.ofs_off = off;
     off += align_up((size_t)By * Bx * K * sizeof(int));
     g.gm_off = off;
-    off += align_up((size_t)By * Bx * K * kPatch * kPatch * sizeof(float));
+    off += align_up((size_t)By * Bx * K * N * N * sizeof(float));
     g.bytes = off;
     return g;
 }
@@ -426,46 +481,35 @@ cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const in
                              float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, const GroupOut &out,
                              void *ht_ws, cudaStream_t st)
 {
+    if (g.N != 8 && g.N != 16) return cudaErrorInvalidValue;
     char *base = (char *)ht_ws;
     int *ofs = (int *)(base + g.ofs_off);
     const int nent = g.By * g.Bx * g.K;
-    k_offsets<<<(nent + 255) / 256, 256, 0, st>>>(idx, nent, H, W, pitch, ofs);
+    k_offsets<<<(nent + 255) / 256, 256, 0, st>>>(idx, nent, H, W, g.N, pitch, ofs);
     float *C[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int l = 1; l <= g.levels; l++) C[l] = (float *)(base + g.level_off[l]);
     // the level-1 synthesis writes group-major: the output itself, or a
     // scratch that the TV pass permutes into the output's layout
     const bool permute = out.slot_of != nullptr;
     float *gm = permute ? (float *)(base + g.gm_off) : out.base;
-    const GroupOut gm_out = group_major(gm, nullptr);
-    const float inv_c = 1.f / (float)cycle_spins;
-    for (int c = 0; c < cycle_spins; c++) {
-        for (int l = 1; l <= g.levels; l++) { // analysis
-            const int Y = g.Yd >> (l - 1), X = g.Xd >> (l - 1), Z = g.K >> (l - 1);
-            const float tau = sigma * (tau_a - tau_b * (float)l);
-            const int vec = ((X >> 1) % 4) == 0;
-            dim3 grid((X / 2 + TX - 1) / TX, (Y / 2 + TY - 1) / TY, Z / 2);
-            if (l == 1)
-                k_dwt_ana<true><<<grid, 256, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
-            else
-                k_dwt_ana<false><<<grid, 256, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau, vec);
-        }
-        // synthesis, levels L..1; level l writes the approximation of level
-        // l-1, i.e. band 0 of C[l-1] (or the blocks for l = 1)
-        for (int l = g.levels; l >= 1; l--) {
-            const int Yc = g.Yd >> l, Xc = g.Xd >> l, Zc = g.K >> l;
-            dim3 grid((Xc + TX - 1) / TX, (Yc + TY - 1) / TY, Zc);
-            if (l == 1)
-                k_dwt_syn<true><<<grid, 256, 0, st>>>(C[1], Yc, Xc, Zc, nullptr, gm_out, g.Bx, c, inv_c, c > 0);
-            else
-                k_dwt_syn<false><<<grid, 256, 0, st>>>(C[l], Yc, Xc, Zc, C[l - 1], gm_out, 0, 0, 0.f, 0);
-        }
-    }
+    const GroupOut gm_out = group_major(gm, nullptr, g.N);
+    if (g.N == 8)
+        launch_levels<3>(g, img, pitch, ofs, C, sigma, tau_a, tau_b, cycle_spins, gm_out, st);
+    else
+        launch_levels<4>(g, img, pitch, ofs, C, sigma, tau_a, tau_b, cycle_spins, gm_out, st);
     const int G = g.By * g.Bx;
-    const int tb = (G + kTvWarps - 1) / kTvWarps;
-    switch (g.K) {
-    case 8: k_tv<8><<<tb, kTvWarps * 32, 0, st>>>(gm, G, eps_w, out, permute); break;
-    case 16: k_tv<16><<<tb, kTvWarps * 32, 0, st>>>(gm, G, eps_w, out, permute); break;
-    default: k_tv<32><<<tb, kTvWarps * 32, 0, st>>>(gm, G, eps_w, out, permute); break;
+    if (g.N == 8) {
+        switch (g.K) {
+        case 8: launch_tv<8, 8>(gm, G, eps_w, out, permute, st); break;
+        case 16: launch_tv<16, 8>(gm, G, eps_w, out, permute, st); break;
+        default: launch_tv<32, 8>(gm, G, eps_w, out, permute, st); break;
+        }
+    } else {
+        switch (g.K) {
+        case 8: launch_tv<8, 16>(gm, G, eps_w, out, permute, st); break;
+        case 16: launch_tv<16, 16>(gm, G, eps_w, out, permute, st); break;
+        default: launch_tv<32, 16>(gm, G, eps_w, out, permute, st); break;
+        }
     }
     return cudaGetLastError();
 }

@@ -10,7 +10,8 @@
 
 namespace gbm3d {
 
-constexpr int kPatch = 8;      // the block side this build is specialised for
+constexpr int kPatch = 8;      // block side of the Wiener filter and of the tensor-core matcher
+constexpr int kMaxPatch = 16;  // largest block side (stage 1 of the Sec. 5 parameters)
 constexpr int kMaxK = 32;      // largest group size (one warp lane per list slot)
 constexpr size_t kAlign = 256; // workspace sub-buffer alignment
 
@@ -31,30 +32,30 @@ __host__ __device__ inline int grid_pos(int p, int s, int M, int N)
     return v < M - N ? v : M - N;
 }
 
-// Top-left (k, l) of block position pos = k*W + l, clamped so that an
-// out-of-range entry in a caller-supplied match list can never address
-// memory outside the image (such entries yield garbage, not a fault).
-__device__ __forceinline__ void block_kl(int pos, int H, int W, int &k, int &l)
+// Top-left (k, l) of the N x N block at position pos = k*W + l, clamped so
+// that an out-of-range entry in a caller-supplied match list can never
+// address memory outside the image (such entries yield garbage, not a fault).
+__device__ __forceinline__ void block_kl(int pos, int H, int W, int N, int &k, int &l)
 {
     if (pos < 0 || pos >= H * W) pos = 0;
     k = pos / W;
     l = pos - k * W;
-    k = k < H - kPatch ? k : H - kPatch;
-    l = l < W - kPatch ? l : W - kPatch;
+    k = k < H - N ? k : H - N;
+    l = l < W - N ? l : W - N;
 }
 
-// True when pos is a valid block top-left for an H x W image.
-__device__ __forceinline__ bool block_ok(int pos, int H, int W)
+// True when pos is a valid N x N block top-left for an H x W image.
+__device__ __forceinline__ bool block_ok(int pos, int H, int W, int N)
 {
     if (pos < 0 || pos >= H * W) return false;
     const int k = pos / W, l = pos - k * W;
-    return k <= H - kPatch && l <= W - kPatch;
+    return k <= H - N && l <= W - N;
 }
 
 // Where the filters put block r of group g (entry e = g*K + r), row a:
-//   base + slot(e) * s_slot + a * s_row   (8 consecutive floats, b = 0..7),
+//   base + slot(e) * s_slot + a * s_row   (N consecutive floats, b = 0..N-1),
 // slot(e) = slot_of[e] (position-sorted order used by the aggregation) or e
-// itself (the group-major [G][K][8][8] layout of the public calls).  Weights
+// itself (the group-major [G][K][N][N] layout of the public calls).  Weights
 // go to w[g] (per_slot = 0) or to w[slot(e)] for each of the group's K
 // entries (per_slot = 1).
 struct GroupOut {
@@ -67,28 +68,29 @@ struct GroupOut {
     __device__ __forceinline__ float *row(long long e, int a) const { return base + slot(e) * s_slot + a * s_row; }
 };
 
-inline GroupOut group_major(float *groups, float *w)
+inline GroupOut group_major(float *groups, float *w, int N)
 {
-    return GroupOut{groups, nullptr, 64, 8, w, 0};
+    return GroupOut{groups, nullptr, (long long)N * N, N, w, 0};
 }
 
-inline GroupOut position_planar(float *planes, const int *slot_of, long long n_entries, float *w_slot)
+inline GroupOut position_planar(float *planes, const int *slot_of, long long n_entries, float *w_slot, int N)
 {
-    return GroupOut{planes, slot_of, 8, n_entries * 8, w_slot, 1};
+    return GroupOut{planes, slot_of, N, n_entries * N, w_slot, 1};
 }
 
 // Geometry of the stage-1 mosaic volume and of its wavelet pyramid.
 struct HtGeom {
+    int N;                  // block side (8 or 16)
     int By, Bx, K;          // groups along y, x; blocks per group
     int Yd, Xd;             // mosaic dims (By*N, Bx*N)
     int levels;
     size_t level_elems[4];  // elements of the coefficient buffer of level l (1-based)
     size_t level_off[4];    // byte offset of each level buffer in the HT scratch
     size_t ofs_off;         // byte offset of the pixel-offset table (G*K ints)
-    size_t gm_off;          // byte offset of the group-major block scratch (G*K*64 floats)
+    size_t gm_off;          // byte offset of the group-major block scratch (G*K*N*N floats)
     size_t bytes;           // total HT scratch
 };
-HtGeom ht_geom(int By, int Bx, int K, int levels);
+HtGeom ht_geom(int By, int Bx, int K, int levels, int N);
 
 struct AggLayout {
     size_t cnt, off, cursor, list, slot_of, lpos, bsum, bytes; // byte offsets and total
@@ -98,10 +100,11 @@ AggLayout agg_layout(int H, int W, int G, int K, bool with_slots = false);
 
 // Inverted match lists (block position -> entries, entries ascending within a
 // position) in the aggregation scratch; with_slots also fills slot_of.
-cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, void *agg_ws, bool with_slots,
+// N: block side (entries that are not valid N x N block positions are skipped).
+cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, int N, void *agg_ws, bool with_slots,
                       cudaStream_t st);
 
-size_t match_smem_bytes(int s, int R);
+size_t match_smem_bytes(int s, int R, int N);
 
 // Size of the fixed device scratch used by gbm3d_aggregate_noalloc, and its
 // device address on the current device (looked up once per device).
@@ -109,14 +112,15 @@ constexpr size_t kFixedScratchBytes = size_t(8) << 20;
 cudaError_t fixed_scratch(void **ptr);
 
 // ---- launch wrappers (each returns cudaGetLastError()) -------------------
-cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+// Direct FP32 block matching, N = 8 or 16.
+cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int N, int s, int R, int K,
                          int32_t *idx, float *dist, cudaStream_t st);
 
 // Tensor-core matching (same results as launch_match, bit for bit) where the
 // geometry fits (N = 8, union of 8 grid columns' windows <= 64 columns,
 // K <= 32); it ends with launch_match_fix, which re-matches with the direct
 // kernel the references it marked (slot 0 < 0).
-bool match_tc_supported(int H, int W, int s, int R, int K);
+bool match_tc_supported(int H, int W, int N, int s, int R, int K);
 cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                             int32_t *idx, float *dist, cudaStream_t st);
 cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
@@ -135,12 +139,13 @@ cudaError_t launch_filter_wiener(const float *noisy, int npitch, const float *pi
                                  cudaStream_t st);
 
 // Aggregation from the position-planar layout written through a GroupOut
-// made by position_planar() with the slot_of of build_csr.
-cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, int n_entries, int H, int W,
-                                    int pitch, const float *window8, float *out, const void *agg_ws, cudaStream_t st);
+// made by position_planar() with the slot_of of build_csr.  window: the N
+// per-axis window factors.
+cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, int n_entries, int H, int W, int N,
+                                    int pitch, const float *window, float *out, const void *agg_ws, cudaStream_t st);
 
 cudaError_t launch_aggregate(const float *groups, const float *w, const int32_t *idx, int G, int K, int H, int W,
-                             int pitch, const float *window8, float *out, void *agg_ws, cudaStream_t st);
+                             int N, int pitch, const float *window, float *out, void *agg_ws, cudaStream_t st);
 
 cudaError_t launch_shift(const float *src, int spitch, float *dst, int dpitch, int H, int W, int h, float scale,
                          int accumulate, cudaStream_t st);

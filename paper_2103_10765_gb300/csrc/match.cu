@@ -4,7 +4,9 @@
 // One warp per reference block, eight references (consecutive grid columns
 // of one grid row) per CTA sharing one shared-memory copy of their search
 // region.  The reference block lives in registers (64 floats per lane, the
-// same in every lane); each lane takes four vertically stacked candidates at
+// same in every lane; a 16 x 16 block, 256 floats, would not fit, so there
+// the lanes hold 4 of its rows at a time and reload the next 4 from shared
+// memory, a broadcast read); each lane takes four vertically stacked candidates at
 // a time, so every 8-pixel image row it loads from shared memory serves up
 // to four candidate rows (11 row loads per 4 candidates instead of 32).
 // Distances are the exact sum of squared differences in FP32 -- the direct
@@ -207,12 +209,19 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
     float *wb_d = buf_d + warp * kBuf;
     int *wb_i = buf_i + warp * kBuf;
 
-    f2 r[N][N / 2]; // negated reference block, column pairs (b, b+1) packed
+    // negated reference block rows a0 .. a0+NA-1, column pairs (b, b+1) packed:
+    // all of it for N = 8, four rows at a time for N = 16
+    constexpr int NA = N <= 8 ? N : 4;
+    f2 r[NA][N / 2];
+    auto load_ref = [&](int a0) {
 #pragma unroll
-    for (int a = 0; a < N; a++)
+        for (int a = 0; a < NA; a++)
 #pragma unroll
-        for (int b = 0; b < N; b += 2)
-            r[a][b / 2] = pack2(-sm[(i - ry0 + a) * rw + (j - rx0 + b)], -sm[(i - ry0 + a) * rw + (j - rx0 + b + 1)]);
+            for (int b = 0; b < N; b += 2)
+                r[a][b / 2] = pack2(-sm[(i - ry0 + a0 + a) * rw + (j - rx0 + b)],
+                                    -sm[(i - ry0 + a0 + a) * rw + (j - rx0 + b + 1)]);
+    };
+    if (NA == N) load_ref(0);
 
     const int k0 = ry0, k1 = min(H - N, i + R);
     const int l0 = max(0, j - R), l1 = min(W - N, j + R);
@@ -249,17 +258,22 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
             // region, odd ones in the shifted copy (rw is even)
             const int cc = (k - ry0) * rw + (l - rx0);
             const f2 *base = reinterpret_cast<const f2 *>((cc & 1) ? smB + cc + 1 : sm + cc);
+            // rows a of the block in ascending order for every candidate
+#pragma unroll 1
+            for (int a0 = 0; a0 < N; a0 += NA) {
+                if (NA < N) load_ref(a0);
 #pragma unroll
-            for (int t = 0; t < kVB + N - 1; t++) {
-                f2 x[N / 2];
+                for (int t = 0; t < kVB + NA - 1; t++) {
+                    f2 x[N / 2];
 #pragma unroll
-                for (int b = 0; b < N / 2; b++) x[b] = base[t * (rw / 2) + b];
+                    for (int b = 0; b < N / 2; b++) x[b] = base[(a0 + t) * (rw / 2) + b];
 #pragma unroll
-                for (int c = 0; c < kVB; c++) {
-                    const int a = t - c;
-                    if (a >= 0 && a < N) {
+                    for (int c = 0; c < kVB; c++) {
+                        const int a = t - c;
+                        if (a >= 0 && a < NA) {
 #pragma unroll
-                        for (int b = 0; b < N / 2; b++) dd[c] = sqdiff_acc2(r[a][b], x[b], dd[c]);
+                            for (int b = 0; b < N / 2; b++) dd[c] = sqdiff_acc2(r[a][b], x[b], dd[c]);
+                        }
                     }
                 }
             }
@@ -356,7 +370,7 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
 }
 
 template <int N>
-__global__ void __launch_bounds__(kRefsPerCta * 32, 3) k_match(MatchArgs a)
+__global__ void __launch_bounds__(kRefsPerCta * 32, N <= 8 ? 3 : 2) k_match(MatchArgs a)
 {
     extern __shared__ float sm[];
     match_group<N, kRefsPerCta>(a, blockIdx.y, blockIdx.x * kRefsPerCta, sm);
@@ -394,18 +408,18 @@ struct MatchGeom {
     int copy_off, bufs_off; // floats: offset of the shifted copy, of the selection buffers
 };
 
-MatchGeom match_geom(int s, int R, int nrefs = kRefsPerCta)
+MatchGeom match_geom(int s, int R, int N, int nrefs = kRefsPerCta)
 {
     MatchGeom g;
     g.col_pad = (2 * R + 1 + 7) / 8 * 8;
     // widest row a lane can touch: (l0 - rx0) <= (nrefs-1) s, plus the
     // padded column count, plus the block width
-    int need = (nrefs - 1) * s + g.col_pad + kPatch;
-    const int data = (nrefs - 1) * s + 2 * R + kPatch;
+    int need = (nrefs - 1) * s + g.col_pad + N;
+    const int data = (nrefs - 1) * s + 2 * R + N;
     if (data > need) need = data;
     g.rw = need; // kVB * rw == col_pad (mod 32)
     while ((kVB * g.rw - g.col_pad) % 32 != 0) g.rw++;
-    g.rows = 2 * R + kPatch + kVB;
+    g.rows = 2 * R + N + kVB;
     // the shifted copy starts 14 words (mod 32) after the region so that the
     // even-column lanes (region) and odd-column lanes (copy) of a half-warp
     // fall on disjoint banks
@@ -416,29 +430,38 @@ MatchGeom match_geom(int s, int R, int nrefs = kRefsPerCta)
 
 } // namespace
 
-size_t match_smem_bytes(int s, int R)
+size_t match_smem_bytes(int s, int R, int N)
 {
-    const MatchGeom g = match_geom(s, R);
+    const MatchGeom g = match_geom(s, R, N);
     return (size_t)g.bufs_off * sizeof(float) + (size_t)kRefsPerCta * kBuf * (sizeof(float) + sizeof(int));
 }
 
-cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
-                         int32_t *idx, float *dist, cudaStream_t st)
+template <int N>
+static cudaError_t launch_match_n(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+                                  int32_t *idx, float *dist, cudaStream_t st)
 {
-    const MatchGeom g = match_geom(s, R);
-    const size_t smem = match_smem_bytes(s, R);
-    cudaError_t e = cudaFuncSetAttribute(k_match<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const MatchGeom g = match_geom(s, R, N);
+    const size_t smem = match_smem_bytes(s, R, N);
+    cudaError_t e = cudaFuncSetAttribute(k_match<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kRefsPerCta - 1) / kRefsPerCta, By);
     const MatchArgs a{img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, g.copy_off, g.bufs_off, idx, dist};
-    k_match<kPatch><<<grid, kRefsPerCta * 32, smem, st>>>(a);
+    k_match<N><<<grid, kRefsPerCta * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int N, int s, int R, int K,
+                         int32_t *idx, float *dist, cudaStream_t st)
+{
+    if (N == 16) return launch_match_n<16>(img, H, W, pitch, By, Bx, s, R, K, idx, dist, st);
+    if (N == 8) return launch_match_n<8>(img, H, W, pitch, By, Bx, s, R, K, idx, dist, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                              int32_t *idx, float *dist, cudaStream_t st)
 {
-    const MatchGeom g = match_geom(s, R, 1);
+    const MatchGeom g = match_geom(s, R, kPatch, 1);
     const size_t smem = (size_t)g.bufs_off * sizeof(float) + (size_t)kBuf * (sizeof(float) + sizeof(int));
     cudaError_t e = cudaFuncSetAttribute(k_match_fix<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -811,10 +811,10 @@ TcLayout tc_layout(int H, int s, int R, int K)
     return t;
 }
 
-bool match_tc_supported(int H, int W, int s, int R, int K)
+bool match_tc_supported(int H, int W, int N, int s, int R, int K)
 {
     (void)W;
-    if (K < 2 || K > kMaxK) return false;
+    if (N != kPatch || K < 2 || K > kMaxK) return false;
     if ((kTileX - 1) * s + 2 * R + 1 > kChunkCols) return false; // union width must fit one chunk row
     const TcLayout t = tc_layout(H, s, R, K);
     if ((t.reg_rows - kPatch + 1) / kChunkRows > 128) return false; // chunk order table

@@ -140,7 +140,7 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
     const int r = t >> 3, a = t & 7; // row and column passes: (block r, row/column a)
     if (t < K) {
         int k, l;
-        block_kl(__ldg(idx + (size_t)g * K + t), H, W, k, l);
+        block_kl(__ldg(idx + (size_t)g * K + t), H, W, kPatch, k, l);
         s_zoff[t] = (long long)k * npitch + l;
         s_poff[t] = (long long)k * ppitch + l;
         s_slot[t] = out.slot((long long)g * K + t);

@@ -29,7 +29,7 @@ class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("patch", "step", "search_radius", "k1", "k2", "levels", "cycle_spins", "translations", "stages")] + \
                [(n, ctypes.c_float) for n in ("tau_a", "tau_b", "kaiser_beta", "eps_w")] + \
-               [("match_engine", ctypes.c_int)]
+               [(n, ctypes.c_int) for n in ("match_engine", "patch2", "step2")]
 
     def replace(self, **kw) -> "Params":
         q = Params()
@@ -59,6 +59,7 @@ def load(build_if_missing: bool = True):
     lib = ctypes.CDLL(path)
     vp, ci, cf, P = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.POINTER(Params)
     lib.gbm3d_params_default.argtypes = [P, ci]
+    lib.gbm3d_params_stage.argtypes = [P, ci, P]
     lib.gbm3d_grid_dims.argtypes = [ci, ci, P, ctypes.POINTER(ci), ctypes.POINTER(ci)]
     lib.gbm3d_workspace_bytes.argtypes = [ci, ci, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.gbm3d_match.argtypes = [vp, ci, ci, ci, P, ci, vp, vp, vp, vp]
@@ -73,7 +74,7 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_match_stats.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.gbm3d_last_error_string.restype = ctypes.c_char_p
     lib.gbm3d_version.restype = ctypes.c_char_p
-    for name in ("gbm3d_params_default", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
+    for name in ("gbm3d_params_default", "gbm3d_params_stage", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
                  "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise",
                  "gbm3d_aggregate_noalloc", "gbm3d_match_stats", "gbm3d_set_match_events",
                  "gbm3d_workspace_bytes_color", "gbm3d_denoise_color"):
@@ -91,6 +92,14 @@ def params_default(preset: int = 0) -> Params:
     p = Params()
     _check(load().gbm3d_params_default(ctypes.byref(p), preset))
     return p
+
+
+def params_stage(p: Params, stage: int) -> Params:
+    """The block-level parameters of stage 1 or 2 of the whole method
+    (gbm3d_params_stage: patch / step set to that stage's block side and stride)."""
+    q = Params()
+    _check(load().gbm3d_params_stage(ctypes.byref(p), stage, ctypes.byref(q)))
+    return q
 
 
 def grid_dims(H: int, W: int, p: Params | None = None):
@@ -165,33 +174,6 @@ def denoise_color(noisy: torch.Tensor, sigma: float, p: Params | None = None, ws
     return out
 
 
-def workspace_bytes_color(H: int, W: int, p: Params | None = None) -> int:
-    p = p or params_default()
-    n = ctypes.c_size_t()
-    _check(load().gbm3d_workspace_bytes_color(H, W, ctypes.byref(p), ctypes.byref(n)))
-    return n.value
-
-
-def denoise_color(noisy: torch.Tensor, sigma: float, p: Params | None = None, ws: torch.Tensor | None = None,
-                  out: torch.Tensor | None = None) -> torch.Tensor:
-    """Colour G-BM3D of a (3, H, W) float32 CUDA tensor of R, G, B planes
-    (rows contiguous; any row pitch and plane stride)."""
-    p = p or params_default()
-    if not (noisy.is_cuda and noisy.dtype == torch.float32 and noisy.dim() == 3 and noisy.shape[0] == 3
-            and noisy.stride(2) == 1):
-        raise ValueError("noisy must be a (3, H, W) float32 CUDA tensor with unit column stride")
-    _, H, W = noisy.shape
-    if ws is None:
-        ws = torch.empty(max(workspace_bytes_color(H, W, p), 1), dtype=torch.uint8, device=noisy.device)
-    if out is None:  # the same row pitch and plane stride as noisy (one pair for both in the ABI)
-        out = torch.empty_strided(noisy.shape, noisy.stride(), dtype=torch.float32, device=noisy.device)
-    if out.stride() != noisy.stride() or out.shape != noisy.shape:
-        raise ValueError("out must have the shape and strides of noisy")
-    _check(load().gbm3d_denoise_color(_ptr(noisy), H, W, noisy.stride(1), noisy.stride(0), float(sigma),
-                                      ctypes.byref(p), _ptr(out), _ptr(ws), _stream(noisy)))
-    return out
-
-
 _match_events_keep = None
 
 
@@ -220,12 +202,12 @@ def match_stats():
 
 def filter_ht(noisy: torch.Tensor, idx: torch.Tensor, sigma: float, p: Params | None = None,
               ws: torch.Tensor | None = None):
-    """Stage-1 global hard thresholding: (groups [G, K1, 8, 8], w [G])."""
+    """Stage-1 global hard thresholding: (groups [G, K1, N, N], w [G]), N = p.patch."""
     p = p or params_default()
     H, W, pitch = _img(noisy, "noisy")
     G = idx.shape[0]
     ws = ws if ws is not None else workspace(H, W, p, noisy.device)
-    groups = torch.empty((G, p.k1, 8, 8), dtype=torch.float32, device=noisy.device)
+    groups = torch.empty((G, p.k1, p.patch, p.patch), dtype=torch.float32, device=noisy.device)
     w = torch.empty(G, dtype=torch.float32, device=noisy.device)
     _check(load().gbm3d_filter_ht(_ptr(noisy), H, W, pitch, _ptr(idx.contiguous()), float(sigma), ctypes.byref(p),
                                   _ptr(groups), _ptr(w), _ptr(ws), _stream(noisy)))

@@ -42,10 +42,37 @@ def test_presets(g):
         (8, 3, 19, 16, 32, 3, 2, 1, 2)
     assert abs(p.tau_a - 3.6) < 1e-6 and abs(p.tau_b - 0.3) < 1e-6 and p.kaiser_beta == 2.0
     assert p.match_engine == 0
+    assert (p.patch2, p.step2) == (8, 3)
+    # Sec. 5: 16 x 16 tiling blocks in stage 1, 8 x 8 in stage 2, 32-pixel window, K = 16, 2 translations
     q = g.params_default(1)
-    assert (q.step, q.search_radius, q.k1, q.translations) == (8, 16, 16, 2)
+    assert (q.patch, q.step, q.patch2, q.step2, q.search_radius, q.k1, q.k2, q.levels, q.cycle_spins,
+            q.translations, q.stages) == (16, 16, 8, 8, 16, 16, 16, 3, 2, 2, 2)
     with pytest.raises(g.Gbm3dError):
         g.params_default(7)
+
+
+def test_params_stage(g, orc):
+    q = g.params_default(1)
+    s1, s2 = g.params_stage(q, 1), g.params_stage(q, 2)
+    assert (s1.patch, s1.step, s1.patch2, s1.step2) == (16, 16, 0, 0)
+    assert (s2.patch, s2.step, s2.patch2, s2.step2) == (8, 8, 0, 0)
+    assert (s1.k1, s1.k2, s1.translations) == (q.k1, q.k2, q.translations)
+    assert g.grid_dims(1024, 1024, s1) == (64, 64) and g.grid_dims(1024, 1024, s2) == (128, 128)
+    for H, W in ((100, 77), (48, 40)):
+        assert g.grid_dims(H, W, s1) == (len(orc.grid(H, 16, 16)), len(orc.grid(W, 16, 16)))
+    p0 = g.params_default(0)
+    t = g.params_stage(p0, 2)
+    assert (t.patch, t.step) == (8, 3)
+    with pytest.raises(g.Gbm3dError):
+        g.params_stage(q, 3)
+
+
+def test_workspace_covers_both_stage_geometries(g):
+    q = g.params_default(1)
+    n = g.workspace_bytes(1024, 1024, q)
+    # stage-1 mosaic pyramid (64*16)^2 * 16 floats plus stage-2 blocks 128^2 * 16 * 64 floats
+    assert n > (1024 * 1024 * 16 + 128 * 128 * 16 * 64) * 4
+    assert g.workspace_bytes(1024, 1024) > n  # s = 3 overlapping grids need far more
 
 
 def test_grid_dims_closed_form(g, orc):
@@ -90,7 +117,8 @@ def test_validation_errors(g):
     # search window too small for K: 9 x 9 image has 2 x 2 block positions
     assert lib.gbm3d_match(fake, 9, 9, 9, P, 16, fake, None, None, None) == g.EINVAL
     # unsupported parameters
-    for bad in (dict(patch=16), dict(k1=64), dict(levels=4), dict(k2=12), dict(translations=4)):
+    for bad in (dict(patch=12), dict(patch2=4), dict(step2=-1), dict(k1=64), dict(levels=4), dict(k2=12),
+                dict(translations=4)):
         q = p.replace(**bad)
         st = lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None)
         assert st in (g.EINVAL, g.EUNSUPPORTED), bad
@@ -109,6 +137,19 @@ def test_validation_errors(g):
     # unsupported group size for aggregation
     assert lib.gbm3d_aggregate(fake, fake, fake, 12, 64, 64, 64, P, ctypes.c_float(0.0), fake, fake,
                                None) == g.EUNSUPPORTED
+    # the Wiener filter is built for 8 x 8 blocks: 16 x 16 in stage 2 is refused before any launch
+    q = p.replace(patch=16, patch2=16)
+    assert lib.gbm3d_denoise(fake, 64, 64, 64, ctypes.c_float(0.1), ctypes.byref(q), ctypes.c_void_p(0x2000),
+                             ctypes.c_void_p(0x4000), None) == g.EUNSUPPORTED
+    assert lib.gbm3d_filter_wiener(fake, fake, 64, 64, 64, fake, ctypes.c_float(0.1), ctypes.byref(q),
+                                   ctypes.c_void_p(0x3000), fake, None, None) == g.EUNSUPPORTED
+    # tensor-core matching is for 8 x 8 blocks
+    q = g.params_default(1).replace(match_engine=2)
+    assert lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None) == g.EUNSUPPORTED
+    # the image must hold the largest block of the stages
+    q = g.params_default(1)
+    assert lib.gbm3d_denoise(fake, 12, 64, 64, ctypes.c_float(0.1), ctypes.byref(q), ctypes.c_void_p(0x2000),
+                             ctypes.c_void_p(0x4000), None) == g.EINVAL
 
 
 def test_color_validation(g):

@@ -1,6 +1,7 @@
 """The multi-rank benchmark path on CPU: two gloo ranks, as torch.distributed.run
 would start them.  The path runs independent replicas (one image stream per
 GPU); the only collective is the max over ranks of the timed region."""
+import ctypes
 import os
 import socket
 
@@ -71,9 +72,34 @@ def test_launch_count_matches_launch_list():
     # them the bench's L2-flush fill)
     import bench
     from types import SimpleNamespace
-    p = SimpleNamespace(cycle_spins=2, levels=3, stages=2)
+    p = SimpleNamespace(cycle_spins=2, levels=3, stages=2, translations=1)
     assert bench.launches_per_denoise(p, 1) == 35 == (142 - 2) // 4
     assert bench.launches_per_denoise(p, 3) == 71
+    # Sec. 5 preset: direct matching in both stages, 2 translations with their shifts
+    q = SimpleNamespace(cycle_spins=2, levels=3, stages=2, translations=2)
+    assert bench.launches_per_denoise(q, 1, (False, False)) == 2 * (1 + 7 + 15 + 2) + 2 * (1 + 7 + 2 + 3)
+
+
+def test_engine_choice_mirrors_library():
+    import bench
+    from paper_2103_10765_gb300 import build, gbm3d
+    build.build_library()
+    lib = gbm3d.load()
+    for preset in (0, 1):
+        p = gbm3d.params_default(preset)
+        for stage in (1, 2):
+            g = gbm3d.params_stage(p, stage)
+            K = p.k1 if stage == 1 else p.k2
+            expect = bench.tc_supported(1024, 1024, g.patch, g.step, p.search_radius, K)
+            q = g.replace(match_engine=2)
+            if not expect:
+                # engine 2 on an unsupported geometry is refused on the host, before any
+                # launch (the pointers are never dereferenced)
+                fake = ctypes.c_void_p(0x1000)
+                st = lib.gbm3d_match(fake, 1024, 1024, 1024, ctypes.byref(q), K, fake, None, None, None)
+                assert st == gbm3d.EUNSUPPORTED, (preset, stage)
+    assert bench.tc_supported(1024, 1024, 8, 3, 19, 16) and bench.tc_supported(1024, 1024, 8, 3, 19, 32)
+    assert not bench.tc_supported(1024, 1024, 8, 8, 16, 16) and not bench.tc_supported(1024, 1024, 16, 16, 16, 16)
 
 
 def test_clock_sampler_keeps_only_timed_window(tmp_path, monkeypatch):

@@ -41,7 +41,7 @@ def block_d(X, i, j, idx, W, N=8):
     return np.array([np.sum((ref - X[v // W:v // W + N, v % W:v % W + N]) ** 2) for v in idx])
 
 
-def check_match(X, gidx, gdist, oidx, odist, W, K, refs):
+def check_match(X, gidx, gdist, oidx, odist, W, K, refs, N=8):
     """Compare GPU lists (K) with oracle lists computed with K+1 slots."""
     X = X.astype(np.float64)
     exact = 0
@@ -50,7 +50,7 @@ def check_match(X, gidx, gdist, oidx, odist, W, K, refs):
         assert g[0] == i * W + j
         assert len(set(g.tolist())) == K
         od = odist[t]
-        gd = block_d(X, i, j, g[1:], W)
+        gd = block_d(X, i, j, g[1:], W, N)
         # GPU's own FP32 distances agree with FP64
         np.testing.assert_allclose(gdist[t, 1:], gd, rtol=1e-5, atol=TIE)
         # every chosen block is among the K best up to the tie tolerance
@@ -68,8 +68,8 @@ def check_match(X, gidx, gdist, oidx, odist, W, K, refs):
     return exact / len(refs)
 
 
-def grid_refs(orc, H, W):
-    return [(int(i), int(j)) for i in orc.grid(H, 8, 3) for j in orc.grid(W, 8, 3)]
+def grid_refs(orc, H, W, N=8, s=3):
+    return [(int(i), int(j)) for i in orc.grid(H, N, s) for j in orc.grid(W, N, s)]
 
 
 @pytest.mark.parametrize("H,W,sigma,K", [(64, 72, 25, 16), (100, 83, 25, 32), (13, 13, 50, 32), (13, 45, 15, 16),
@@ -243,3 +243,97 @@ def test_denoise_4096_runs():
     p_noisy = 10 * np.log10(1 / np.mean((X.astype(np.float64) - c) ** 2))
     p_out = 10 * np.log10(1 / np.mean((out - c) ** 2))
     assert p_out > p_noisy + 8, (p_noisy, p_out)
+
+
+# ---- the Sec. 5 parameter list: 16 x 16 tiling blocks in stage 1, 8 x 8 in stage 2
+
+def paper_stage(stage, **kw):
+    return gbm3d.params_stage(gbm3d.params_default(1), stage).replace(**kw)
+
+
+@pytest.mark.parametrize("H,W,sigma,K,s", [(64, 72, 25, 16, 16), (100, 83, 25, 32, 5), (37, 45, 50, 16, 3),
+                                           (16, 40, 15, 8, 16), (48, 48, 0, 16, 16)])
+def test_match_n16_parity(orc, H, W, sigma, K, s):
+    _, X = synth.make_pair(H, W, sigma / 255, 2)
+    p = paper_stage(1, step=s)
+    gidx, gdist = gbm3d.match(gpu(X), K, p, with_dist=True)
+    oidx, odist = orc.match(X, N=16, s=s, R=16, K=K + 1, nthreads=NT)
+    frac = check_match(X, gidx.cpu().numpy(), gdist.cpu().numpy(), oidx, odist, W, K,
+                       grid_refs(orc, H, W, 16, s), N=16)
+    assert frac > 0.9
+
+
+@pytest.mark.parametrize("H,W,sigma,C,K", [(64, 80, 25, 2, 16), (100, 83, 50, 2, 16), (48, 48, 15, 1, 8),
+                                           (32, 32, 25, 2, 32), (16, 40, 25, 3, 16)])
+def test_filter_ht_n16_parity(orc, H, W, sigma, C, K):
+    _, X = synth.make_pair(H, W, sigma / 255, 3)
+    p = paper_stage(1, cycle_spins=C, k1=K)
+    z = gpu(X)
+    idx, _ = gbm3d.match(z, K, p)
+    groups, w = gbm3d.filter_ht(z, idx, sigma / 255, p)
+    assert groups.shape[2:] == (16, 16)
+    by, bx = gbm3d.grid_dims(H, W, p)
+    og, ow = orc.filter_ht(X, idx.cpu().numpy(), sigma / 255, by, bx, N=16, K=K, C=C)
+    assert np.abs(groups.cpu().numpy() - og).max() <= ATOL
+    np.testing.assert_allclose(w.cpu().numpy(), ow, rtol=ATOL)
+
+
+@pytest.mark.parametrize("beta,s", [(0.0, 16), (2.0, 5)])
+def test_aggregate_n16_parity(orc, beta, s):
+    H, W = 77, 64
+    _, X = synth.make_pair(H, W, 0.1, 2)
+    p = paper_stage(1, step=s)
+    idx, _ = gbm3d.match(gpu(X), 16, p)
+    G = idx.shape[0]
+    rs = np.random.default_rng(3)
+    groups = rs.standard_normal((G, 16, 16, 16)).astype(np.float32)
+    w = (rs.random(G) + 0.1).astype(np.float32)
+    out = gbm3d.aggregate(gpu(groups), gpu(w), idx, H, W, p, window_beta=beta)
+    ref = orc.aggregate(groups, w, idx.cpu().numpy(), H, W, N=16, beta=beta)
+    assert np.abs(out.cpu().numpy() - ref).max() <= ATOL
+
+
+@pytest.mark.parametrize("H,W,sigma", [(64, 80, 25), (100, 83, 50)])
+def test_paper_preset_chained_parity(orc, H, W, sigma):
+    """Each stage of the Sec. 5 preset against the oracle's filter and
+    aggregation driven by the GPU's own match lists."""
+    s = sigma / 255
+    _, X = synth.make_pair(H, W, s, 2)
+    q = gbm3d.params_default(1).replace(translations=1)
+    z = gpu(X)
+    y1 = gbm3d.denoise(z, s, q.replace(stages=1))
+    p1, p2 = gbm3d.params_stage(q, 1), gbm3d.params_stage(q, 2)
+    idx1, _ = gbm3d.match(z, q.k1, p1)
+    by, bx = gbm3d.grid_dims(H, W, p1)
+    og, ow = orc.filter_ht(X, idx1.cpu().numpy(), s, by, bx, N=16, K=q.k1)
+    oy1 = orc.aggregate(og, ow, idx1.cpu().numpy(), H, W, N=16)
+    assert np.abs(y1.cpu().numpy() - oy1).max() <= ATOL
+    y2 = gbm3d.denoise(z, s, q)
+    idx2, _ = gbm3d.match(y1, q.k2, p2)
+    og2, ow2 = orc.filter_wiener(X, y1.cpu().numpy(), idx2.cpu().numpy(), s, N=8, K=q.k2, nthreads=NT)
+    oy2 = orc.aggregate(og2, ow2, idx2.cpu().numpy(), H, W, N=8, beta=2.0)
+    assert np.abs(y2.cpu().numpy() - oy2).max() <= ATOL
+
+
+@pytest.mark.parametrize("H,W,sigma", [(96, 128, 25), (256, 256, 15), (512, 512, 50), (1024, 1024, 25)])
+def test_paper_preset_end_to_end_psnr(orc, H, W, sigma):
+    """The whole Sec. 5 preset (both stages, 2 translations with each stage's
+    own shifts) within 0.01 dB of the FP64 oracle."""
+    s = sigma / 255
+    clean, X = synth.make_pair(H, W, s, 1)
+    out = gbm3d.denoise(gpu(X), s, gbm3d.params_default(1)).cpu().numpy()
+    ref = orc.denoise(X, s, params=orc.Params.paper(), nthreads=NT)
+    pg, po = orc.psnr(out, clean), orc.psnr(ref, clean)
+    assert abs(pg - po) <= 0.01, (pg, po)
+    assert pg > orc.psnr(X, clean) + 5
+
+
+def test_paper_preset_sigma_zero_and_constant():
+    q = gbm3d.params_default(1)
+    _, X = synth.make_pair(48, 64, 0.0, 1)
+    out = gbm3d.denoise(gpu(X), 0.0, q).cpu().numpy()
+    assert np.abs(out - X).max() <= 1e-5
+    c, s = 0.45, 25 / 255
+    out = gbm3d.denoise(gpu(synth.constant_image(48, 40, c)), s, q).cpu().numpy()
+    P = c * 8 * np.sqrt(16)
+    assert np.abs(out - c * P ** 2 / (P ** 2 + s ** 2)).max() <= 1e-5
