@@ -145,3 +145,49 @@ def make_color_pair(H: int, W: int, sigma: float, scene_seed: int = 1):
 
 def constant_image(H: int, W: int, value: float = 0.5) -> np.ndarray:
     return np.full((H, W), value, dtype=np.float32)
+
+
+def degrade_blur(clean: np.ndarray, psf: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """Deconvolution input: the clean image circularly convolved with the
+    point-spread function psf (odd side, centred), plus white Gaussian noise of
+    deviation sigma from the noise seed; float32, not clipped.  This is the
+    degradation that produces test inputs, not a step of the restoration."""
+    x = clean.astype(np.float64)
+    r = psf.shape[0] // 2
+    y = np.zeros_like(x)
+    for a in range(-r, r + 1):
+        for b in range(-r, r + 1):
+            y += psf[a + r, b + r] * np.roll(x, (a, b), axis=(0, 1))
+    return (y + sigma * normals(seed, x.size).reshape(x.shape)).astype(np.float32)
+
+
+def gaussian_psf(size: int = 9, std: float = 1.6) -> np.ndarray:
+    """The k x k normalised Gaussian blur of the deconvolution workload (outer
+    product of a sampled 1-D Gaussian, summing to 1)."""
+    t = np.arange(size, dtype=np.float64) - size // 2
+    g = np.exp(-0.5 * (t / std) ** 2)
+    g /= g.sum()
+    return np.outer(g, g)
+
+
+def pnp_batch_specs(n: int = 64, seed: int = 7, lo: int = 128, hi: int = 1024):
+    """Sizes and noise levels of a batch of deconvolution problems: per image
+    H and W uniform over the multiples of 8 in [lo, hi] and sigma uniform in
+    [5, 50] / 255, all drawn from one SplitMix64 stream.  Returns a list of
+    (H, W, sigma, scene_seed)."""
+    u = uniforms(seed, 3 * n)
+    steps = (hi - lo) // 8 + 1
+    out = []
+    for i in range(n):
+        H = lo + 8 * min(int(u[3 * i] * steps), steps - 1)
+        W = lo + 8 * min(int(u[3 * i + 1] * steps), steps - 1)
+        sigma = (5.0 + 45.0 * float(u[3 * i + 2])) / 255.0
+        out.append((H, W, sigma, 100 + i))
+    return out
+
+
+def make_blur_pair(H: int, W: int, sigma: float, scene_seed: int = 1, psf_size: int = 9, psf_std: float = 1.6):
+    """(clean, blurred + noisy) float32 images for deconvolution; the noise
+    seed is 5000 + scene_seed."""
+    clean = clean_scene(H, W, scene_seed)
+    return clean, degrade_blur(clean, gaussian_psf(psf_size, psf_std), sigma, 5000 + scene_seed)
