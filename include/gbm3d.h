@@ -239,6 +239,69 @@ int gbm3d_match_stats(unsigned long long *timeouts, unsigned long long *rematche
  * real denoise.  The array must stay valid while set.  Always GBM3D_OK. */
 int gbm3d_set_match_events(void *events);
 
+/* ---- Plug-and-play ADMM deconvolution (Sec. 1: plug-and-play priors couple a
+ * denoiser with inverse problems such as deconvolution, one denoiser call per
+ * iteration; Sec. 6).  The paper does not state the iteration; the library runs
+ * the standard scaled-dual ADMM for y = h * x + n (circular convolution with a
+ * separable symmetric point-spread function h = g g^T, white noise sigma_n):
+ *   x <- (H^T H + rho I)^-1 (H^T y + rho (v - u))      (exact, see below)
+ *   v <- gbm3d_denoise(x + u, sigma_n / sqrt(rho))     (the data-term weight
+ *                                                       lambda = sigma_n^2)
+ *   u <- u + x - v
+ * from v = y, u = 0; the result is v after `iters` iterations.  The x-update
+ * is exact up to FP32 rounding: H^T H + rho I is diagonal in the separable
+ * discrete Hartley basis, applied as dense FP32 matrix products (any image
+ * side that is a multiple of 8).  A plan binds a batch of images of uneven
+ * sizes, each with its own sigma_n, to caller buffers. */
+typedef struct {
+    int iters;     /* ADMM iterations (>= 1)                                   */
+    float rho;     /* penalty (> 0); the denoiser runs at sigma_n / sqrt(rho)  */
+    int use_graph; /* 1: one iteration of all images captured as a CUDA graph, */
+                   /* one branch per image, replayed iters times; 0: the same  */
+                   /* launches image after image on the caller's stream.       */
+                   /* Same results, bit for bit.                               */
+    int autotune;  /* 1: time the tile shapes of the x-update's products per   */
+                   /* (M, N, K) at plan creation and keep the fastest (every   */
+                   /* shape gives the same bits); 0: the first shape           */
+} gbm3d_pnp_params;
+
+typedef struct gbm3d_pnp_plan_st *gbm3d_pnp_plan;
+
+/* Device scratch for a plan over n images of H[i] x W[i] (sides multiples of
+ * 8) denoised with *p: per image the gbm3d_denoise workspace and six H x W
+ * planes, plus the transform tables of every distinct side.  Host-only. */
+int gbm3d_pnp_workspace_bytes(int n, const int *H, const int *W, const gbm3d_params *p, size_t *bytes);
+
+/* Plan for n problems.  Host arrays of n entries: H, W; y[i] (device, the
+ * blurred noisy image, row pitch ypitch[i] elements); out[i] (device, result,
+ * pitch opitch[i]); sigma[i] (noise deviation sigma_n).  psf: host array of
+ * the 1-D factor g of the point-spread function, odd length psf_len <= 63,
+ * centred and symmetric (g[c-t] == g[c+t]); h[a][b] = g[a] g[b].  ws: device
+ * scratch of ws_bytes >= gbm3d_pnp_workspace_bytes, 256-byte aligned, owned
+ * by the caller and used by the plan until it is destroyed.  The call builds
+ * the transform tables on `stream`, autotunes (q->autotune), synchronises the
+ * stream and, with q->use_graph, captures the iteration graph (it creates
+ * streams, events and the graph; no device memory).  y, out and ws are bound
+ * to the plan: refill y and rerun.  EINVAL/ENOMEM/EUNSUPPORTED for bad
+ * arguments (before any launch), ECUDA if a CUDA call fails. */
+int gbm3d_pnp_plan_create(int n, const int *H, const int *W, const float *const *y, const int *ypitch,
+                          float *const *out, const int *opitch, const float *sigma, const float *psf,
+                          int psf_len, const gbm3d_params *p, const gbm3d_pnp_params *q, void *ws,
+                          size_t ws_bytes, gbm3d_stream_t stream, gbm3d_pnp_plan *plan);
+
+/* Runs the whole ADMM loop of every image of the plan on `stream`
+ * (asynchronous): H^T y and the start values, `iters` iterations, v copied to
+ * out.  EINVAL for a NULL plan, ECUDA on a failed launch. */
+int gbm3d_pnp_run(gbm3d_pnp_plan plan, gbm3d_stream_t stream);
+
+/* Frees the plan's host objects, streams, events and graph (not ws).  NULL
+ * is accepted.  Always GBM3D_OK. */
+int gbm3d_pnp_plan_destroy(gbm3d_pnp_plan plan);
+
+/* The tile shapes (0..3: 128x128, 128x64, 64x128, 64x64) the plan uses for
+ * image `image`'s products with contraction length H and W. */
+int gbm3d_pnp_gemm_config(gbm3d_pnp_plan plan, int image, int *cfg_k_h, int *cfg_k_w);
+
 /* Description of the last failure on this host thread ("" if none). */
 const char *gbm3d_last_error_string(void);
 

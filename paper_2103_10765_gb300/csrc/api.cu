@@ -29,6 +29,18 @@ static int cuda_fail(cudaError_t e, const char *where)
     return fail(GBM3D_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+int set_error(int code, const char *msg)
+{
+    return fail(code, "%s", msg);
+}
+
+cudaEvent_t *swap_match_events(cudaEvent_t *events)
+{
+    cudaEvent_t *old = g_match_events;
+    g_match_events = events;
+    return old;
+}
+
 static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // Block side and grid stride of a stage (stage 2: patch2 / step2 where set).

@@ -111,6 +111,11 @@ size_t match_smem_bytes(int s, int R, int N);
 constexpr size_t kFixedScratchBytes = size_t(8) << 20;
 cudaError_t fixed_scratch(void **ptr);
 
+// Sets the thread's last-error message (gbm3d_last_error_string) and returns code.
+int set_error(int code, const char *msg);
+// Replaces the thread's measurement-hook events (gbm3d_set_match_events); returns the old ones.
+cudaEvent_t *swap_match_events(cudaEvent_t *events);
+
 // ---- launch wrappers (each returns cudaGetLastError()) -------------------
 // Direct FP32 block matching, N = 8 or 16.
 cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int N, int s, int R, int K,

@@ -42,6 +42,15 @@ class Params(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class PnpParams(ctypes.Structure):
+    """Mirror of gbm3d_pnp_params (defaults: 50 iterations, rho 0.1, graph, autotune)."""
+    _fields_ = [("iters", ctypes.c_int), ("rho", ctypes.c_float), ("use_graph", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
+
+    def __init__(self, iters=50, rho=0.1, use_graph=1, autotune=1):
+        super().__init__(iters, rho, use_graph, autotune)
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -72,12 +81,21 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_workspace_bytes_color.argtypes = [ci, ci, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.gbm3d_denoise_color.argtypes = [vp, ci, ci, ci, ctypes.c_longlong, cf, P, vp, vp, vp]
     lib.gbm3d_match_stats.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
+    ip, fpp = ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_void_p)
+    lib.gbm3d_pnp_workspace_bytes.argtypes = [ci, ip, ip, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.gbm3d_pnp_plan_create.argtypes = [ci, ip, ip, fpp, ip, fpp, ip, ctypes.POINTER(cf), ctypes.POINTER(cf), ci, P,
+                                          ctypes.POINTER(PnpParams), vp, ctypes.c_size_t, vp,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+    lib.gbm3d_pnp_run.argtypes = [vp, vp]
+    lib.gbm3d_pnp_plan_destroy.argtypes = [vp]
+    lib.gbm3d_pnp_gemm_config.argtypes = [vp, ci, ip, ip]
     lib.gbm3d_last_error_string.restype = ctypes.c_char_p
     lib.gbm3d_version.restype = ctypes.c_char_p
     for name in ("gbm3d_params_default", "gbm3d_params_stage", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
                  "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise",
                  "gbm3d_aggregate_noalloc", "gbm3d_match_stats", "gbm3d_set_match_events",
-                 "gbm3d_workspace_bytes_color", "gbm3d_denoise_color"):
+                 "gbm3d_workspace_bytes_color", "gbm3d_denoise_color", "gbm3d_pnp_workspace_bytes",
+                 "gbm3d_pnp_plan_create", "gbm3d_pnp_run", "gbm3d_pnp_plan_destroy", "gbm3d_pnp_gemm_config"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -301,3 +319,71 @@ class HostDenoiser:
         self.host_out.copy_(self.dev_out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return self.host_out
+
+
+def _int_array(v):
+    return (ctypes.c_int * len(v))(*[int(x) for x in v])
+
+
+def pnp_workspace_bytes(shapes, p: Params | None = None) -> int:
+    """Scratch bytes of a plug-and-play plan over images of the given (H, W) shapes."""
+    p = p or params_default()
+    n = ctypes.c_size_t()
+    _check(load().gbm3d_pnp_workspace_bytes(len(shapes), _int_array([h for h, _ in shapes]),
+                                            _int_array([w for _, w in shapes]), ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+class PnpPlan:
+    """gbm3d_pnp_plan over a batch of blurred noisy device images ys[i] (2-D
+    float32 CUDA tensors, any sizes with sides multiples of 8) with noise
+    deviations sigmas[i]; psf is the 1-D factor g of the separable blur
+    (odd length, symmetric).  run() executes the whole ADMM loop on the
+    current stream; results land in self.outs.  The inputs are bound: write
+    new data into ys and call run() again."""
+
+    def __init__(self, ys, sigmas, psf, p: Params | None = None, q: PnpParams | None = None):
+        self.p = p or params_default()
+        self.q = q or PnpParams()
+        self.ys = list(ys)
+        dev = self.ys[0].device
+        shapes = []
+        for y in self.ys:
+            shapes.append(_img(y, "y")[:2])
+        self.outs = [torch.empty_like(y) for y in self.ys]
+        n = len(self.ys)
+        nbytes = pnp_workspace_bytes(shapes, self.p)
+        self.ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+        g = [float(v) for v in psf]
+        H, W = _int_array([h for h, _ in shapes]), _int_array([w for _, w in shapes])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in self.ys])
+        op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        ypitch = _int_array([y.stride(0) for y in self.ys])
+        opitch = _int_array([o.stride(0) for o in self.outs])
+        sig = (ctypes.c_float * n)(*[float(s) for s in sigmas])
+        psf_arr = (ctypes.c_float * len(g))(*g)
+        handle = ctypes.c_void_p()
+        _check(load().gbm3d_pnp_plan_create(n, H, W, yp, ypitch, op, opitch, sig, psf_arr, len(g),
+                                            ctypes.byref(self.p), ctypes.byref(self.q), _ptr(self.ws), nbytes,
+                                            _stream(self.ys[0]), ctypes.byref(handle)))
+        self._handle = handle
+
+    def run(self):
+        _check(load().gbm3d_pnp_run(self._handle, _stream(self.ys[0])))
+        return self.outs
+
+    def gemm_configs(self, i: int):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().gbm3d_pnp_gemm_config(self._handle, i, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_handle", None):
+            load().gbm3d_pnp_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -37,3 +37,9 @@ def orc():
 @pytest.fixture
 def rng():
     return np.random.default_rng(12345)
+
+
+@pytest.fixture(scope="session")
+def pnp_orc(orc):
+    from oracle import pnp
+    return pnp

@@ -187,3 +187,39 @@ def test_binding_fails_loudly_without_library(g, monkeypatch, tmp_path):
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         g.load(build_if_missing=False)
+
+
+def test_pnp_host_validation(g):
+    """Plug-and-play plan arguments are checked on the host before any launch."""
+    lib = g.load()
+    p = g.params_default()
+    shapes = [(128, 136), (64, 72)]
+    n = g.pnp_workspace_bytes(shapes, p)
+    per = sum(g.workspace_bytes(h, w, p) + 6 * h * w * 4 for h, w in shapes)
+    assert n >= per  # plus the transform tables of sides 64, 72, 128, 136
+    assert n - per >= 4 * (64 * 64 + 72 * 72 + 128 * 128 + 136 * 136)
+    with pytest.raises(g.Gbm3dError):
+        g.pnp_workspace_bytes([(100, 64)], p)  # sides must be multiples of 8
+    ci, cf, vp = ctypes.c_int, ctypes.c_float, ctypes.c_void_p
+    H, W = (ci * 1)(64), (ci * 1)(64)
+    ptrs = (vp * 1)(0x1000)
+    outs = (vp * 1)(0x2000)
+    pitch = (ci * 1)(64)
+    sig = (cf * 1)(0.1)
+    good = [0.25, 0.5, 1.0, 0.5, 0.25]
+    ws = vp(0x10000000)
+    big = 1 << 40
+
+    def create(psf=good, q=None, wsb=big, sigma=sig):
+        arr = (cf * len(psf))(*psf)
+        h = vp()
+        return lib.gbm3d_pnp_plan_create(1, H, W, ptrs, pitch, outs, pitch, sigma, arr, len(psf), ctypes.byref(p),
+                                         ctypes.byref(q or g.PnpParams()), ws, wsb, None, ctypes.byref(h))
+    assert create(psf=[0.5, 0.5]) == g.EINVAL             # even length
+    assert create(psf=[0.2, 0.5, 0.3]) == g.EINVAL        # not symmetric
+    assert create(q=g.PnpParams(rho=0.0)) == g.EINVAL
+    assert create(q=g.PnpParams(iters=0)) == g.EINVAL
+    assert create(wsb=1024) == g.ENOMEM
+    assert create(sigma=(cf * 1)(-1.0)) == g.EINVAL
+    assert lib.gbm3d_pnp_run(None, None) == g.EINVAL
+    assert lib.gbm3d_pnp_plan_destroy(None) == g.OK
