@@ -204,56 +204,75 @@ k_gather(const float *__restrict__ groups, const float *__restrict__ w, const in
 // block column lpos[j].  For one block row k the slots of the blocks
 // covering pixel x (positions k*W + x-N+1 .. k*W + x) are one contiguous range,
 // walked in order (= columns ascending, entries ascending: the same
-// per-pixel order as k_gather), so each lane visits only its own blocks and
-// the reads stream through memory.
+// per-pixel order as k_gather).
+//
+// One warp per 32 consecutive pixels of a row.  For each block row k the
+// slots covering any of its pixels are again one contiguous range (about
+// (N + 31) positions' entries); the warp stages it, up to kCap slots at a
+// time, in shared memory (lane i loads slots c0 + i, c0 + i + 32, ...: their
+// N values as float4, column and weight -- coalesced), then every lane walks
+// the part of its own range inside the staged chunk.  kCap is sized so that
+// one chunk holds the whole range in the common case: each lane's walk is
+// then one pass, and the warp's time per k is its longest range.
+constexpr int kGatherWarps = 8;
+
 template <int N>
-__global__ void __launch_bounds__(256)
+struct GatherCfg {
+    static constexpr int kCap = N == 8 ? 160 : 96;                  // slots staged per warp
+    static constexpr int kWarpFloats = kCap * N + 2 * kCap;          // values, columns, weights
+    static constexpr int kSmem = kGatherWarps * kWarpFloats * 4 + 64; // bytes, plus the window
+};
+
+template <int N>
+__global__ void __launch_bounds__(kGatherWarps * 32)
 k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_slot, const int *__restrict__ off,
                 const int *__restrict__ lpos, long long plane_stride, int H, int W, int pitch, Win win,
                 float *__restrict__ out)
 {
-    __shared__ float sw[N];
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < N; i++) sw[i] = win.v[i];
-    }
+    constexpr int kCap = GatherCfg<N>::kCap;
+    extern __shared__ __align__(16) float g_smem[];
+    float *sw = g_smem; // window (16 floats)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sv = g_smem + 16 + warp * GatherCfg<N>::kWarpFloats;
+    int *sc = reinterpret_cast<int *>(sv + kCap * N);
+    float *swt = sv + kCap * N + kCap;
+    if (threadIdx.x < N) sw[threadIdx.x] = win.v[threadIdx.x];
     __syncthreads();
-    const int j = threadIdx.x & 7;
-    const int x0 = blockIdx.x * (8 * kSegX) + ((threadIdx.x >> 3) & (kSegX - 1)) * 8;
-    const int y = blockIdx.y * kSegRows + (threadIdx.x >> 6);
-    if (x0 >= W || y >= H) return;
-    const int x = x0 + j;
+    const int y = blockIdx.y;
+    const int x0 = (blockIdx.x * kGatherWarps + warp) * 32, x = x0 + lane;
+    if (x0 >= W) return; // whole warp
     const bool xin = x < W;
     float num = 0.f, cn = 0.f, den = 0.f, cd = 0.f;
     const int ka = max(0, y - (N - 1)), kb = min(y, H - N);
-    // the blocks of block row k covering pixel x have columns lo .. hi, and
-    // their slots are one contiguous range (positions in order, entries in
-    // order within a position): each lane walks exactly its own range
+    // block columns covering this lane's pixel, and any pixel of the warp
     const int lo = max(0, x - (N - 1)), hi = min(x, W - N);
     const bool any = xin && lo <= hi;
+    const int wlo = max(0, x0 - (N - 1)), whi = min(min(x0 + 31, W - 1), W - N);
     for (int k = ka; k <= kb; k++) {
         const int a = y - k;
         const float wa = sw[a];
         const float *plane = planes + a * plane_stride;
+        const int S0 = __ldg(off + k * W + wlo), S1 = __ldg(off + k * W + whi + 1);
         const int s0 = any ? __ldg(off + k * W + lo) : 0, s1 = any ? __ldg(off + k * W + hi + 1) : 0;
-        for (int e0 = s0; e0 < s1; e0 += 8) { // chunks of 8 slots, loads issued before use
-            int bq[8];
+        for (int c0 = S0; c0 < S1; c0 += kCap) {
+            const int cn_ = min(kCap, S1 - c0);
+            for (int i = lane; i < cn_; i += 32) {
+                const float4 *src = reinterpret_cast<const float4 *>(plane + (size_t)(c0 + i) * N);
+                float4 *dst = reinterpret_cast<float4 *>(sv + i * N);
 #pragma unroll
-            for (int q = 0; q < 8; q++) bq[q] = e0 + q < s1 ? x - __ldg(lpos + e0 + q) : 0;
-            float wq[8], vq[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const bool ok = e0 + q < s1;
-                wq[q] = ok ? __ldg(w_slot + e0 + q) : 0.f;
-                vq[q] = ok ? __ldg(plane + (size_t)(e0 + q) * N + bq[q]) : 0.f;
+                for (int v = 0; v < N / 4; v++) dst[v] = __ldg(src + v);
+                sc[i] = __ldg(lpos + c0 + i);
+                swt[i] = __ldg(w_slot + c0 + i) * wa; // (w wa) kappa[b], the same rounding as before
             }
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                if (e0 + q < s1) {
-                    const float wt = wq[q] * wa * sw[bq[q]];
-                    kahan_add(num, cn, wt * vq[q]);
-                    kahan_add(den, cd, wt);
-                }
+            __syncwarp();
+            const int q0 = max(s0, c0), q1 = min(s1, c0 + cn_);
+            for (int q = q0; q < q1; q++) {
+                const int jj = q - c0, b = x - sc[jj];
+                const float wt = swt[jj] * sw[b];
+                kahan_add(num, cn, wt * sv[jj * N + b]);
+                kahan_add(den, cd, wt);
+            }
+            __syncwarp();
         }
     }
     if (xin) out[(size_t)y * pitch + x] = num / den;
@@ -364,10 +383,13 @@ cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, in
     const AggLayout L = agg_layout(H, W, n_entries, 1, true);
     const int *off = (const int *)((const char *)agg_ws + L.off);
     const int *lpos = (const int *)((const char *)agg_ws + L.lpos);
-    dim3 grid((W + 8 * kSegX - 1) / (8 * kSegX), (H + kSegRows - 1) / kSegRows);
+    dim3 grid((W + 32 * kGatherWarps - 1) / (32 * kGatherWarps), H);
     auto kern = N == 8 ? k_gather_planar<8> : k_gather_planar<16>;
-    kern<<<grid, 256, 0, st>>>(planes, w_slot, off, lpos, (long long)n_entries * N, H, W, pitch, make_win(window, N),
-                               out);
+    const int smem = N == 8 ? GatherCfg<8>::kSmem : GatherCfg<16>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kGatherWarps * 32, smem, st>>>(planes, w_slot, off, lpos, (long long)n_entries * N, H, W, pitch,
+                                                make_win(window, N), out);
     return cudaGetLastError();
 }
 
