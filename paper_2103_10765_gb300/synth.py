@@ -191,3 +191,24 @@ def make_blur_pair(H: int, W: int, sigma: float, scene_seed: int = 1, psf_size: 
     seed is 5000 + scene_seed."""
     clean = clean_scene(H, W, scene_seed)
     return clean, degrade_blur(clean, gaussian_psf(psf_size, psf_std), sigma, 5000 + scene_seed)
+
+
+def he_normal_params(seed: int, shapes) -> np.ndarray:
+    """Starting parameters of a network: for each (fan_in, fan_out) in shapes,
+    fan_in * fan_out weights N(0, 2 / fan_in) followed by fan_out zero biases,
+    concatenated; the normals come from one SplitMix64 stream."""
+    n = sum(fi * fo + fo for fi, fo in shapes)
+    z = normals(seed, n)
+    out = np.zeros(n)
+    o = 0
+    for fi, fo in shapes:
+        out[o:o + fi * fo] = z[o:o + fi * fo] * math.sqrt(2.0 / fi)
+        o += fi * fo + fo
+    return out
+
+
+def pilot_training_specs(n: int = 2000, seed: int = 21, size: int = 256):
+    """(H, W, sigma, scene_seed) of the learned pilot's training images:
+    size x size scenes, sigma uniform in [5, 50] / 255."""
+    u = uniforms(seed, n)
+    return [(size, size, (5.0 + 45.0 * float(u[i])) / 255.0, 10000 + i) for i in range(n)]
