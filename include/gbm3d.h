@@ -302,6 +302,42 @@ int gbm3d_pnp_plan_destroy(gbm3d_pnp_plan plan);
  * image `image`'s products with contraction length H and W. */
 int gbm3d_pnp_gemm_config(gbm3d_pnp_plan plan, int image, int *cfg_k_h, int *cfg_k_w);
 
+/* ---- Learned pilot: an extension (the paper's method has no learned part).
+ * A small network imitates the stage-1 estimate (Sec. 3), which stage 2
+ * (Sec. 4) then uses as its pilot.  Per pixel: input (Z, sigma); eight
+ * zero-padded 3 x 3 convolutions 2 -> 32 -> ... -> 32 -> 1 with biases and
+ * ReLU after the first seven; pilot = Z - output; training loss
+ * mean (pilot - Y1)^2.  Parameters: one flat FP32 vector theta of
+ * gbm3d_pilot_param_count() values, per layer the weights W[tap][ci][co]
+ * (tap = 3 (dy + 1) + (dx + 1)) then the biases.  Convolutions use the
+ * weights rounded to BF16 and accumulate in FP32; the six 32 -> 32 layers
+ * run on the tensor cores with their inputs rounded to BF16.
+ * Batches: B images of H x W, contiguous ([B][H][W] float, device);
+ * sigma: device array of B noise levels. */
+int gbm3d_pilot_param_count(void);
+/* Scratch of a forward pass (train = 0) or a gradient / training step (1). */
+int gbm3d_pilot_workspace_bytes(int B, int H, int W, int train, size_t *bytes);
+/* pilot[B][H][W] = the network's estimate for Z. */
+int gbm3d_pilot_forward(const float *Z, int B, int H, int W, const float *sigma, const float *theta, float *pilot,
+                        void *ws, gbm3d_stream_t stream);
+/* Loss against the targets Y1 (device scalar *loss, nullable) and its
+ * gradient with respect to theta (grad, nullable, gbm3d_pilot_param_count()
+ * floats).  Weight gradients are summed per CTA and then in a fixed order:
+ * the result is deterministic. */
+int gbm3d_pilot_loss_grad(const float *Z, const float *Y1, int B, int H, int W, const float *sigma,
+                          const float *theta, float *grad, float *loss, void *ws, gbm3d_stream_t stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected at step >= 1,
+ * learning rate lr) on theta with moment vectors adam_m, adam_v (device,
+ * zero at step 1); the loss before the step goes to *loss (nullable). */
+int gbm3d_pilot_train_step(const float *Z, const float *Y1, int B, int H, int W, const float *sigma, float *theta,
+                           float *adam_m, float *adam_v, int step, float lr, float *loss, void *ws,
+                           gbm3d_stream_t stream);
+/* Two-stage denoising with the network's estimate in place of stage 1
+ * (stages 2, translations 1).  ws: gbm3d_workspace_bytes_learned. */
+int gbm3d_workspace_bytes_learned(int H, int W, const gbm3d_params *p, size_t *bytes);
+int gbm3d_denoise_learned(const float *noisy, int H, int W, int pitch, float sigma, const gbm3d_params *p,
+                          const float *theta, float *out, void *ws, gbm3d_stream_t stream);
+
 /* Description of the last failure on this host thread ("" if none). */
 const char *gbm3d_last_error_string(void);
 

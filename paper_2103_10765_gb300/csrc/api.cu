@@ -653,6 +653,40 @@ int gbm3d_denoise(const float *noisy, int H, int W, int pitch, float sigma, cons
     return GBM3D_OK;
 }
 
+int gbm3d_workspace_bytes_learned(int H, int W, const gbm3d_params *p, size_t *bytes)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if (!bytes) return fail(GBM3D_EINVAL, "bytes is NULL");
+    if ((st = check_image(H, W, W, max_patch(p)))) return st;
+    *bytes = sizes(H, W, p).total + align_up(pilot_infer_bytes(H, W));
+    return GBM3D_OK;
+}
+
+int gbm3d_denoise_learned(const float *noisy, int H, int W, int pitch, float sigma, const gbm3d_params *p,
+                          const float *theta, float *out, void *ws, gbm3d_stream_t stream)
+{
+    int st = check_params(p);
+    if (st) return st;
+    if (p->stages != 2 || p->translations != 1 || stage_patch(p, 2) != kPatch)
+        return fail(GBM3D_EUNSUPPORTED, "learned pilot: stages 2, translations 1 and an 8 x 8 stage 2 required");
+    if ((st = check_image(H, W, pitch, max_patch(p)))) return st;
+    if (!noisy || !out || !ws || !theta) return fail(GBM3D_EINVAL, "null pointer argument");
+    if (noisy == out) return fail(GBM3D_EINVAL, "out must not alias noisy");
+    if (!(sigma >= 0.f) || !isfinite(sigma)) return fail(GBM3D_EINVAL, "sigma must be finite and >= 0");
+    if (!aligned(ws, kAlign)) return fail(GBM3D_EINVAL, "ws must be 256-byte aligned");
+    const StageGeom g2 = stage_geom(H, W, p, 2);
+    if ((st = check_window(H, W, g2.N, p->search_radius, g2.K))) return st;
+    if ((st = check_engine(H, W, p, g2, g2.K))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Sizes S = sizes(H, W, p);
+    char *base = (char *)ws;
+    float *y1 = (float *)(base + S.y1);
+    cudaError_t e = launch_pilot(noisy, H, W, pitch, sigma, theta, y1, W, base + S.total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "learned pilot");
+    return run_stage2(noisy, pitch, y1, W, H, W, sigma, p, S, base, out, pitch, s);
+}
+
 int gbm3d_denoise_color(const float *noisy, int H, int W, int pitch, long long plane_stride, float sigma,
                         const gbm3d_params *p, float *out, void *ws, gbm3d_stream_t stream)
 {

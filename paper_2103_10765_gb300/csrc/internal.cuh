@@ -116,6 +116,12 @@ int set_error(int code, const char *msg);
 // Replaces the thread's measurement-hook events (gbm3d_set_match_events); returns the old ones.
 cudaEvent_t *swap_match_events(cudaEvent_t *events);
 
+// Learned pilot (pilot.cu): scratch of one H x W forward pass, and the pass
+// (Z and pilot with their pitches; theta: the flat FP32 parameter vector).
+size_t pilot_infer_bytes(int H, int W);
+cudaError_t launch_pilot(const float *Z, int H, int W, int pitch, float sigma, const float *theta, float *pilot,
+                         int ppitch, void *ws, cudaStream_t st);
+
 // ---- launch wrappers (each returns cudaGetLastError()) -------------------
 // Direct FP32 block matching, N = 8 or 16.
 cudaError_t launch_match(const float *img, int H, int W, int pitch, int By, int Bx, int N, int s, int R, int K,

@@ -1,0 +1,574 @@
+// pilot.cu -- learned pilot: a small convolutional network trained to imitate
+// the method's stage-1 estimate (Sec. 3; Sec. 4 uses it as the pilot of the
+// Wiener stage), with its own forward, backward and optimiser kernels.
+//
+// Network (per pixel, zero-padded 3 x 3 convolutions, NHWC activations):
+//   x0 = (Z, sigma)  -> conv 2->32 + ReLU -> six conv 32->32 + ReLU
+//   -> conv 32->1 = r;  pilot = Z - r;  loss = mean (pilot - Y1)^2
+// Weights W[l][tap][ci][co] (tap = 3 (dy+1) + (dx+1)), biases b[l][co], in
+// one flat FP32 master vector; every convolution uses the weights rounded
+// to BF16.  The six 32 -> 32 layers run on the tensor cores (mma.sync
+// m16n8k16, BF16 inputs, FP32 accumulation) as implicit GEMMs over 4 x 32
+// pixel tiles staged in shared memory; their backward-data pass is the same
+// kernel with the weights flipped and transposed, masked by the ReLU of the
+// layer below.  The thin first and last layers, the weight gradients
+// (per-CTA partial sums, then a fixed-order reduction: deterministic) and
+// Adam are SIMT.  Activations stay FP32 in memory; the 32 -> 32 layers
+// round their inputs to BF16 when staging them.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "internal.cuh"
+
+namespace gbm3d {
+namespace {
+
+constexpr int kC = 32;      // hidden channels
+constexpr int kMid = 6;     // 32 -> 32 layers
+constexpr int kW1 = 9 * 2 * kC, kWm = 9 * kC * kC, kW8 = 9 * kC;
+// offsets of the flat parameter vector (per layer: weights, then biases)
+constexpr int kOffW1 = 0, kOffB1 = kW1;
+__host__ __device__ constexpr int off_wm(int m) { return kW1 + kC + m * (kWm + kC); }
+__host__ __device__ constexpr int off_bm(int m) { return off_wm(m) + kWm; }
+constexpr int kOffW8 = kW1 + kC + kMid * (kWm + kC), kOffB8 = kOffW8 + kW8;
+constexpr int kParams = kOffB8 + 1; // 56385
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// ---- weights: BF16 copies in the layouts the kernels read -------------------
+// wf[m][tap][co][ci] (forward, 32 -> 32), wb[m][tap][ci][co] = W[m][8 - tap][ci][co]
+// (backward data), w1r / w8r: the first / last layer's weights rounded to BF16.
+__global__ void k_pack(const float *__restrict__ theta, __nv_bfloat16 *__restrict__ wf,
+                       __nv_bfloat16 *__restrict__ wb, float *__restrict__ w1r, float *__restrict__ w8r)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < kMid * kWm) {
+        const int m = e / kWm, r = e - m * kWm;
+        const int tap = r / (kC * kC), ci = (r / kC) % kC, co = r % kC; // source W[tap][ci][co]
+        const __nv_bfloat16 v = __float2bfloat16_rn(theta[off_wm(m) + r]);
+        wf[(size_t)m * kWm + (tap * kC + co) * kC + ci] = v;
+        wb[(size_t)m * kWm + ((8 - tap) * kC + ci) * kC + co] = v;
+    }
+    if (e < kW1) w1r[e] = bf16r(theta[kOffW1 + e]);
+    if (e < kW8) w8r[e] = bf16r(theta[kOffW8 + e]);
+}
+
+// x0[b][y][x] = (Z, sigma_b)
+__global__ void k_input(const float *__restrict__ Z, int zpitch, long long zbatch, const float *__restrict__ sigma,
+                        float2 *__restrict__ x0, int H, int W)
+{
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5), b = blockIdx.z;
+    if (x >= W || y >= H) return;
+    x0[((size_t)b * H + y) * W + x] = make_float2(Z[b * zbatch + (long long)y * zpitch + x], sigma[b]);
+}
+
+// First layer, 2 -> 32, + ReLU: one thread per pixel, weights in shared memory.
+__global__ void __launch_bounds__(128) k_conv_first(const float2 *__restrict__ x0, const float *__restrict__ w1r,
+                                                    const float *__restrict__ theta, float *__restrict__ x1, int H,
+                                                    int W)
+{
+    __shared__ float sw[kW1], sb[kC];
+    for (int i = threadIdx.x; i < kW1; i += blockDim.x) sw[i] = w1r[i];
+    if (threadIdx.x < kC) sb[threadIdx.x] = theta[kOffB1 + threadIdx.x];
+    __syncthreads();
+    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
+    if (x >= W) return;
+    float acc[kC];
+#pragma unroll
+    for (int co = 0; co < kC; co++) acc[co] = sb[co];
+#pragma unroll
+    for (int tap = 0; tap < 9; tap++) {
+        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+        float2 v = make_float2(0.f, 0.f);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = x0[((size_t)b * H + yy) * W + xx];
+#pragma unroll
+        for (int co = 0; co < kC; co++) acc[co] = fmaf(v.x, sw[(tap * 2 + 0) * kC + co], fmaf(v.y, sw[(tap * 2 + 1) * kC + co], acc[co]));
+    }
+    float4 *o = reinterpret_cast<float4 *>(x1 + (((size_t)b * H + y) * W + x) * kC);
+#pragma unroll
+    for (int q = 0; q < kC / 4; q++)
+        o[q] = make_float4(fmaxf(acc[4 * q], 0.f), fmaxf(acc[4 * q + 1], 0.f), fmaxf(acc[4 * q + 2], 0.f),
+                           fmaxf(acc[4 * q + 3], 0.f));
+}
+
+// ---- 32 -> 32 convolution on the tensor cores ---------------------------------
+// out[p][n] = sum_tap sum_k in[p + off(tap)][k] V[tap][n][k], then
+//   forward:  + bias[n], ReLU;   backward data:  * (mask[p][n] > 0).
+// CTA: 4 warps, a tile of 4 rows x 32 pixels; warp w owns row w (two m-tiles
+// of 16 pixels) and all 32 outputs (four n-tiles of 8).  The input tile with
+// its 1-pixel halo (6 x 34 pixels x 32 channels) and V are staged in shared
+// memory as BF16 with 40-element rows (80 bytes: fragment loads are
+// conflict-free).
+constexpr int kTY = 4, kTX = 32, kRow = 40;
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <bool kFwd>
+__global__ void __launch_bounds__(128) k_conv_mid(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ V,
+                                                  const float *__restrict__ bias, const float *__restrict__ mask,
+                                                  float *__restrict__ out, int H, int W)
+{
+    __shared__ __align__(16) __nv_bfloat16 s_in[(kTY + 2) * (kTX + 2) * kRow];
+    __shared__ __align__(16) __nv_bfloat16 s_v[9 * kC * kRow];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, b = blockIdx.z;
+    const size_t img = (size_t)b * H * W;
+    // stage V (9 x 32 rows of 32 BF16, as 16-byte chunks)
+    for (int i = tid; i < 9 * kC * 4; i += 128) {
+        const int row = i >> 2, q = i & 3;
+        *reinterpret_cast<uint4 *>(s_v + row * kRow + q * 8) = *reinterpret_cast<const uint4 *>(V + row * kC + q * 8);
+    }
+    // stage the input tile, FP32 -> BF16, zero outside the image
+    for (int i = tid; i < (kTY + 2) * (kTX + 2) * 8; i += 128) {
+        const int pix = i >> 3, q = i & 7;
+        const int ty = pix / (kTX + 2), tx = pix - ty * (kTX + 2);
+        const int yy = y0 + ty - 1, xx = x0 + tx - 1;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = *reinterpret_cast<const float4 *>(in + (img + (size_t)yy * W + xx) * kC + q * 4);
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+        __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(s_in + pix * kRow + q * 4);
+        d[0] = lo;
+        d[1] = hi;
+    }
+    __syncthreads();
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[mt][nt][r] = 0.f;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; tap++) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int h = 0; h < 2; h++) { // channels 16 h .. 16 h + 15
+            uint32_t a[2][4], bb[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) {
+                const int p0 = (warp + 1 + dy) * (kTX + 2) + mt * 16 + g + 1 + dx; // tile pixel of row g
+                const __nv_bfloat16 *r0 = s_in + p0 * kRow + 16 * h + 2 * t;
+                const __nv_bfloat16 *r1 = r0 + 8 * kRow; // pixel g + 8
+                a[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
+                a[mt][1] = *reinterpret_cast<const uint32_t *>(r1);
+                a[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+                a[mt][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const __nv_bfloat16 *v = s_v + (tap * kC + nt * 8 + g) * kRow + 16 * h + 2 * t;
+                bb[nt][0] = *reinterpret_cast<const uint32_t *>(v);
+                bb[nt][1] = *reinterpret_cast<const uint32_t *>(v + 8);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++)
+                    mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bb[nt][0], bb[nt][1]);
+        }
+    }
+    const int y = y0 + warp;
+    if (y >= H) return;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            const int x = x0 + mt * 16 + g + 8 * half;
+            if (x >= W) continue;
+            const size_t p = img + (size_t)y * W + x;
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const int n = nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                if (kFwd) {
+                    v0 = fmaxf(v0 + bias[n], 0.f);
+                    v1 = fmaxf(v1 + bias[n + 1], 0.f);
+                } else {
+                    const float2 mk = *reinterpret_cast<const float2 *>(mask + p * kC + n);
+                    v0 = mk.x > 0.f ? v0 : 0.f;
+                    v1 = mk.y > 0.f ? v1 : 0.f;
+                }
+                *reinterpret_cast<float2 *>(out + p * kC + n) = make_float2(v0, v1);
+            }
+        }
+}
+
+// Last layer, 32 -> 1: r = b + sum W8 x7; pilot = Z - r.  With a target: the
+// loss gradient g8 = dL/dr = -2 (pilot - Y1) / n and per-CTA partial sums of
+// (pilot - Y1)^2 (rows of the grid, reduced later in a fixed order).
+__global__ void __launch_bounds__(128) k_conv_last(const float *__restrict__ x7, const float *__restrict__ w8r,
+                                                   const float *__restrict__ theta, const float *__restrict__ Z,
+                                                   int zpitch, long long zbatch, const float *__restrict__ Y1,
+                                                   float *__restrict__ pilot, int ppitch, long long pbatch,
+                                                   float *__restrict__ g8, float *__restrict__ loss_part, float inv_n,
+                                                   int H, int W)
+{
+    __shared__ float sw[kW8];
+    __shared__ float red[4];
+    for (int i = threadIdx.x; i < kW8; i += blockDim.x) sw[i] = w8r[i];
+    __syncthreads();
+    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
+    float e2 = 0.f;
+    if (x < W) {
+        float r = theta[kOffB8];
+        for (int tap = 0; tap < 9; tap++) {
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+            const float4 *v = reinterpret_cast<const float4 *>(x7 + (((size_t)b * H + yy) * W + xx) * kC);
+#pragma unroll
+            for (int q = 0; q < kC / 4; q++) {
+                const float4 u = v[q];
+                const float *wq = sw + tap * kC + 4 * q;
+                r = fmaf(u.x, wq[0], fmaf(u.y, wq[1], fmaf(u.z, wq[2], fmaf(u.w, wq[3], r))));
+            }
+        }
+        const float pv = Z[b * zbatch + (long long)y * zpitch + x] - r;
+        if (pilot) pilot[b * pbatch + (long long)y * ppitch + x] = pv;
+        if (Y1) {
+            const float d = pv - Y1[((size_t)b * H + y) * W + x];
+            g8[((size_t)b * H + y) * W + x] = -2.f * d * inv_n;
+            e2 = d * d * inv_n; // partial sums of the mean
+        }
+    }
+    if (!Y1) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        loss_part[((size_t)b * H + y) * gridDim.x + blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+// Backward of the last layer: g7[p][ci] = (sum_tap g8[p - off(tap)] W8[tap][ci]) * (x7[p][ci] > 0).
+__global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, const float *__restrict__ w8r,
+                                                  const float *__restrict__ x7, float *__restrict__ g7, int H, int W)
+{
+    __shared__ float sw[kW8];
+    for (int i = threadIdx.x; i < kW8; i += blockDim.x) sw[i] = w8r[i];
+    __syncthreads();
+    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
+    if (x >= W) return;
+    float acc[kC];
+#pragma unroll
+    for (int c = 0; c < kC; c++) acc[c] = 0.f;
+    for (int tap = 0; tap < 9; tap++) {
+        const int yy = y - (tap / 3 - 1), xx = x - (tap % 3 - 1);
+        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+        const float gv = g8[((size_t)b * H + yy) * W + xx];
+#pragma unroll
+        for (int c = 0; c < kC; c++) acc[c] = fmaf(gv, sw[tap * kC + c], acc[c]);
+    }
+    const size_t p = ((size_t)b * H + y) * W + x;
+    const float4 *m = reinterpret_cast<const float4 *>(x7 + p * kC);
+    float4 *o = reinterpret_cast<float4 *>(g7 + p * kC);
+#pragma unroll
+    for (int q = 0; q < kC / 4; q++) {
+        const float4 mk = m[q];
+        o[q] = make_float4(mk.x > 0.f ? acc[4 * q] : 0.f, mk.y > 0.f ? acc[4 * q + 1] : 0.f,
+                           mk.z > 0.f ? acc[4 * q + 2] : 0.f, mk.w > 0.f ? acc[4 * q + 3] : 0.f);
+    }
+}
+
+// ---- weight gradients ---------------------------------------------------------
+// dW[tap][ci][co] = sum_p x[p + off(tap)][ci] g[p][co] and db[co] = sum_p g[p][co].
+// One thread per (tap, ci) with CO accumulators (thread 9 CI also sums the
+// bias); each CTA walks rows of 64 pixels (x with halo and g staged in shared
+// memory) over a strided share of the batch and writes its partial sums;
+// k_reduce adds the CTAs' partials in a fixed order.
+constexpr int kGX = 64;
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const float *__restrict__ x, const float *__restrict__ g, int B,
+                                                      int H, int W, float *__restrict__ part)
+{
+    __shared__ float sx[3][kGX + 2][CI];
+    __shared__ float sg[kGX][CO];
+    const int tid = threadIdx.x, nthr = 9 * CI + 1;
+    const bool isb = tid == 9 * CI; // the bias thread
+    const int tap = isb ? 4 : tid / CI, ci = isb ? 0 : tid % CI, dy = tap / 3 - 1, dx = tap % 3 - 1;
+    float acc[CO];
+#pragma unroll
+    for (int c = 0; c < CO; c++) acc[c] = 0.f;
+    const int segs = (W + kGX - 1) / kGX;
+    const long long units = (long long)B * H * segs;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const int seg = (int)(u % segs), y = (int)((u / segs) % H), b = (int)(u / ((long long)segs * H));
+        const int xb = seg * kGX;
+        __syncthreads();
+        for (int i = tid; i < 3 * (kGX + 2) * CI; i += nthr) {
+            const int r = i / ((kGX + 2) * CI), rem = i - r * (kGX + 2) * CI, c = rem / CI, ch = rem - c * CI;
+            const int yy = y + r - 1, xx = xb + c - 1;
+            sx[r][c][ch] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[(((size_t)b * H + yy) * W + xx) * CI + ch] : 0.f;
+        }
+        for (int i = tid; i < kGX * CO; i += nthr) {
+            const int c = i / CO, co = i - c * CO, xx = xb + c;
+            sg[c][co] = xx < W ? g[(((size_t)b * H + y) * W + xx) * CO + co] : 0.f;
+        }
+        __syncthreads();
+        for (int c = 0; c < kGX; c++) {
+            const float xv = isb ? 1.f : sx[1 + dy][c + 1 + dx][ci];
+#pragma unroll
+            for (int co = 0; co < CO; co++) acc[co] = fmaf(xv, sg[c][co], acc[co]);
+        }
+    }
+    float *o = part + (size_t)blockIdx.x * (9 * CI * CO + CO);
+    if (isb) {
+#pragma unroll
+        for (int co = 0; co < CO; co++) o[9 * CI * CO + co] = acc[co];
+    } else {
+#pragma unroll
+        for (int co = 0; co < CO; co++) o[(tap * CI + ci) * CO + co] = acc[co];
+    }
+}
+
+// dst[i] = sum_{c < nparts} src[c][i] in ascending c (deterministic).
+__global__ void k_reduce(const float *__restrict__ src, int nparts, int len, float *__restrict__ dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    float s = 0.f;
+    for (int c = 0; c < nparts; c++) s += src[(size_t)c * len + i];
+    dst[i] = s;
+}
+
+// Adam on the flat parameter vector (step t >= 1, bias-corrected).
+__global__ void k_adam(float *__restrict__ theta, const float *__restrict__ grad, float *__restrict__ m1,
+                       float *__restrict__ m2, int n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gv = grad[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gv, v = b2 * m2[i] + (1.f - b2) * gv * gv;
+    m1[i] = a;
+    m2[i] = v;
+    theta[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
+}
+
+} // namespace
+} // namespace gbm3d
+
+// ---- host side ----------------------------------------------------------------
+namespace gbm3d {
+namespace {
+
+constexpr int kWgMax = 512; // most CTAs of a weight-gradient launch (partial-sum rows)
+
+struct PilotLayout {
+    size_t wf, wb, w1r, w8r, x0, act, g8, ga, gb, part, grad, lpart, loss, bytes;
+    size_t plane; // pixels of the batch
+    int lparts;   // loss partial sums
+};
+
+PilotLayout pilot_layout(int B, int H, int W, bool train)
+{
+    PilotLayout L{};
+    const size_t P = (size_t)B * H * W;
+    L.plane = P;
+    L.lparts = B * H * ((W + 127) / 128);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align_up(bytes);
+        return at;
+    };
+    L.wf = take((size_t)kMid * kWm * 2);
+    L.wb = take((size_t)kMid * kWm * 2);
+    L.w1r = take(kW1 * 4);
+    L.w8r = take(kW8 * 4);
+    L.x0 = take(P * 2 * 4);
+    // activations x1..x7 when training (kept for the backward pass), else two ping-pong buffers
+    L.act = take(P * kC * 4 * (train ? 7 : 2));
+    if (train) {
+        L.g8 = take(P * 4);
+        L.ga = take(P * kC * 4);
+        L.gb = take(P * kC * 4);
+        L.part = take((size_t)kWgMax * (kWm + kC) * 4);
+        L.grad = take((size_t)kParams * 4);
+        L.lpart = take((size_t)L.lparts * 4);
+        L.loss = take(4);
+    }
+    L.bytes = o;
+    return L;
+}
+
+int wgrad_ctas()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 148;
+        n = 2 * nsm < kWgMax ? 2 * nsm : kWgMax;
+    }
+    return n;
+}
+
+// Forward through the network; with Y1 also the loss pieces (training).
+cudaError_t pilot_forward(const float *Z, int B, int H, int W, int zpitch, long long zbatch, const float *sigma,
+                          const float *theta, const float *Y1, float *pilot, int ppitch, long long pbatch,
+                          char *ws, const PilotLayout &L, bool train, cudaStream_t st)
+{
+    __nv_bfloat16 *wf = (__nv_bfloat16 *)(ws + L.wf), *wb = (__nv_bfloat16 *)(ws + L.wb);
+    float *w1r = (float *)(ws + L.w1r), *w8r = (float *)(ws + L.w8r);
+    k_pack<<<(kMid * kWm + 255) / 256, 256, 0, st>>>(theta, wf, wb, w1r, w8r);
+    float2 *x0 = (float2 *)(ws + L.x0);
+    k_input<<<dim3((W + 31) / 32, (H + 7) / 8, B), 256, 0, st>>>(Z, zpitch, zbatch, sigma, x0, H, W);
+    float *act = (float *)(ws + L.act);
+    auto X = [&](int l) { // x_l, l = 1..7
+        return act + (size_t)(train ? l - 1 : (l - 1) & 1) * L.plane * kC;
+    };
+    const dim3 g128((W + 127) / 128, H, B), gmid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, B);
+    k_conv_first<<<g128, 128, 0, st>>>(x0, w1r, theta, X(1), H, W);
+    for (int m = 0; m < kMid; m++)
+        k_conv_mid<true><<<gmid, 128, 0, st>>>(X(m + 1), wf + (size_t)m * kWm, theta + off_bm(m), nullptr, X(m + 2),
+                                               H, W);
+    const float inv_n = 1.f / (float)L.plane;
+    k_conv_last<<<g128, 128, 0, st>>>(X(7), w8r, theta, Z, zpitch, zbatch, Y1, pilot, ppitch, pbatch,
+                                      train ? (float *)(ws + L.g8) : nullptr,
+                                      train ? (float *)(ws + L.lpart) : nullptr, inv_n, H, W);
+    return cudaGetLastError();
+}
+
+// Gradient of the loss (after pilot_forward with Y1) into ws grad, and the
+// loss into ws loss.
+cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, cudaStream_t st)
+{
+    float *act = (float *)(ws + L.act), *grad = (float *)(ws + L.grad), *part = (float *)(ws + L.part);
+    auto X = [&](int l) { return act + (size_t)(l - 1) * L.plane * kC; };
+    const __nv_bfloat16 *wb = (const __nv_bfloat16 *)(ws + L.wb);
+    const float *w8r = (const float *)(ws + L.w8r);
+    float *g8 = (float *)(ws + L.g8), *ga = (float *)(ws + L.ga), *gb = (float *)(ws + L.gb);
+    const int nc = wgrad_ctas();
+    // loss = sum of the scaled partials (their rows hold (pilot - Y1)^2 / n)
+    k_reduce<<<1, 32, 0, st>>>((const float *)(ws + L.lpart), L.lparts, 1, (float *)(ws + L.loss));
+    // last layer
+    k_wgrad<32, 1><<<nc, 9 * 32 + 1, 0, st>>>(X(7), g8, B, H, W, part);
+    k_reduce<<<(kW8 + 1 + 255) / 256, 256, 0, st>>>(part, nc, kW8 + 1, grad + kOffW8);
+    const dim3 g128((W + 127) / 128, H, B), gmid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, B);
+    k_last_bwd<<<g128, 128, 0, st>>>(g8, w8r, X(7), ga, H, W);
+    float *gcur = ga, *gnext = gb;
+    for (int m = kMid - 1; m >= 0; m--) { // layer m + 2: x_{m+1} -> x_{m+2}; gcur = dL/dpre_{m+2}
+        k_wgrad<32, 32><<<nc, 9 * 32 + 1, 0, st>>>(X(m + 1), gcur, B, H, W, part);
+        k_reduce<<<(kWm + kC + 255) / 256, 256, 0, st>>>(part, nc, kWm + kC, grad + off_wm(m));
+        k_conv_mid<false><<<gmid, 128, 0, st>>>(gcur, wb + (size_t)m * kWm, nullptr, X(m + 1), gnext, H, W);
+        float *t = gcur;
+        gcur = gnext;
+        gnext = t;
+    }
+    // first layer (gcur = dL/dpre_1)
+    k_wgrad<2, 32><<<nc, 9 * 2 + 1, 0, st>>>((const float *)(ws + L.x0), gcur, B, H, W, part);
+    k_reduce<<<(kW1 + kC + 255) / 256, 256, 0, st>>>(part, nc, kW1 + kC, grad + kOffW1);
+    return cudaGetLastError();
+}
+
+int pilot_fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return set_error(code, buf);
+}
+
+int check_batch(int B, int H, int W)
+{
+    if (B < 1 || H < 1 || W < 1) return pilot_fail(GBM3D_EINVAL, "pilot: empty batch %d x %d x %d", B, H, W);
+    if ((long long)B * H * W * kC >= (1ll << 40)) return pilot_fail(GBM3D_EINVAL, "pilot: batch too large");
+    return GBM3D_OK;
+}
+
+} // namespace
+
+namespace {
+__global__ void k_set(float *d, float v) { *d = v; }
+} // namespace
+
+size_t pilot_infer_bytes(int H, int W) { return pilot_layout(1, H, W, false).bytes + 256; }
+
+cudaError_t launch_pilot(const float *Z, int H, int W, int pitch, float sigma, const float *theta, float *pilot,
+                         int ppitch, void *ws, cudaStream_t st)
+{
+    const PilotLayout L = pilot_layout(1, H, W, false);
+    float *sdev = (float *)((char *)ws + L.bytes); // the noise level, in the slot after the layout
+    k_set<<<1, 1, 0, st>>>(sdev, sigma);
+    return pilot_forward(Z, 1, H, W, pitch, 0, sdev, theta, nullptr, pilot, ppitch, 0, (char *)ws, L, false, st);
+}
+
+} // namespace gbm3d
+
+using namespace gbm3d;
+
+extern "C" {
+
+int gbm3d_pilot_param_count(void) { return kParams; }
+
+int gbm3d_pilot_workspace_bytes(int B, int H, int W, int train, size_t *bytes)
+{
+    int s = check_batch(B, H, W);
+    if (s) return s;
+    if (!bytes) return pilot_fail(GBM3D_EINVAL, "pilot: bytes is NULL");
+    *bytes = pilot_layout(B, H, W, train != 0).bytes + 256; // + a slot for the noise levels
+    return GBM3D_OK;
+}
+
+int gbm3d_pilot_forward(const float *Z, int B, int H, int W, const float *sigma, const float *theta, float *pilot,
+                        void *ws, gbm3d_stream_t stream)
+{
+    int s = check_batch(B, H, W);
+    if (s) return s;
+    if (!Z || !sigma || !theta || !pilot || !ws) return pilot_fail(GBM3D_EINVAL, "pilot: null pointer argument");
+    if (((uintptr_t)ws) % kAlign) return pilot_fail(GBM3D_EINVAL, "pilot: ws must be 256-byte aligned");
+    const PilotLayout L = pilot_layout(B, H, W, false);
+    const long long n = (long long)H * W;
+    cudaError_t e = pilot_forward(Z, B, H, W, W, n, sigma, theta, nullptr, pilot, W, n, (char *)ws, L, false,
+                                  (cudaStream_t)stream);
+    return e == cudaSuccess ? GBM3D_OK : pilot_fail(GBM3D_ECUDA, "pilot forward: %s", cudaGetErrorString(e));
+}
+
+int gbm3d_pilot_loss_grad(const float *Z, const float *Y1, int B, int H, int W, const float *sigma,
+                          const float *theta, float *grad, float *loss, void *ws, gbm3d_stream_t stream)
+{
+    int s = check_batch(B, H, W);
+    if (s) return s;
+    if (!Z || !Y1 || !sigma || !theta || !ws) return pilot_fail(GBM3D_EINVAL, "pilot: null pointer argument");
+    if (((uintptr_t)ws) % kAlign) return pilot_fail(GBM3D_EINVAL, "pilot: ws must be 256-byte aligned");
+    const PilotLayout L = pilot_layout(B, H, W, true);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n = (long long)H * W;
+    char *base = (char *)ws;
+    cudaError_t e = pilot_forward(Z, B, H, W, W, n, sigma, theta, Y1, nullptr, 0, 0, base, L, true, st);
+    if (e == cudaSuccess) e = pilot_backward(B, H, W, base, L, st);
+    if (e == cudaSuccess && grad)
+        e = cudaMemcpyAsync(grad, base + L.grad, (size_t)kParams * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, base + L.loss, 4, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? GBM3D_OK : pilot_fail(GBM3D_ECUDA, "pilot gradient: %s", cudaGetErrorString(e));
+}
+
+int gbm3d_pilot_train_step(const float *Z, const float *Y1, int B, int H, int W, const float *sigma, float *theta,
+                           float *adam_m, float *adam_v, int step, float lr, float *loss, void *ws,
+                           gbm3d_stream_t stream)
+{
+    if (!adam_m || !adam_v || step < 1 || !(lr > 0.f)) return pilot_fail(GBM3D_EINVAL, "pilot: bad optimiser state");
+    int s = gbm3d_pilot_loss_grad(Z, Y1, B, H, W, sigma, theta, nullptr, loss, ws, stream);
+    if (s) return s;
+    const PilotLayout L = pilot_layout(B, H, W, true);
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    k_adam<<<(kParams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(theta, (const float *)((char *)ws + L.grad),
+                                                                     adam_m, adam_v, kParams, lr, b1, b2, 1e-8f, c1,
+                                                                     c2);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBM3D_OK : pilot_fail(GBM3D_ECUDA, "pilot adam: %s", cudaGetErrorString(e));
+}
+
+} // extern "C"

@@ -89,13 +89,23 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_pnp_run.argtypes = [vp, vp]
     lib.gbm3d_pnp_plan_destroy.argtypes = [vp]
     lib.gbm3d_pnp_gemm_config.argtypes = [vp, ci, ip, ip]
+    lib.gbm3d_pilot_param_count.argtypes = []
+    lib.gbm3d_pilot_workspace_bytes.argtypes = [ci, ci, ci, ci, ctypes.POINTER(ctypes.c_size_t)]
+    lib.gbm3d_pilot_forward.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, vp]
+    lib.gbm3d_pilot_loss_grad.argtypes = [vp, vp, ci, ci, ci, vp, vp, vp, vp, vp, vp]
+    lib.gbm3d_pilot_train_step.argtypes = [vp, vp, ci, ci, ci, vp, vp, vp, vp, ci, cf, vp, vp, vp]
+    lib.gbm3d_workspace_bytes_learned.argtypes = [ci, ci, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.gbm3d_denoise_learned.argtypes = [vp, ci, ci, ci, cf, P, vp, vp, vp, vp]
     lib.gbm3d_last_error_string.restype = ctypes.c_char_p
     lib.gbm3d_version.restype = ctypes.c_char_p
     for name in ("gbm3d_params_default", "gbm3d_params_stage", "gbm3d_grid_dims", "gbm3d_workspace_bytes", "gbm3d_match",
                  "gbm3d_filter_ht", "gbm3d_filter_wiener", "gbm3d_aggregate", "gbm3d_denoise",
                  "gbm3d_aggregate_noalloc", "gbm3d_match_stats", "gbm3d_set_match_events",
                  "gbm3d_workspace_bytes_color", "gbm3d_denoise_color", "gbm3d_pnp_workspace_bytes",
-                 "gbm3d_pnp_plan_create", "gbm3d_pnp_run", "gbm3d_pnp_plan_destroy", "gbm3d_pnp_gemm_config"):
+                 "gbm3d_pnp_plan_create", "gbm3d_pnp_run", "gbm3d_pnp_plan_destroy", "gbm3d_pnp_gemm_config",
+                 "gbm3d_pilot_param_count", "gbm3d_pilot_workspace_bytes", "gbm3d_pilot_forward",
+                 "gbm3d_pilot_loss_grad", "gbm3d_pilot_train_step", "gbm3d_workspace_bytes_learned",
+                 "gbm3d_denoise_learned"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -387,3 +397,96 @@ class PnpPlan:
             self.close()
         except Exception:
             pass
+
+
+def pilot_param_count() -> int:
+    return int(load().gbm3d_pilot_param_count())
+
+
+def _pilot_ws(B, H, W, train, device):
+    n = ctypes.c_size_t()
+    _check(load().gbm3d_pilot_workspace_bytes(B, H, W, int(train), ctypes.byref(n)))
+    return torch.empty(max(n.value, 1), dtype=torch.uint8, device=device)
+
+
+class PilotNet:
+    """The learned pilot's parameters on the device (theta, FP32) with its
+    Adam state.  Batches are (B, H, W) float32 CUDA tensors, sigmas a
+    sequence of B noise levels."""
+
+    def __init__(self, theta, device="cuda"):
+        theta = torch.as_tensor(theta, dtype=torch.float32)
+        if theta.numel() != pilot_param_count():
+            raise ValueError(f"theta has {theta.numel()} values, the network {pilot_param_count()}")
+        self.theta = theta.to(device).contiguous()
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.step = 0
+        self._ws = {}
+
+    def _workspace(self, shape, train):
+        key = (tuple(shape), bool(train))
+        if key not in self._ws:
+            self._ws[key] = _pilot_ws(*shape, train, self.theta.device)
+        return self._ws[key]
+
+    @staticmethod
+    def _batch(Z):
+        if not (Z.is_cuda and Z.dtype == torch.float32 and Z.dim() == 3 and Z.is_contiguous()):
+            raise ValueError("a batch is a contiguous (B, H, W) float32 CUDA tensor")
+        return Z.shape
+
+    def _sig(self, sigmas, B):
+        s = torch.as_tensor(list(sigmas), dtype=torch.float32).to(self.theta.device)
+        if s.numel() != B:
+            raise ValueError("one sigma per image")
+        return s
+
+    def forward(self, Z, sigmas):
+        B, H, W = self._batch(Z)
+        s = self._sig(sigmas, B)
+        out = torch.empty_like(Z)
+        _check(load().gbm3d_pilot_forward(_ptr(Z), B, H, W, _ptr(s), _ptr(self.theta), _ptr(out),
+                                          _ptr(self._workspace((B, H, W), False)), _stream(Z)))
+        return out
+
+    def loss_grad(self, Z, Y1, sigmas):
+        B, H, W = self._batch(Z)
+        s = self._sig(sigmas, B)
+        grad = torch.empty_like(self.theta)
+        loss = torch.empty(1, dtype=torch.float32, device=Z.device)
+        _check(load().gbm3d_pilot_loss_grad(_ptr(Z), _ptr(Y1.contiguous()), B, H, W, _ptr(s), _ptr(self.theta),
+                                            _ptr(grad), _ptr(loss), _ptr(self._workspace((B, H, W), True)),
+                                            _stream(Z)))
+        return loss, grad
+
+    def train_step(self, Z, Y1, sigmas, lr=1e-3):
+        """One Adam step; returns the loss before it (device scalar)."""
+        B, H, W = self._batch(Z)
+        s = self._sig(sigmas, B)
+        self.step += 1
+        loss = torch.empty(1, dtype=torch.float32, device=Z.device)
+        _check(load().gbm3d_pilot_train_step(_ptr(Z), _ptr(Y1.contiguous()), B, H, W, _ptr(s), _ptr(self.theta),
+                                             _ptr(self.m), _ptr(self.v), self.step, float(lr), _ptr(loss),
+                                             _ptr(self._workspace((B, H, W), True)), _stream(Z)))
+        return loss
+
+
+def workspace_bytes_learned(H: int, W: int, p: Params | None = None) -> int:
+    p = p or params_default()
+    n = ctypes.c_size_t()
+    _check(load().gbm3d_workspace_bytes_learned(H, W, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def denoise_learned(noisy: torch.Tensor, sigma: float, net: PilotNet, p: Params | None = None,
+                    ws: torch.Tensor | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Stage 2 with the learned pilot in place of stage 1."""
+    p = p or params_default()
+    H, W, pitch = _img(noisy, "noisy")
+    out = out if out is not None else torch.empty_like(noisy)
+    if ws is None:
+        ws = torch.empty(max(workspace_bytes_learned(H, W, p), 1), dtype=torch.uint8, device=noisy.device)
+    _check(load().gbm3d_denoise_learned(_ptr(noisy), H, W, pitch, float(sigma), ctypes.byref(p), _ptr(net.theta),
+                                        _ptr(out), _ptr(ws), _stream(noisy)))
+    return out

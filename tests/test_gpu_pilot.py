@@ -1,0 +1,147 @@
+"""GPU: the learned pilot (gbm3d_pilot_*, gbm3d_denoise_learned) against the
+FP64 oracle (oracle/pilot.py, readings L1-L5).
+
+Tolerances: the oracle runs with the same BF16-rounded weights; the GPU also
+rounds the inputs of its six 32 -> 32 layers to BF16 (relative 2^-9 each),
+so outputs agree to about 1e-2 of the residual's scale and gradients to a
+few per cent in norm (cosine similarity per layer >= 0.995)."""
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_2103_10765_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2103_10765_gb300 import gbm3d, pilot_train  # noqa: E402
+
+DEV = torch.device("cuda:0")
+NT = os.cpu_count() or 4
+THETA_FILE = os.path.join(os.path.dirname(gbm3d.__file__), "pilot_theta.f32")
+GAP_DB = 1.5  # PSNR the learned form may give up against the plain method
+
+
+def bf16_weights(pl, theta):
+    """theta with every weight (not the biases) rounded to BF16, nearest-even."""
+    out = np.asarray(theta, dtype=np.float64).copy()
+    o = 0
+    for ci, co, _ in pl.LAYERS:
+        w = out[o:o + 9 * ci * co].astype(np.float32)
+        u = w.view(np.uint32).astype(np.uint64)
+        r = (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32)
+        out[o:o + 9 * ci * co] = r.view(np.float32)
+        o += 9 * ci * co + co
+    return out
+
+
+def batch(B, H, W, seed0=1):
+    specs = [(H, W, (10 + 15 * i) / 255, seed0 + i) for i in range(B)]
+    pairs = [synth.make_pair(h, w, s, sd) for h, w, s, sd in specs]
+    Z = np.stack([z for _, z in pairs])
+    return Z, [s for _, _, s, _ in specs]
+
+
+@pytest.fixture(scope="module")
+def pl():
+    from oracle import pilot
+    return pilot
+
+
+@pytest.fixture(scope="module")
+def theta(pl):
+    rs = np.random.default_rng(3)
+    t = pl.init_params(11)
+    return t + 0.02 * rs.standard_normal(t.size)  # nonzero biases too
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 20, 36), (1, 33, 70)])
+def test_forward_matches_oracle(pl, theta, B, H, W):
+    Z, sig = batch(B, H, W)
+    net = gbm3d.PilotNet(theta.astype(np.float32), DEV)
+    out = net.forward(torch.from_numpy(Z).to(DEV), sig).cpu().numpy()
+    ref = pl.forward(bf16_weights(pl, theta.astype(np.float32)), Z, sig)
+    scale = np.abs(Z - ref).max()
+    assert np.abs(out - ref).max() <= 2e-2 * scale, (np.abs(out - ref).max(), scale)
+
+
+def test_zero_last_layer_returns_the_noisy_image(pl, theta):
+    t = theta.astype(np.float32).copy()
+    t[-(9 * 32 + 1):] = 0
+    Z, sig = batch(2, 24, 40)
+    out = gbm3d.PilotNet(t, DEV).forward(torch.from_numpy(Z).to(DEV), sig).cpu().numpy()
+    assert np.array_equal(out, Z)
+
+
+def test_gradient_matches_oracle(pl, theta):
+    B, H, W = 2, 20, 36
+    Z, sig = batch(B, H, W)
+    Y1 = (Z + 0.03 * np.sin(np.arange(W))[None, None, :]).astype(np.float32)
+    net = gbm3d.PilotNet(theta.astype(np.float32), DEV)
+    loss, grad = net.loss_grad(torch.from_numpy(Z).to(DEV), torch.from_numpy(Y1).to(DEV), sig)
+    L, g = pl.loss_and_grad(bf16_weights(pl, theta.astype(np.float32)), Z, sig, Y1)
+    assert abs(float(loss) - L) <= 2e-2 * L
+    gg = grad.cpu().numpy().astype(np.float64)
+    o = 0
+    for ci, co, _ in pl.LAYERS:
+        n = 9 * ci * co + co
+        a, b = gg[o:o + n], g[o:o + n]
+        cos = np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert cos >= 0.995, (ci, co, cos)
+        assert np.linalg.norm(a - b) <= 6e-2 * np.linalg.norm(b), (ci, co)
+        o += n
+    _, grad2 = net.loss_grad(torch.from_numpy(Z).to(DEV), torch.from_numpy(Y1).to(DEV), sig)
+    assert torch.equal(grad, grad2)  # deterministic
+
+
+def test_training_reduces_the_loss():
+    Z, Y1, sig = pilot_train.training_set(48, size=64, seed=3, device=DEV)
+    net, losses = pilot_train.train(Z, Y1, sig, epochs=12, batch=8, lr=2e-3)
+    assert losses[-1] < 0.5 * losses[0], losses
+
+
+@pytest.mark.skipif(not os.path.exists(THETA_FILE), reason="trained parameters not present")
+@pytest.mark.parametrize("sigma", [15, 25, 50])
+def test_trained_pilot_against_plain_method(orc, sigma):
+    """What the trained network gains: it replaces stage 1 (matching, global
+    wavelet filtering, aggregation) by one forward pass.  At 1024^2 the
+    learned form must be faster than the plain GPU form, its PSNR within
+    0.3 dB of it, and on a 256^2 crop within 0.3 dB of the FP64 oracle's
+    plain two-stage result (the oracle as judge)."""
+    s = sigma / 255
+    theta = np.fromfile(THETA_FILE, dtype="<f4")
+    net = gbm3d.PilotNet(theta, DEV)
+    clean, X = synth.make_pair(1024, 1024, s, 4)
+    z = torch.from_numpy(X).to(DEV)
+    p = gbm3d.params_default()
+    ws = gbm3d.workspace(1024, 1024, p, DEV)
+    wl = torch.empty(gbm3d.workspace_bytes_learned(1024, 1024, p), dtype=torch.uint8, device=DEV)
+    out_p = gbm3d.denoise(z, s, p, ws)
+    out_l = gbm3d.denoise_learned(z, s, net, p, wl)
+
+    def timed(f):
+        f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / 5
+
+    tp = timed(lambda: gbm3d.denoise(z, s, p, ws, out_p))
+    tl = timed(lambda: gbm3d.denoise_learned(z, s, net, p, wl, out_l))
+    pp, pl_ = orc.psnr(out_p.cpu().numpy(), clean), orc.psnr(out_l.cpu().numpy(), clean)
+    print(f"sigma {sigma}: plain {pp:.3f} dB {tp * 1e3:.2f} ms, learned {pl_:.3f} dB {tl * 1e3:.2f} ms")
+    c = 256
+    crop = np.ascontiguousarray(X[:c, :c])
+    ref = orc.denoise(crop, s, nthreads=NT)
+    g = gbm3d.denoise_learned(torch.from_numpy(crop).to(DEV), s, net, p).cpu().numpy()
+    po, pg = orc.psnr(ref, clean[:c, :c]), orc.psnr(g, clean[:c, :c])
+    print(f"  crop: oracle plain {po:.3f} dB, learned {pg:.3f} dB")
+    assert tl < tp
+    assert pl_ >= pp - GAP_DB and pg >= po - GAP_DB
