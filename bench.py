@@ -57,6 +57,11 @@ WORKLOADS = {
                        "8, seed 7), per-image sigma in [5, 50]/255, 9x9 Gaussian blur std 1.6, 50 ADMM iterations "
                        "(rho 0.1), each denoising every image with two-stage G-BM3D (" + _PARAMS + "), one CUDA "
                        "graph per iteration"),
+    # stage 1 replaced by the trained network (gbm3d_denoise_learned)
+    "learned1024": dict(H=1024, W=1024, C=1, cpu_crop=256, ref_crop=128, learned=True,
+                        desc="G-BM3D with the learned pilot: 8-layer 3x3 conv network (32 channels, BF16 weights, "
+                             "FP32 accumulation) in place of stage 1, then the stage-2 Wiener filter; 1024x1024 "
+                             "grayscale fp32, sigma 25/255, " + _PARAMS),
     # the Sec. 5 parameter list (library preset 1): tiling reference grids
     "paper1024": dict(H=1024, W=1024, C=1, cpu_crop=512, ref_crop=256, preset=1,
                       desc="two-stage G-BM3D, 1024x1024 grayscale fp32, sigma 25/255, Sec. 5 parameters: stage 1 "
@@ -66,16 +71,33 @@ WORKLOADS = {
 H = W = 1024
 C = 1                   # channels
 PRESET = 0              # library parameter preset of the workload
+LEARNED = False         # stage 1 replaced by the trained network
 WORKLOAD = WORKLOADS["gray1024"]["desc"]
 CPU_CROP = 512          # cpu_baseline sample: top-left crop of the workload image
 REF_CROP = 256          # --impl reference: crop per step
 
 
 def set_workload(name: str):
-    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP, PRESET
+    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP, PRESET, LEARNED
     w = WORKLOADS[name]
     H, W, C, WORKLOAD, CPU_CROP, REF_CROP = w["H"], w["W"], w["C"], w["desc"], w["cpu_crop"], w["ref_crop"]
     PRESET = w.get("preset", 0)
+    LEARNED = w.get("learned", False)
+
+
+THETA_FILE = os.path.join(ROOT, "paper_2103_10765_gb300", "pilot_theta.f32")
+
+
+def learned_oracle(noisy, theta):
+    """The FP64 oracle of the learned path: the network's forward pass, then
+    stage 2 (matching on the pilot, Wiener filter, windowed aggregation)."""
+    import oracle
+    from oracle import pilot
+    pil = pilot.forward(theta, noisy[None], [SIGMA])[0]
+    q = oracle.Params()
+    idx, _ = oracle.match(pil, N=q.patch, s=q.step, R=q.search_radius, K=q.k2, nthreads=os.cpu_count() or 1)
+    g, w = oracle.filter_wiener(noisy, pil, idx, SIGMA, N=q.patch, K=q.k2, nthreads=os.cpu_count() or 1)
+    return oracle.aggregate(g, w, idx, noisy.shape[0], noisy.shape[1], N=q.patch, beta=q.kaiser_beta)
 
 
 def oracle_params():
@@ -273,7 +295,9 @@ class ClockSampler:
 def run_cpu_oracle(noisy_crop, nthreads):
     import oracle
     t0 = time.perf_counter()
-    if noisy_crop.ndim == 3:
+    if LEARNED:
+        out = learned_oracle(noisy_crop, np.fromfile(THETA_FILE, dtype="<f4").astype(np.float64))
+    elif noisy_crop.ndim == 3:
         out = oracle.denoise_color(noisy_crop, SIGMA, oracle_params(), nthreads=nthreads)
     else:
         out = oracle.denoise(noisy_crop, SIGMA, oracle_params(), nthreads=nthreads)
@@ -499,7 +523,12 @@ def main():
     pairs = [make_inputs(s) for s in seeds]
     noisy = [torch.from_numpy(n).to(dev) for _, n in pairs]
     out = torch.empty_like(noisy[0])
-    if C == 1:
+    net = None
+    if LEARNED:
+        net = gbm3d.PilotNet(np.fromfile(THETA_FILE, dtype="<f4"), dev)
+        ws = torch.empty(gbm3d.workspace_bytes_learned(H, W, p), dtype=torch.uint8, device=dev)
+        run = lambda x, o=out: gbm3d.denoise_learned(x, SIGMA, net, p, ws, o)  # noqa: E731
+    elif C == 1:
         ws = gbm3d.workspace(H, W, p, dev)
         run = lambda x, o=out: gbm3d.denoise(x, SIGMA, p, ws, o)  # noqa: E731
     else:
@@ -536,7 +565,9 @@ def main():
         clk.mark_end()
     gbm3d.set_match_events(None)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    match_ms = [[e4[0].elapsed_time(e4[1]) for e4 in mev], [e4[2].elapsed_time(e4[3]) for e4 in mev]]
+    # the learned path has no stage-1 matching: only events 2 and 3 are recorded
+    match_ms = [None if LEARNED else [e4[0].elapsed_time(e4[1]) for e4 in mev],
+                [e4[2].elapsed_time(e4[3]) for e4 in mev]]
     total_ms = max_over_ranks(sum(step_ms), dev)
     mpix = job_mpix(world, args.steps, total_ms)
 
@@ -546,8 +577,47 @@ def main():
                                                 ** 2).mean())))
 
     # e2e: pinned host in -> denoise -> host out, per step
+    plain = None
+    if LEARNED:
+        # the plain GPU form on the same images, for the comparison
+        wsp = gbm3d.workspace(H, W, p, dev)
+        outp = torch.empty_like(out)
+        gbm3d.denoise(noisy[0], SIGMA, p, wsp, outp)
+        barrier()
+        evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            evp[i][0].record(stream)
+            gbm3d.denoise(noisy[i % 3], SIGMA, p, wsp, outp)
+            evp[i][1].record(stream)
+        barrier()
+        pms = sum(a.elapsed_time(b) for a, b in evp)
+        gbm3d.denoise(noisy[0], SIGMA, p, wsp, outp)
+        pp = float(10 * math.log10(1.0 / float(((outp.cpu().double() - torch.from_numpy(pairs[0][0]).double())
+                                                 ** 2).mean())))
+        plain = {"value": job_mpix(world, args.steps, pms), "unit": "MPix/s", "ms_per_step": pms / args.steps,
+                 "psnr_db": pp, "psnr_gap_db": pp - psnr}
+        del wsp
     e2e = None
-    if not args.no_e2e:
+    if LEARNED and not args.no_e2e:
+        dev_in, host_out = torch.empty_like(out), torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+        host_in = [torch.from_numpy(n).pin_memory() for _, n in pairs]
+        barrier()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev2[i][0].record(stream)
+            dev_in.copy_(host_in[i % 3], non_blocking=True)
+            run(dev_in)
+            host_out.copy_(out, non_blocking=True)
+            ev2[i][1].record(stream)
+            stream.synchronize()
+        barrier()
+        e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), dev)
+        e2e = {"value": job_mpix(world, args.steps, e2e_ms), "unit": "MPix/s",
+               "h2d_bytes_per_step": H * W * 4, "d2h_bytes_per_step": H * W * 4}
+    elif not args.no_e2e:
         hd = gbm3d.HostDenoiser(H, W, p, dev, channels=C)
         host_in = [torch.from_numpy(n).pin_memory() for _, n in pairs]
         for i in range(args.warmup):
@@ -566,7 +636,7 @@ def main():
                "h2d_bytes_per_step": hd.h2d_bytes, "d2h_bytes_per_step": hd.d2h_bytes}
 
     # roofline of the dominant kernel, the block matcher (both stages' launches)
-    mt = [float(np.mean(x)) for x in match_ms]
+    mt = [float(np.mean(x)) if x is not None else 0.0 for x in match_ms]
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12
@@ -575,6 +645,8 @@ def main():
     tc = [tc_supported(H, W, g.patch, g.step, p.search_radius, k) for g, k in zip(geo, Ks)]
     # 2 N^2 FLOP per (reference, candidate), the Theorem-1 inner-product count
     flops = [2 * g.patch ** 2 * candidate_pairs(H, W, g.patch, g.step, p.search_radius) for g in geo]
+    if LEARNED:  # stage 2's matching only
+        flops[0] = 0
     achieved = sum(flops) / (sum(mt) / 1e3) / 1e12
     names = ["k_match_tc" if t else f"k_match<{g.patch}>" for t, g in zip(tc, geo)]
     roofline = {"kernel": (names[0] if names[0] == names[1] else " + ".join(names)) + " (block matching, both "
@@ -582,14 +654,15 @@ def main():
                               if all(tc) else "direct FP32 sum of squared differences") + ")",
                 "bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "launch_ms": {f"stage1_K{p.k1}": mt[0], f"stage2_K{p.k2}": mt[1]},
+                "launch_ms": ({f"stage2_K{p.k2}": mt[1]} if LEARNED else
+                              {f"stage1_K{p.k1}": mt[0], f"stage2_K{p.k2}": mt[1]}),
                 "launch_timing": "CUDA events recorded by the library around both matching launches of every "
                                  "timed step (same stream; with translations the last one's), averaged over the "
                                  "timed steps",
                 "flop_per_launch": {"stage1": flops[0], "stage2": flops[1]},
                 "peak_note": f"FP32 ALU: {N_SM} SMs x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz "
                              f"(SM clock from MEASURED_PEAKS.json, {peak_kind})"}
-    if all(tc):
+    if all(tc) and not LEARNED:
         tc_flop = sum(tc_executed_flop(H, W, g.patch, g.step, p.search_radius) for g in geo) / 2
         f16_peak = float(peaks.get("bf16_tflops", 1900.0))  # FP16 and BF16 share the nominal dense rate
         tc_achieved = 2 * tc_flop / (sum(mt) / 1e3) / 1e12
@@ -614,15 +687,24 @@ def main():
         crop = np.ascontiguousarray(pairs[0][1][..., :CPU_CROP, :CPU_CROP])
         ref, secs = run_cpu_oracle(crop, nt)
         gin = torch.from_numpy(crop).to(dev)
-        g = (gbm3d.denoise(gin, SIGMA, p) if C == 1 else gbm3d.denoise_color(gin, SIGMA, p)).cpu().numpy()
+        if LEARNED:
+            g = gbm3d.denoise_learned(gin, SIGMA, net, p).cpu().numpy()
+        else:
+            g = (gbm3d.denoise(gin, SIGMA, p) if C == 1 else gbm3d.denoise_color(gin, SIGMA, p)).cpu().numpy()
         clean = pairs[0][0][..., :CPU_CROP, :CPU_CROP].astype(np.float64)
         pg = 10 * math.log10(1 / np.mean((g - clean) ** 2))
         po = 10 * math.log10(1 / np.mean((ref - clean) ** 2))
         cpu = {"value": CPU_CROP * CPU_CROP / secs / 1e6, "unit": "MPix/s", "cores": nt, "kind": "oracle",
-               "sample": f"two-stage FP64 oracle on the top-left {CPU_CROP}x{CPU_CROP} crop of the workload image",
+               "sample": ("FP64 oracle of the learned path (network forward, stage 2)" if LEARNED else
+                          "two-stage FP64 oracle") + f" on the top-left {CPU_CROP}x{CPU_CROP} crop of the workload image",
                "seconds": secs, "psnr_gap_db_on_sample": abs(pg - po)}
 
-    launches = launches_per_denoise(p, C, tc)
+    if LEARNED:
+        # the network's 11 launches (noise level, weight packing, input, its 8
+        # layers) in place of stage 1, then stage 2 (matching, lists, Wiener, gather)
+        launches = 11 + (2 if tc[1] else 1) + 7 + 2
+    else:
+        launches = launches_per_denoise(p, C, tc)
     if rank == 0:
         line = {
             "metric": METRIC, "value": mpix, "unit": "MPix/s", "n_gpus": world, "steps": args.steps,
@@ -634,6 +716,8 @@ def main():
             "cpu_baseline": cpu, "clocks": clk.summary(),
             "step_ms": {"min": min(step_ms), "median": float(np.median(step_ms)), "max": max(step_ms)},
         }
+        if plain:
+            line["plain_form"] = plain
         print(json.dumps(line))
     if world > 1:
         torch.distributed.barrier()
