@@ -254,6 +254,38 @@ static GroupOut planar_out(const Sizes &S, char *ws, int H, int W, const StageGe
                            (float *)(ws + S.wslot), g.N);
 }
 
+// A second stream per host thread and device, with two events, on which
+// stage 1 builds its inverted lists while the wavelet transforms run (they
+// need only the match lists; the TV pass that permutes into the planar
+// layout waits for the lists).  Not used while the caller's stream is being
+// captured into a graph (every capture branch would share this stream).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;
+};
+
+static bool side_stream(cudaStream_t st, SideStream **out)
+{
+    constexpr int kMaxDev = 64;
+    static thread_local SideStream side[kMaxDev];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return false;
+    SideStream &ss = side[dev];
+    if (!ss.s) {
+        if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess) {
+            ss.s = nullptr;
+            return false;
+        }
+        if (cudaEventCreateWithFlags(&ss.ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ss.done, cudaEventDisableTiming) != cudaSuccess)
+            return false;
+    }
+    *out = &ss;
+    return true;
+}
+
 // ---- one stage on (possibly shifted) images ------------------------------
 static int run_stage1(const float *z, int zp, int H, int W, float sigma, const gbm3d_params *p, const Sizes &S,
                       char *ws, float *out, int op, cudaStream_t st)
@@ -265,11 +297,22 @@ static int run_stage1(const float *z, int zp, int H, int W, float sigma, const g
     cudaError_t e = match_any(z, H, W, zp, g, p, K, idx, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "match (stage 1)");
     if (g_match_events) cudaEventRecord(g_match_events[1], st);
-    e = build_csr(idx, g.G, K, H, W, g.N, ws + S.csr, true, st);
+    SideStream *side = nullptr;
+    const bool overlap = side_stream(st, &side);
+    if (overlap) { // inverted lists on the side stream, overlapping the transforms
+        e = cudaEventRecord(side->ready, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side->s, side->ready, 0);
+        if (e == cudaSuccess) e = build_csr(idx, g.G, K, H, W, g.N, ws + S.csr, true, side->s);
+        if (e == cudaSuccess) e = cudaEventRecord(side->done, side->s);
+    } else {
+        e = build_csr(idx, g.G, K, H, W, g.N, ws + S.csr, true, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "inverted lists (stage 1)");
     const GroupOut go = planar_out(S, ws, H, W, g);
-    e = launch_filter_ht(z, H, W, zp, idx, S.ht, sigma, p->tau_a, p->tau_b, p->cycle_spins, p->eps_w, go,
-                         ws + S.ht_off, st);
+    e = launch_ht_transforms(z, H, W, zp, idx, S.ht, sigma, p->tau_a, p->tau_b, p->cycle_spins, go, ws + S.ht_off,
+                             st);
+    if (e == cudaSuccess && overlap) e = cudaStreamWaitEvent(st, side->done, 0);
+    if (e == cudaSuccess) e = launch_ht_weights(S.ht, p->eps_w, go, ws + S.ht_off, st);
     if (e != cudaSuccess) return cuda_fail(e, "filter_ht");
     float win[kMaxPatch];
     kaiser(g.N, 0.f, win);

@@ -477,9 +477,9 @@ HtGeom ht_geom(int By, int Bx, int K, int levels, int N)
     return g;
 }
 
-cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
-                             float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, const GroupOut &out,
-                             void *ht_ws, cudaStream_t st)
+cudaError_t launch_ht_transforms(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
+                                 float sigma, float tau_a, float tau_b, int cycle_spins, const GroupOut &out,
+                                 void *ht_ws, cudaStream_t st)
 {
     if (g.N != 8 && g.N != 16) return cudaErrorInvalidValue;
     char *base = (char *)ht_ws;
@@ -497,6 +497,14 @@ cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const in
         launch_levels<3>(g, img, pitch, ofs, C, sigma, tau_a, tau_b, cycle_spins, gm_out, st);
     else
         launch_levels<4>(g, img, pitch, ofs, C, sigma, tau_a, tau_b, cycle_spins, gm_out, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ht_weights(const HtGeom &g, float eps_w, const GroupOut &out, void *ht_ws, cudaStream_t st)
+{
+    char *base = (char *)ht_ws;
+    const bool permute = out.slot_of != nullptr;
+    float *gm = permute ? (float *)(base + g.gm_off) : out.base;
     const int G = g.By * g.Bx;
     if (g.N == 8) {
         switch (g.K) {
@@ -512,6 +520,18 @@ cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const in
         }
     }
     return cudaGetLastError();
+}
+
+} // namespace gbm3d
+
+namespace gbm3d {
+
+cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
+                             float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, const GroupOut &out,
+                             void *ht_ws, cudaStream_t st)
+{
+    cudaError_t e = launch_ht_transforms(img, H, W, pitch, idx, g, sigma, tau_a, tau_b, cycle_spins, out, ht_ws, st);
+    return e == cudaSuccess ? launch_ht_weights(g, eps_w, out, ht_ws, st) : e;
 }
 
 } // namespace gbm3d

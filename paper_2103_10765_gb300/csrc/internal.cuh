@@ -141,6 +141,13 @@ cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, 
 // (synchronous read).
 cudaError_t tc_stats(unsigned long long *timeouts, unsigned long long *rematched);
 
+// launch_filter_ht in two parts: the cycle-spun transforms into the
+// group-major scratch (needs only idx), then the TV weights and, for a
+// position-planar out, the permutation (needs out's slot table).
+cudaError_t launch_ht_transforms(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
+                                 float sigma, float tau_a, float tau_b, int cycle_spins, const GroupOut &out,
+                                 void *ht_ws, cudaStream_t st);
+cudaError_t launch_ht_weights(const HtGeom &g, float eps_w, const GroupOut &out, void *ht_ws, cudaStream_t st);
 cudaError_t launch_filter_ht(const float *img, int H, int W, int pitch, const int32_t *idx, const HtGeom &g,
                              float sigma, float tau_a, float tau_b, int cycle_spins, float eps_w, const GroupOut &out,
                              void *ht_ws, cudaStream_t st);
