@@ -73,10 +73,14 @@ typedef struct {
     float eps_w;        /* lower guard on TV and Wiener weight denominators   */
     int match_engine;   /* block matching: 0 = tensor cores where supported,   */
                         /* else direct; 1 = direct FP32 SSD; 2 = tensor cores */
-                        /* (EUNSUPPORTED where not).  Same results, bit for    */
-                        /* bit: the tensor-core engine ranks with the norm    */
-                        /* expansion of Theorem 1 and re-ranks its certified  */
-                        /* survivors with the exact direct sum.               */
+                        /* (EUNSUPPORTED where not).  Engines 1 and 2 give     */
+                        /* the same results, bit for bit: the tensor-core     */
+                        /* engine ranks with the norm expansion of Theorem 1  */
+                        /* and re-ranks its certified survivors with the      */
+                        /* exact direct sum.  3 = box sums shared by          */
+                        /* neighbouring references (N = 8, s <= 3): exact     */
+                        /* selection on FP32 distances summed in another      */
+                        /* order (equal to the others up to FP32 rounding).   */
     int patch2;         /* stage-2 block side; 0 = patch.  The Wiener filter  */
                         /* is built for 8 (Sec. 5: N = 16 in stage 1, 8 in 2) */
     int step2;          /* stage-2 grid stride; 0 = step                      */

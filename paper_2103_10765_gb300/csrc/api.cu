@@ -92,8 +92,8 @@ static int check_params(const gbm3d_params *p)
     if (!(p->eps_w > 0.f) || !isfinite(p->eps_w)) return fail(GBM3D_EINVAL, "eps_w must be positive");
     if (!isfinite(p->tau_a) || !isfinite(p->tau_b) || !isfinite(p->kaiser_beta) || p->kaiser_beta < 0.f)
         return fail(GBM3D_EINVAL, "tau_a, tau_b, kaiser_beta must be finite (beta >= 0)");
-    if (p->match_engine < 0 || p->match_engine > 2)
-        return fail(GBM3D_EINVAL, "match_engine %d: 0 auto, 1 direct, 2 tensor cores", p->match_engine);
+    if (p->match_engine < 0 || p->match_engine > 3)
+        return fail(GBM3D_EINVAL, "match_engine %d: 0 auto, 1 direct, 2 tensor cores, 3 box sums", p->match_engine);
     for (int sg = 1; sg <= 2; sg++)
         if (match_smem_bytes(stage_step(p, sg), p->search_radius, stage_patch(p, sg)) > 227 * 1024)
             return fail(GBM3D_EUNSUPPORTED, "search region of R=%d, s=%d, N=%d exceeds shared memory",
@@ -138,6 +138,9 @@ static int check_window(int H, int W, int N, int R, int K)
 // switched off), else the direct one; engine 2 where unsupported is refused.
 static int check_engine(int H, int W, const gbm3d_params *p, const StageGeom &g, int K)
 {
+    if (p->match_engine == 3 && !match_box_supported(g.N, g.s, p->search_radius, K))
+        return fail(GBM3D_EUNSUPPORTED, "box-sum matching needs N = 8, s <= 3 and K <= 32 (N=%d s=%d K=%d)", g.N, g.s,
+                    K);
     if (p->match_engine == 2 && !match_tc_supported(H, W, g.N, g.s, p->search_radius, K))
         return fail(GBM3D_EUNSUPPORTED,
                     "tensor-core matching needs N = 8, 7 s + 2 R + 1 <= 64 and K <= 32 (N=%d s=%d R=%d K=%d)", g.N,
@@ -160,6 +163,8 @@ static int check_stages(int H, int W, const gbm3d_params *p)
 static cudaError_t match_any(const float *img, int H, int W, int pitch, const StageGeom &g, const gbm3d_params *p,
                              int K, int32_t *idx, float *dist, cudaStream_t st)
 {
+    if (p->match_engine == 3)
+        return launch_match_box(img, H, W, pitch, g.By, g.Bx, g.s, p->search_radius, K, idx, dist, st);
     if (p->match_engine != 1 && match_tc_supported(H, W, g.N, g.s, p->search_radius, K))
         return launch_match_tc(img, H, W, pitch, g.By, g.Bx, g.s, p->search_radius, K, idx, dist, st);
     return launch_match(img, H, W, pitch, g.By, g.Bx, g.N, g.s, p->search_radius, K, idx, dist, st);

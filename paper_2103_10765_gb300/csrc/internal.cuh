@@ -136,6 +136,11 @@ cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, i
                             int32_t *idx, float *dist, cudaStream_t st);
 cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                              int32_t *idx, float *dist, cudaStream_t st);
+// Box-sum matching (same lists as launch_match up to FP32 rounding of the
+// distances; exact selection) for N = 8 and strides 1..3.
+bool match_box_supported(int N, int s, int R, int K);
+cudaError_t launch_match_box(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
+                             int32_t *idx, float *dist, cudaStream_t st);
 // Cumulative counts of the tensor-core matcher on the current device: bounded
 // waits that gave up, references re-matched by the direct kernel
 // (synchronous read).

@@ -126,6 +126,10 @@ def test_validation_errors(g):
     # matching engine: out of range; tensor cores where the window union is too wide
     q = p.replace(match_engine=3)
     assert lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None) == g.EINVAL
+    q = p.replace(match_engine=3, step=4)  # box sums: s <= 3
+    assert lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None) == g.EUNSUPPORTED
+    q = p.replace(match_engine=4)
+    assert lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None) == g.EINVAL
     q = p.replace(match_engine=2, search_radius=30)
     assert lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None) == g.EUNSUPPORTED
     assert lib.gbm3d_denoise(fake, 64, 64, 64, ctypes.c_float(0.1), ctypes.byref(q), ctypes.c_void_p(0x2000),

@@ -337,3 +337,52 @@ def test_paper_preset_sigma_zero_and_constant():
     out = gbm3d.denoise(gpu(synth.constant_image(48, 40, c)), s, q).cpu().numpy()
     P = c * 8 * np.sqrt(16)
     assert np.abs(out - c * P ** 2 / (P ** 2 + s ** 2)).max() <= 1e-5
+
+
+# ---- box-sum matching engine (match_engine = 3)
+
+@pytest.mark.parametrize("H,W,sigma,K,s,R", [(64, 72, 25, 16, 3, 19), (100, 83, 25, 32, 3, 19), (13, 13, 50, 32, 3, 19),
+                                             (40, 40, 0, 32, 3, 19), (57, 131, 15, 8, 1, 5), (70, 66, 25, 16, 2, 9),
+                                             (90, 77, 50, 32, 3, 12), (48, 48, 25, 2, 3, 3)])
+def test_box_engine_parity(orc, H, W, sigma, K, s, R):
+    _, X = synth.make_pair(H, W, sigma / 255, 2)
+    p = gbm3d.params_default().replace(match_engine=3, step=s, search_radius=R)
+    gidx, gdist = gbm3d.match(gpu(X), K, p, with_dist=True)
+    oidx, odist = orc.match(X, N=8, s=s, R=R, K=K + 1, nthreads=NT)
+    frac = check_match(X, gidx.cpu().numpy(), gdist.cpu().numpy(), oidx, odist, W, K, grid_refs(orc, H, W, 8, s))
+    assert frac > 0.9
+
+
+def test_box_engine_exact_ties_flat_image(orc):
+    X = np.zeros((48, 56), np.float32)
+    X[:, 28:] = 0.5
+    X[20:30, 10:20] = 0.25
+    p = gbm3d.params_default().replace(match_engine=3)
+    gidx, _ = gbm3d.match(gpu(X), 32, p, with_dist=True)
+    oidx, _ = orc.match(X, K=32, nthreads=NT)
+    np.testing.assert_array_equal(gidx.cpu().numpy(), oidx)
+
+
+@pytest.mark.parametrize("K", [16, 32])
+def test_box_engine_full_size_sampled(orc, K):
+    H = W = 1024
+    _, X = synth.make_pair(H, W, 25 / 255, 1)
+    p = gbm3d.params_default().replace(match_engine=3)
+    gidx, gdist = gbm3d.match(gpu(X), K, p, with_dist=True)
+    gidx2, _ = gbm3d.match(gpu(X), K, p, with_dist=True)
+    assert torch.equal(gidx, gidx2)  # deterministic
+    gy, gx = orc.grid(H, 8, 3), orc.grid(W, 8, 3)
+    rs = np.random.default_rng(8)
+    sel = list(rs.choice(len(gy) * len(gx), 300, replace=False)) + [0, len(gx) - 1, len(gy) * len(gx) - 1]
+    refs = [(int(gy[t // len(gx)]), int(gx[t % len(gx)])) for t in sel]
+    oidx, odist = orc.match_refs(X, [r[0] for r in refs], [r[1] for r in refs], K=K + 1, nthreads=NT)
+    frac = check_match(X, gidx.cpu().numpy()[sel], gdist.cpu().numpy()[sel], oidx, odist, W, K, refs)
+    assert frac > 0.9
+
+
+def test_box_engine_denoise_psnr(orc):
+    s = 25 / 255
+    clean, X = synth.make_pair(256, 256, s, 1)
+    out = gbm3d.denoise(gpu(X), s, gbm3d.params_default().replace(match_engine=3)).cpu().numpy()
+    ref = orc.denoise(X, s, nthreads=NT)
+    assert abs(orc.psnr(out, clean) - orc.psnr(ref, clean)) <= 0.01
