@@ -108,18 +108,29 @@ struct BoxArgs {
     float *dist;
 };
 
-// Offset pair number o -> (dy, dx0): rows by increasing |dy| (0, 1, -1, 2, ...),
-// within a row dx0 = -R, -R + 4, ...
-__device__ __forceinline__ void batch_offset(int o, int R, int nbx, int &dy, int &dx0)
+// Order of the dx batches [dx0, dx0 + 3] (dx0 = -R + 4 b) within a row of
+// offsets: by increasing distance of their centre from 0, nearest candidates
+// first so that the thresholds tighten early.  Rows go by increasing |dy|
+// (0, 1, -1, 2, ...).
+constexpr int kMaxNbx = 32; // R <= 125
+
+__device__ __forceinline__ int batch_dy(int row) { return (row & 1) ? (row + 1) >> 1 : -(row >> 1); }
+
+__device__ void batch_order(int R, int nbx, int *dx0)
 {
-    const int row = o / nbx, b = o - row * nbx;
-    dy = (row & 1) ? (row + 1) >> 1 : -(row >> 1);
-    dx0 = -R + kDX * b;
+    // b0: the batch whose centre -R + 4 b0 + 1.5 is nearest 0; then b0 + 1,
+    // b0 - 1, b0 + 2, ... (those inside [0, nbx))
+    const int b0 = (R + 1) / kDX - ((R + 1) % kDX == 0 ? 1 : 0);
+    int n = 0;
+    for (int t = 0; n < nbx; t++) {
+        const int cand = b0 + ((t & 1) ? (t + 1) >> 1 : -(t >> 1));
+        if (cand >= 0 && cand < nbx) dx0[n++] = -R + kDX * cand;
+    }
 }
 
 // SS: the grid stride (compile time, so the row windows stay in registers).
 template <int LP, int SS>
-__global__ void __launch_bounds__(kThr, 1) k_match_box(BoxArgs A)
+__global__ void __launch_bounds__(kThr, 2) k_match_box(BoxArgs A)
 {
     extern __shared__ __align__(16) float sm[];
     const int H = A.H, W = A.W, R = A.R, K = A.K, RW = A.RW;
@@ -199,9 +210,15 @@ __global__ void __launch_bounds__(kThr, 1) k_match_box(BoxArgs A)
 
     const int nbx = (2 * R + 1 + kDX - 1) / kDX, nrow = 2 * R + 1;
     const int nb = nrow * nbx;
-    for (int o = 0; o < nb; o++) {
-        int dy, dx0;
-        batch_offset(o, R, nbx, dy, dx0);
+    __shared__ int s_dx0[kMaxNbx];
+    if (tid == 0) batch_order(R, nbx, s_dx0);
+    __syncthreads();
+    for (int o = 0, row = 0, k = 0; o < nb; o++) {
+        const int dy = batch_dy(row), dx0 = s_dx0[k];
+        if (++k == nbx) {
+            k = 0;
+            row++;
+        }
         float *sxb = sx + (o & 1) * sxs;
         // phase A: row sums of this row for 4 offsets and 4 lattice columns
         if (arow) {
@@ -340,7 +357,8 @@ bool match_box_supported(int N, int s, int R, int K)
 {
     // the 64 phase-A rows (256 threads, 4 per row) cover the tile's
     // (kTP - 1) s + N pixel rows for s <= 3
-    return N == kPatch && s >= 1 && s <= 3 && K >= 2 && K <= kMaxK && box_layout(s, R).bytes <= 200 * 1024;
+    return N == kPatch && s >= 1 && s <= 3 && K >= 2 && K <= kMaxK && (2 * R + 1 + kDX - 1) / kDX <= kMaxNbx &&
+           box_layout(s, R).bytes <= 200 * 1024;
 }
 
 cudaError_t launch_match_box(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
