@@ -81,6 +81,9 @@ def test_launch_count_matches_launch_list():
 
 
 def test_engine_choice_mirrors_library():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("passes fake device pointers: runs where no GPU is visible")
     import bench
     from paper_2103_10765_gb300 import build, gbm3d
     build.build_library()
