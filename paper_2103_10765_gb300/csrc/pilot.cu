@@ -112,94 +112,142 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <bool kFwd>
-__global__ void __launch_bounds__(128) k_conv_mid(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ V,
-                                                  const float *__restrict__ bias, const float *__restrict__ mask,
-                                                  float *__restrict__ out, int H, int W)
+// Persistent: each CTA stages V once, then walks tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the next tile's input is loaded into
+// registers while the tensor cores work on the current one (two input
+// buffers in shared memory).
+constexpr int kInPix = (kTY + 2) * (kTX + 2);                 // 204 pixels per input tile
+constexpr int kInLd = (kInPix * 8 + 127) / 128;               // float4 loads per thread per tile (13)
+constexpr int kConvSmem = (9 * kC * kRow + 2 * kInPix * kRow) * 2; // bytes: V + two input tiles
+
+struct ConvTiles {
+    int tx, ty, per_img, total; // tiles along x, y; per image; in the batch
+};
+
+__device__ __forceinline__ void conv_tile(const ConvTiles &T, int t, int &b, int &y0, int &x0)
 {
-    __shared__ __align__(16) __nv_bfloat16 s_in[(kTY + 2) * (kTX + 2) * kRow];
-    __shared__ __align__(16) __nv_bfloat16 s_v[9 * kC * kRow];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, b = blockIdx.z;
-    const size_t img = (size_t)b * H * W;
-    // stage V (9 x 32 rows of 32 BF16, as 16-byte chunks)
+    b = t / T.per_img;
+    const int r = t - b * T.per_img, ty = r / T.tx;
+    y0 = ty * kTY;
+    x0 = (r - ty * T.tx) * kTX;
+}
+
+template <bool kFwd>
+__global__ void __launch_bounds__(128, 4) k_conv_mid(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ V,
+                                                     const float *__restrict__ bias, const float *__restrict__ mask,
+                                                     float *__restrict__ out, int H, int W, ConvTiles T)
+{
+    extern __shared__ __align__(16) __nv_bfloat16 cs[];
+    __nv_bfloat16 *s_v = cs, *s_in0 = cs + 9 * kC * kRow;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+    // stage V (9 x 32 rows of 32 BF16, as 16-byte chunks) once
     for (int i = tid; i < 9 * kC * 4; i += 128) {
         const int row = i >> 2, q = i & 3;
         *reinterpret_cast<uint4 *>(s_v + row * kRow + q * 8) = *reinterpret_cast<const uint4 *>(V + row * kC + q * 8);
     }
-    // stage the input tile, FP32 -> BF16, zero outside the image
-    for (int i = tid; i < (kTY + 2) * (kTX + 2) * 8; i += 128) {
-        const int pix = i >> 3, q = i & 7;
-        const int ty = pix / (kTX + 2), tx = pix - ty * (kTX + 2);
-        const int yy = y0 + ty - 1, xx = x0 + tx - 1;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = *reinterpret_cast<const float4 *>(in + (img + (size_t)yy * W + xx) * kC + q * 4);
-        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-        __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(s_in + pix * kRow + q * 4);
-        d[0] = lo;
-        d[1] = hi;
+    float4 pre[kInLd];
+    auto fetch = [&](int t) { // the input tile of t, with halo, zero outside the image
+        int b, y0, x0;
+        conv_tile(T, t, b, y0, x0);
+        const size_t img = (size_t)b * H * W;
+#pragma unroll
+        for (int j = 0; j < kInLd; j++) {
+            const int i = tid + 128 * j, pix = i >> 3, q = i & 7;
+            const int ty = pix / (kTX + 2), tx = pix - ty * (kTX + 2);
+            const int yy = y0 + ty - 1, xx = x0 + tx - 1;
+            pre[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < kInPix * 8 && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                pre[j] = *reinterpret_cast<const float4 *>(in + (img + (size_t)yy * W + xx) * kC + q * 4);
+        }
+    };
+    auto put = [&](__nv_bfloat16 *dst) { // FP32 -> BF16 into an input buffer
+#pragma unroll
+        for (int j = 0; j < kInLd; j++) {
+            const int i = tid + 128 * j;
+            if (i >= kInPix * 8) continue;
+            const int pix = i >> 3, q = i & 7;
+            __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(dst + pix * kRow + q * 4);
+            d[0] = __floats2bfloat162_rn(pre[j].x, pre[j].y);
+            d[1] = __floats2bfloat162_rn(pre[j].z, pre[j].w);
+        }
+    };
+    int t = blockIdx.x;
+    if (t < T.total) {
+        fetch(t);
+        put(s_in0);
     }
     __syncthreads();
-    float acc[2][4][4];
+    for (int it = 0; t < T.total; t += gridDim.x, it++) {
+        const __nv_bfloat16 *s_in = s_in0 + (it & 1) * kInPix * kRow;
+        const int tn = t + gridDim.x;
+        if (tn < T.total) fetch(tn); // in flight during the MMAs below
+        float acc[2][4][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; mt++)
+        for (int mt = 0; mt < 2; mt++)
 #pragma unroll
-        for (int nt = 0; nt < 4; nt++)
+            for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-            for (int r = 0; r < 4; r++) acc[mt][nt][r] = 0.f;
+                for (int r = 0; r < 4; r++) acc[mt][nt][r] = 0.f;
 #pragma unroll 1
-    for (int tap = 0; tap < 9; tap++) {
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        for (int tap = 0; tap < 9; tap++) {
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
 #pragma unroll
-        for (int h = 0; h < 2; h++) { // channels 16 h .. 16 h + 15
-            uint32_t a[2][4], bb[4][2];
+            for (int h = 0; h < 2; h++) { // channels 16 h .. 16 h + 15
+                uint32_t a[2][4], bb[4][2];
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) {
-                const int p0 = (warp + 1 + dy) * (kTX + 2) + mt * 16 + g + 1 + dx; // tile pixel of row g
-                const __nv_bfloat16 *r0 = s_in + p0 * kRow + 16 * h + 2 * t;
-                const __nv_bfloat16 *r1 = r0 + 8 * kRow; // pixel g + 8
-                a[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
-                a[mt][1] = *reinterpret_cast<const uint32_t *>(r1);
-                a[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-                a[mt][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+                for (int mt = 0; mt < 2; mt++) {
+                    const int p0 = (warp + 1 + dy) * (kTX + 2) + mt * 16 + g + 1 + dx; // tile pixel of row g
+                    const __nv_bfloat16 *r0 = s_in + p0 * kRow + 16 * h + 2 * t4;
+                    const __nv_bfloat16 *r1 = r0 + 8 * kRow; // pixel g + 8
+                    a[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
+                    a[mt][1] = *reinterpret_cast<const uint32_t *>(r1);
+                    a[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+                    a[mt][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+                }
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++) {
+                    const __nv_bfloat16 *v = s_v + (tap * kC + nt * 8 + g) * kRow + 16 * h + 2 * t4;
+                    bb[nt][0] = *reinterpret_cast<const uint32_t *>(v);
+                    bb[nt][1] = *reinterpret_cast<const uint32_t *>(v + 8);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                    for (int nt = 0; nt < 4; nt++)
+                        mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bb[nt][0], bb[nt][1]);
             }
-#pragma unroll
-            for (int nt = 0; nt < 4; nt++) {
-                const __nv_bfloat16 *v = s_v + (tap * kC + nt * 8 + g) * kRow + 16 * h + 2 * t;
-                bb[nt][0] = *reinterpret_cast<const uint32_t *>(v);
-                bb[nt][1] = *reinterpret_cast<const uint32_t *>(v + 8);
-            }
+        }
+        int b, y0, x0;
+        conv_tile(T, t, b, y0, x0);
+        const size_t img = (size_t)b * H * W;
+        const int y = y0 + warp;
+        if (y < H) {
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll
-                for (int nt = 0; nt < 4; nt++)
-                    mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bb[nt][0], bb[nt][1]);
-        }
-    }
-    const int y = y0 + warp;
-    if (y >= H) return;
+                for (int half = 0; half < 2; half++) {
+                    const int x = x0 + mt * 16 + g + 8 * half;
+                    if (x >= W) continue;
+                    const size_t pp = img + (size_t)y * W + x;
 #pragma unroll
-    for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-        for (int half = 0; half < 2; half++) {
-            const int x = x0 + mt * 16 + g + 8 * half;
-            if (x >= W) continue;
-            const size_t p = img + (size_t)y * W + x;
-#pragma unroll
-            for (int nt = 0; nt < 4; nt++) {
-                const int n = nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if (kFwd) {
-                    v0 = fmaxf(v0 + bias[n], 0.f);
-                    v1 = fmaxf(v1 + bias[n + 1], 0.f);
-                } else {
-                    const float2 mk = *reinterpret_cast<const float2 *>(mask + p * kC + n);
-                    v0 = mk.x > 0.f ? v0 : 0.f;
-                    v1 = mk.y > 0.f ? v1 : 0.f;
+                    for (int nt = 0; nt < 4; nt++) {
+                        const int n = nt * 8 + 2 * t4;
+                        float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                        if (kFwd) {
+                            v0 = fmaxf(v0 + bias[n], 0.f);
+                            v1 = fmaxf(v1 + bias[n + 1], 0.f);
+                        } else {
+                            const float2 mk = *reinterpret_cast<const float2 *>(mask + pp * kC + n);
+                            v0 = mk.x > 0.f ? v0 : 0.f;
+                            v1 = mk.y > 0.f ? v1 : 0.f;
+                        }
+                        *reinterpret_cast<float2 *>(out + pp * kC + n) = make_float2(v0, v1);
+                    }
                 }
-                *reinterpret_cast<float2 *>(out + p * kC + n) = make_float2(v0, v1);
-            }
         }
+        if (tn < T.total) put(s_in0 + ((it + 1) & 1) * kInPix * kRow);
+        __syncthreads();
+    }
 }
 
 // Last layer, 32 -> 1: r = b + sum W8 x7; pilot = Z - r.  With a target: the
@@ -400,6 +448,33 @@ PilotLayout pilot_layout(int B, int H, int W, bool train)
     return L;
 }
 
+ConvTiles conv_tiles(int B, int H, int W)
+{
+    ConvTiles T;
+    T.tx = (W + kTX - 1) / kTX;
+    T.ty = (H + kTY - 1) / kTY;
+    T.per_img = T.tx * T.ty;
+    T.total = B * T.per_img;
+    return T;
+}
+
+// Persistent grid of the 32 -> 32 convolutions: four CTAs per SM (shared
+// memory allows four), no more than there are tiles.  Sets the kernels'
+// shared-memory limit once.
+int conv_ctas(const ConvTiles &T)
+{
+    static int per_dev = 0;
+    if (!per_dev) {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 148;
+        cudaFuncSetAttribute(k_conv_mid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+        cudaFuncSetAttribute(k_conv_mid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+        per_dev = 4 * nsm;
+    }
+    return T.total < per_dev ? T.total : per_dev;
+}
+
 int wgrad_ctas()
 {
     static int n = 0;
@@ -426,11 +501,13 @@ cudaError_t pilot_forward(const float *Z, int B, int H, int W, int zpitch, long 
     auto X = [&](int l) { // x_l, l = 1..7
         return act + (size_t)(train ? l - 1 : (l - 1) & 1) * L.plane * kC;
     };
-    const dim3 g128((W + 127) / 128, H, B), gmid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, B);
+    const dim3 g128((W + 127) / 128, H, B);
+    const ConvTiles T = conv_tiles(B, H, W);
+    const int gm = conv_ctas(T);
     k_conv_first<<<g128, 128, 0, st>>>(x0, w1r, theta, X(1), H, W);
     for (int m = 0; m < kMid; m++)
-        k_conv_mid<true><<<gmid, 128, 0, st>>>(X(m + 1), wf + (size_t)m * kWm, theta + off_bm(m), nullptr, X(m + 2),
-                                               H, W);
+        k_conv_mid<true><<<gm, 128, kConvSmem, st>>>(X(m + 1), wf + (size_t)m * kWm, theta + off_bm(m), nullptr,
+                                                     X(m + 2), H, W, T);
     const float inv_n = 1.f / (float)L.plane;
     k_conv_last<<<g128, 128, 0, st>>>(X(7), w8r, theta, Z, zpitch, zbatch, Y1, pilot, ppitch, pbatch,
                                       train ? (float *)(ws + L.g8) : nullptr,
@@ -453,13 +530,15 @@ cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, 
     // last layer
     k_wgrad<32, 1><<<nc, 9 * 32 + 1, 0, st>>>(X(7), g8, B, H, W, part);
     k_reduce<<<(kW8 + 1 + 255) / 256, 256, 0, st>>>(part, nc, kW8 + 1, grad + kOffW8);
-    const dim3 g128((W + 127) / 128, H, B), gmid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, B);
+    const dim3 g128((W + 127) / 128, H, B);
+    const ConvTiles T = conv_tiles(B, H, W);
+    const int gm = conv_ctas(T);
     k_last_bwd<<<g128, 128, 0, st>>>(g8, w8r, X(7), ga, H, W);
     float *gcur = ga, *gnext = gb;
     for (int m = kMid - 1; m >= 0; m--) { // layer m + 2: x_{m+1} -> x_{m+2}; gcur = dL/dpre_{m+2}
         k_wgrad<32, 32><<<nc, 9 * 32 + 1, 0, st>>>(X(m + 1), gcur, B, H, W, part);
         k_reduce<<<(kWm + kC + 255) / 256, 256, 0, st>>>(part, nc, kWm + kC, grad + off_wm(m));
-        k_conv_mid<false><<<gmid, 128, 0, st>>>(gcur, wb + (size_t)m * kWm, nullptr, X(m + 1), gnext, H, W);
+        k_conv_mid<false><<<gm, 128, kConvSmem, st>>>(gcur, wb + (size_t)m * kWm, nullptr, X(m + 1), gnext, H, W, T);
         float *t = gcur;
         gcur = gnext;
         gnext = t;

@@ -42,7 +42,7 @@ def initial_theta(seed: int = 11) -> np.ndarray:
     return synth.he_normal_params(seed, shapes)
 
 
-def train(Z, Y1, sigmas, epochs: int = 40, batch: int = 16, lr: float = 1e-3, lr_min: float = 1e-5,
+def train(Z, Y1, sigmas, epochs: int = 120, batch: int = 16, lr: float = 1e-3, lr_min: float = 1e-5,
           seed: int = 5, theta0=None, log=None):
     """Adam over shuffled mini-batches (the order drawn from a SplitMix64
     stream); returns the trained PilotNet and the per-epoch mean losses."""
@@ -72,7 +72,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--n", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--epochs", type=int, default=120)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=1e-3)
     a = ap.parse_args()

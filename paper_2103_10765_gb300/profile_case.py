@@ -8,6 +8,9 @@ estimate for stage-2 ops), then `reps` launches of the chosen entry point:
   ht                gbm3d_filter_ht        wiener   gbm3d_filter_wiener
   agg1 / agg2       gbm3d_aggregate of the stage-1 / stage-2 groups
   denoise           gbm3d_denoise
+  match3            gbm3d_match with the box-sum engine (K1)
+  pilot             the learned pilot's forward pass (committed parameters)
+  pnp               one plug-and-play iteration of a 4-image batch (no graph)
 """
 import argparse
 
@@ -42,7 +45,24 @@ def main():
         "agg1": lambda: gbm3d.aggregate(g1, w1, idx1, H, W, p, 0.0, ws),
         "agg2": lambda: gbm3d.aggregate(g2, w2, idx2, H, W, p, p.kaiser_beta, ws),
         "denoise": lambda: gbm3d.denoise(z, a.sigma, p, ws),
+        "match3": lambda: gbm3d.match(z, p.k1, p.replace(match_engine=3)),
     }
+    if a.op == "pilot":
+        import os
+
+        import numpy as np
+        theta = np.fromfile(os.path.join(os.path.dirname(gbm3d.__file__), "pilot_theta.f32"), dtype="<f4")
+        net = gbm3d.PilotNet(theta, z.device)
+        zb = z[None].contiguous()
+        ops["pilot"] = lambda: net.forward(zb, [a.sigma])
+    if a.op == "pnp":
+        import numpy as np
+        t = np.arange(9) - 4.0
+        g = np.exp(-0.5 * (t / 1.6) ** 2)
+        g = (g / g.sum()).astype(np.float32)
+        ys = [torch.from_numpy(synth.make_blur_pair(h, w, 0.1, 7)[1]).cuda() for h, w in ((H, W), (H // 2, W), (H, W // 2), (H // 2, W // 2))]
+        plan = gbm3d.PnpPlan(ys, [0.1] * 4, g, p, gbm3d.PnpParams(iters=1, use_graph=0, autotune=0))
+        ops["pnp"] = plan.run
     for _ in range(a.reps):
         ops[a.op]()
     torch.cuda.synchronize()
