@@ -218,24 +218,26 @@ constexpr int kGatherWarps = 8;
 
 template <int N>
 struct GatherCfg {
-    static constexpr int kCap = N == 8 ? 160 : 96;                  // slots staged per warp
-    static constexpr int kWarpFloats = kCap * N + 2 * kCap;          // values, columns, weights
+    static constexpr int kCap = N == 8 ? 144 : 88;                  // slots staged per warp (4 CTAs per SM)
+    static constexpr int kRowS = N + 1;                              // staged value row stride (odd: fewer conflicts)
+    static constexpr int kWarpFloats = kCap * kRowS + 2 * kCap;      // values; (column, weight) pairs
     static constexpr int kSmem = kGatherWarps * kWarpFloats * 4 + 64; // bytes, plus the window
 };
 
-template <int N>
+// WIN: the window is not flat (stage 2's Kaiser window); stage 1's flat
+// window skips the per-contribution lookup (its factors are all 1).
+template <int N, bool WIN>
 __global__ void __launch_bounds__(kGatherWarps * 32)
 k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_slot, const int *__restrict__ off,
                 const int *__restrict__ lpos, long long plane_stride, int H, int W, int pitch, Win win,
                 float *__restrict__ out)
 {
-    constexpr int kCap = GatherCfg<N>::kCap;
+    constexpr int kCap = GatherCfg<N>::kCap, kRowS = GatherCfg<N>::kRowS;
     extern __shared__ __align__(16) float g_smem[];
     float *sw = g_smem; // window (16 floats)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *sv = g_smem + 16 + warp * GatherCfg<N>::kWarpFloats;
-    int *sc = reinterpret_cast<int *>(sv + kCap * N);
-    float *swt = sv + kCap * N + kCap;
+    float2 *scw = reinterpret_cast<float2 *>(sv + kCap * kRowS + (kCap * kRowS & 1)); // (column as int bits, w wa)
     if (threadIdx.x < N) sw[threadIdx.x] = win.v[threadIdx.x];
     __syncthreads();
     const int y = blockIdx.y;
@@ -258,18 +260,26 @@ k_gather_planar(const float *__restrict__ planes, const float *__restrict__ w_sl
             const int cn_ = min(kCap, S1 - c0);
             for (int i = lane; i < cn_; i += 32) {
                 const float4 *src = reinterpret_cast<const float4 *>(plane + (size_t)(c0 + i) * N);
-                float4 *dst = reinterpret_cast<float4 *>(sv + i * N);
+                float *dst = sv + i * kRowS;
 #pragma unroll
-                for (int v = 0; v < N / 4; v++) dst[v] = __ldg(src + v);
-                sc[i] = __ldg(lpos + c0 + i);
-                swt[i] = __ldg(w_slot + c0 + i) * wa; // (w wa) kappa[b], the same rounding as before
+                for (int v = 0; v < N / 4; v++) {
+                    const float4 q = __ldg(src + v);
+                    dst[4 * v] = q.x;
+                    dst[4 * v + 1] = q.y;
+                    dst[4 * v + 2] = q.z;
+                    dst[4 * v + 3] = q.w;
+                }
+                // (w wa) kappa[b]: the same rounding as forming w wa first
+                scw[i] = make_float2(__int_as_float(__ldg(lpos + c0 + i)), __ldg(w_slot + c0 + i) * wa);
             }
             __syncwarp();
             const int q0 = max(s0, c0), q1 = min(s1, c0 + cn_);
             for (int q = q0; q < q1; q++) {
-                const int jj = q - c0, b = x - sc[jj];
-                const float wt = swt[jj] * sw[b];
-                kahan_add(num, cn, wt * sv[jj * N + b]);
+                const int jj = q - c0;
+                const float2 cw = scw[jj];
+                const int b = x - __float_as_int(cw.x);
+                const float wt = WIN ? cw.y * sw[b] : cw.y;
+                kahan_add(num, cn, wt * sv[jj * kRowS + b]);
                 kahan_add(den, cd, wt);
             }
             __syncwarp();
@@ -384,7 +394,10 @@ cudaError_t launch_aggregate_planar(const float *planes, const float *w_slot, in
     const int *off = (const int *)((const char *)agg_ws + L.off);
     const int *lpos = (const int *)((const char *)agg_ws + L.lpos);
     dim3 grid((W + 32 * kGatherWarps - 1) / (32 * kGatherWarps), H);
-    auto kern = N == 8 ? k_gather_planar<8> : k_gather_planar<16>;
+    bool flat = true; // every window factor 1 (stage 1): no per-contribution lookup
+    for (int i = 0; i < N; i++) flat = flat && window[i] == 1.f;
+    auto kern = N == 8 ? (flat ? k_gather_planar<8, false> : k_gather_planar<8, true>)
+                       : (flat ? k_gather_planar<16, false> : k_gather_planar<16, true>);
     const int smem = N == 8 ? GatherCfg<8>::kSmem : GatherCfg<16>::kSmem;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
