@@ -220,7 +220,8 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
 // of 16 x 32 coefficient positions and one slice pair.  SCATTER (level 1):
 // the voxel at spun position (z,y,x) belongs to mosaic position
 // (z,y,x) - shift, i.e. block r = z of group (y/N, x/N) at (y%N, x%N), with
-// N = 2^LN; it is written (or added) scaled through the GroupOut.
+// N = 2^LN; it is written (or added) scaled into out, which is group-major
+// (out.base[((g K + r) N + row) N + col]).
 template <bool SCATTER, int LN>
 __global__ void __launch_bounds__(256)
 k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restrict__ dst, GroupOut out, int Bx,
@@ -314,10 +315,13 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
             const int orow = (tid >> 6) + 4 * i, ys = 2 * y0 + orow;
             p0[i] = p1[i] = nullptr;
             if (ys < Yo) {
+                // the level-1 output is group-major ([group][block][row][col],
+                // strides N^2 and N: compile-time shifts)
                 const int y = pwrap(ys - shift, Yo);
                 const long long g = (long long)(y >> LN) * Bx + gx;
-                p0[i] = out.row(g * Zo + z0, y & ((1 << LN) - 1)) + bx;
-                p1[i] = out.row(g * Zo + z1, y & ((1 << LN) - 1)) + bx;
+                float *rowp = out.base + (g * Zo << (2 * LN)) + ((y & ((1 << LN) - 1)) << LN) + bx;
+                p0[i] = rowp + ((long long)z0 << (2 * LN));
+                p1[i] = rowp + ((long long)z1 << (2 * LN));
             }
             o0[i] = o1[i] = 0.f;
         }
@@ -492,7 +496,7 @@ cudaError_t launch_ht_transforms(const float *img, int H, int W, int pitch, cons
     // scratch that the TV pass permutes into the output's layout
     const bool permute = out.slot_of != nullptr;
     float *gm = permute ? (float *)(base + g.gm_off) : out.base;
-    const GroupOut gm_out = group_major(gm, nullptr, g.N);
+    const GroupOut gm_out = group_major(gm, nullptr, g.N); // the layout k_dwt_syn<true> assumes
     if (g.N == 8)
         launch_levels<3>(g, img, pitch, ofs, C, sigma, tau_a, tau_b, cycle_spins, gm_out, st);
     else
