@@ -7,14 +7,15 @@
 //   -> conv 32->1 = r;  pilot = Z - r;  loss = mean (pilot - Y1)^2
 // Weights W[l][tap][ci][co] (tap = 3 (dy+1) + (dx+1)), biases b[l][co], in
 // one flat FP32 master vector; every convolution uses the weights rounded
-// to BF16.  The six 32 -> 32 layers run on the tensor cores (mma.sync
-// m16n8k16, BF16 inputs, FP32 accumulation) as implicit GEMMs over 4 x 32
-// pixel tiles staged in shared memory; their backward-data pass is the same
-// kernel with the weights flipped and transposed, masked by the ReLU of the
-// layer below.  The thin first and last layers, the weight gradients
-// (per-CTA partial sums, then a fixed-order reduction: deterministic) and
-// Adam are SIMT.  Activations stay FP32 in memory; the 32 -> 32 layers
-// round their inputs to BF16 when staging them.
+// to BF16.  Activations x1 .. x7 are stored BF16 (NHWC, 64 bytes a pixel,
+// rounded to nearest-even by the layer that writes them); accumulation is
+// FP32 throughout.  The six forward 32 -> 32 layers run on the
+// 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory)
+// as implicit GEMMs over 128-pixel row tiles; their backward-data passes
+// run on mma.sync over 4 x 32 pixel tiles (weights flipped and transposed,
+// masked by the ReLU of the layer below).  The thin first and last layers,
+// the weight gradients (per-CTA partial sums, then a fixed-order reduction:
+// deterministic) and Adam are SIMT.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdarg.h>
@@ -36,6 +37,15 @@ constexpr int kOffW8 = kW1 + kC + kMid * (kWm + kC), kOffB8 = kOffW8 + kW8;
 constexpr int kParams = kOffB8 + 1; // 56385
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// four BF16 channels (8 bytes) as FP32
+__device__ __forceinline__ float4 ld_bf16x4(const __nv_bfloat16 *p)
+{
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 c = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, c.x, c.y);
+}
 
 // ---- weights: BF16 copies in the layouts the kernels read -------------------
 // wf[m][tap][co][ci] (forward, 32 -> 32), wb[m][tap][ci][co] = W[m][8 - tap][ci][co]
@@ -64,39 +74,56 @@ __global__ void k_input(const float *__restrict__ Z, int zpitch, long long zbatc
     x0[((size_t)b * H + y) * W + x] = make_float2(Z[b * zbatch + (long long)y * zpitch + x], sigma[b]);
 }
 
-// First layer, 2 -> 32, + ReLU: one thread per pixel, weights in shared memory.
-__global__ void __launch_bounds__(128) k_conv_first(const float2 *__restrict__ x0, const float *__restrict__ w1r,
-                                                    const float *__restrict__ theta, float *__restrict__ x1, int H,
-                                                    int W)
+// First layer, 2 -> 32, + ReLU, straight from Z and sigma: a CTA of 256
+// threads covers 16 pixels of kThinRows rows; it stages the two input
+// channels of its tile with the 1-pixel halo in shared memory (zero outside
+// the image, the zero padding of both channels), then sixteen lanes per pixel
+// compute two output channels each from the 36 weights they hold in
+// registers (the 64-byte BF16 output row of a pixel is one coalesced store).
+constexpr int kThinRows = 8;
+
+__global__ void __launch_bounds__(256) k_conv_first(const float *__restrict__ Z, int zpitch, long long zbatch,
+                                                    const float *__restrict__ sigma, const float *__restrict__ w1r,
+                                                    const float *__restrict__ theta, __nv_bfloat16 *__restrict__ x1,
+                                                    int H, int W)
 {
-    __shared__ float sw[kW1], sb[kC];
-    for (int i = threadIdx.x; i < kW1; i += blockDim.x) sw[i] = w1r[i];
-    if (threadIdx.x < kC) sb[threadIdx.x] = theta[kOffB1 + threadIdx.x];
-    __syncthreads();
-    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
-    if (x >= W) return;
-    float acc[kC];
-#pragma unroll
-    for (int co = 0; co < kC; co++) acc[co] = sb[co];
-#pragma unroll
-    for (int tap = 0; tap < 9; tap++) {
-        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-        float2 v = make_float2(0.f, 0.f);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = x0[((size_t)b * H + yy) * W + xx];
-#pragma unroll
-        for (int co = 0; co < kC; co++) acc[co] = fmaf(v.x, sw[(tap * 2 + 0) * kC + co], fmaf(v.y, sw[(tap * 2 + 1) * kC + co], acc[co]));
+    __shared__ float2 sx[kThinRows + 2][16 + 2];
+    const int b = blockIdx.z, xb = blockIdx.x * 16, yb = blockIdx.y * kThinRows;
+    const float sg = sigma[b];
+    for (int i = threadIdx.x; i < (kThinRows + 2) * 18; i += 256) {
+        const int r = i / 18, c = i - r * 18, yy = yb + r - 1, xx = xb + c - 1;
+        const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        sx[r][c] = inside ? make_float2(Z[b * zbatch + (long long)yy * zpitch + xx], sg) : make_float2(0.f, 0.f);
     }
-    float4 *o = reinterpret_cast<float4 *>(x1 + (((size_t)b * H + y) * W + x) * kC);
+    const int cp = threadIdx.x & 15, px = threadIdx.x >> 4; // output channels 2 cp, 2 cp + 1 of pixel px
+    float2 w[9][2];
 #pragma unroll
-    for (int q = 0; q < kC / 4; q++)
-        o[q] = make_float4(fmaxf(acc[4 * q], 0.f), fmaxf(acc[4 * q + 1], 0.f), fmaxf(acc[4 * q + 2], 0.f),
-                           fmaxf(acc[4 * q + 3], 0.f));
+    for (int tap = 0; tap < 9; tap++)
+#pragma unroll
+        for (int ci = 0; ci < 2; ci++) w[tap][ci] = reinterpret_cast<const float2 *>(w1r + (tap * 2 + ci) * kC)[cp];
+    const float2 bq = reinterpret_cast<const float2 *>(theta + kOffB1)[cp];
+    __syncthreads();
+    const int x = xb + px;
+    if (x >= W) return;
+    const int rows = min(kThinRows, H - yb);
+    for (int r = 0; r < rows; r++) {
+        float2 a = bq;
+#pragma unroll
+        for (int tap = 0; tap < 9; tap++) {
+            const float2 v = sx[r + tap / 3][px + tap % 3];
+            a.x = fmaf(v.x, w[tap][0].x, fmaf(v.y, w[tap][1].x, a.x));
+            a.y = fmaf(v.x, w[tap][0].y, fmaf(v.y, w[tap][1].y, a.y));
+        }
+        reinterpret_cast<__nv_bfloat162 *>(x1 + (((size_t)b * H + yb + r) * W + x) * kC)[cp] =
+            __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
+    }
 }
 
-// ---- 32 -> 32 convolution on the tensor cores ---------------------------------
-// out[p][n] = sum_tap sum_k in[p + off(tap)][k] V[tap][n][k], then
-//   forward:  + bias[n], ReLU;   backward data:  * (mask[p][n] > 0).
-// CTA: 4 warps, a tile of 4 rows x 32 pixels; warp w owns row w (two m-tiles
+// ---- backward data pass of a 32 -> 32 layer (mma.sync tensor cores) ----------
+// out[p][n] = (sum_tap sum_k in[p + off(tap)][k] V[tap][n][k]) * (mask[p][n] > 0),
+// in = the FP32 gradient at the layer's output, V the flipped, transposed
+// weights, mask the layer's BF16 input activation (the ReLU of the layer
+// below).  CTA: 4 warps, a tile of 4 rows x 32 pixels; warp w owns row w (two m-tiles
 // of 16 pixels) and all 32 outputs (four n-tiles of 8).  The input tile with
 // its 1-pixel halo (6 x 34 pixels x 32 channels) and V are staged in shared
 // memory as BF16 with 40-element rows (80 bytes: fragment loads are
@@ -132,10 +159,9 @@ __device__ __forceinline__ void conv_tile(const ConvTiles &T, int t, int &b, int
     x0 = (r - ty * T.tx) * kTX;
 }
 
-template <bool kFwd>
-__global__ void __launch_bounds__(128, 4) k_conv_mid(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ V,
-                                                     const float *__restrict__ bias, const float *__restrict__ mask,
-                                                     float *__restrict__ out, int H, int W, ConvTiles T)
+__global__ void __launch_bounds__(128, 4) k_conv_bwd(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ V,
+                                                     const __nv_bfloat16 *__restrict__ mask, float *__restrict__ out,
+                                                     int H, int W, ConvTiles T)
 {
     extern __shared__ __align__(16) __nv_bfloat16 cs[];
     __nv_bfloat16 *s_v = cs, *s_in0 = cs + 9 * kC * kRow;
@@ -233,14 +259,10 @@ __global__ void __launch_bounds__(128, 4) k_conv_mid(const float *__restrict__ i
                     for (int nt = 0; nt < 4; nt++) {
                         const int n = nt * 8 + 2 * t4;
                         float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                        if (kFwd) {
-                            v0 = fmaxf(v0 + bias[n], 0.f);
-                            v1 = fmaxf(v1 + bias[n + 1], 0.f);
-                        } else {
-                            const float2 mk = *reinterpret_cast<const float2 *>(mask + pp * kC + n);
-                            v0 = mk.x > 0.f ? v0 : 0.f;
-                            v1 = mk.y > 0.f ? v1 : 0.f;
-                        }
+                        const float2 mk =
+                            __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(mask + pp * kC + n));
+                        v0 = mk.x > 0.f ? v0 : 0.f;
+                        v1 = mk.y > 0.f ? v1 : 0.f;
                         *reinterpret_cast<float2 *>(out + pp * kC + n) = make_float2(v0, v1);
                     }
                 }
@@ -250,79 +272,330 @@ __global__ void __launch_bounds__(128, 4) k_conv_mid(const float *__restrict__ i
     }
 }
 
-// Last layer, 32 -> 1: r = b + sum W8 x7; pilot = Z - r.  With a target: the
-// loss gradient g8 = dL/dr = -2 (pilot - Y1) / n and per-CTA partial sums of
-// (pilot - Y1)^2 (rows of the grid, reduced later in a fixed order).
-__global__ void __launch_bounds__(128) k_conv_last(const float *__restrict__ x7, const float *__restrict__ w8r,
+// ---- the forward 32 -> 32 convolution on the 5th-generation tensor cores ------
+// tcgen05.mma kind::f16 (BF16 inputs, FP32 accumulators in tensor memory):
+// per tile of 128 pixels of one image row, M = 128 pixels, N = 32 output
+// channels, K = 16 input channels per instruction; 9 taps x 2 channel halves
+// = 18 instructions accumulate the whole 3 x 3 x 32 contraction.  Input rows
+// (BF16 NHWC in memory) are staged in shared memory as [channel group of
+// 8][pixel][8] BF16 (130 pixels with the halo): a tap's shifted 128-pixel
+// window is then a K-major operand without swizzle (16-byte core-matrix rows,
+// 8-pixel groups 128 bytes apart, channel groups 2080 bytes apart) that
+// starts at the tap's row and pixel.  The weights sit once per CTA in the
+// same layout ([tap][channel group][output channel][8]).
+// Each CTA walks a vertical run of tiles (one 128-pixel column strip, rows
+// y0 .. y1) with a ring of kCRing staged rows filled by cp.async 16-byte
+// copies kCRing - 3 rows ahead of the tensor cores (zero-filled outside the
+// image); per tile the epilogue (tcgen05.ld, bias, ReLU, BF16 store) drains
+// one of two 32-column accumulator buffers while the next tile's product
+// fills the other.  Every mbarrier wait is bounded; a wait that gives up
+// counts in g_conv_timeouts and ends the CTA's work.
+__device__ unsigned long long g_conv_timeouts = 0;
+
+constexpr int kCT = 128;                        // pixels per tile (one row segment)
+constexpr int kCPix = kCT + 2;                  // staged pixels per row
+constexpr int kCGrp = kC / 8;                   // channel groups of 8
+constexpr int kCRowBytes = kCGrp * kCPix * 16;  // one staged row (4 groups x 130 pixels x 16 bytes)
+constexpr int kCRing = 6;                       // staged rows: 3 in use, kCRing - 3 in flight
+constexpr int kCWBytes = 9 * kCGrp * kC * 16;   // the weights
+constexpr int kCTcSmem = kCRing * kCRowBytes + kCWBytes + 64;
+constexpr int kCTcPerSm = 3;                    // CTAs per SM (shared memory: 3 x 68.5 KB)
+constexpr uint32_t kConvIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
+                                ((uint32_t)(kCT >> 4) << 24); // D FP32, A/B BF16, K-major, N 32, M 128
+constexpr int kCSpin = 1 << 22;
+static_assert(kCRing >= 4, "the ring holds the three rows of a product and at least one in flight");
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t cdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool cbar_wait(uint32_t a, uint32_t parity)
+{
+    for (int i = 0; i < kCSpin; i++) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Runs: (image b, strip sx, rows y0 .. y0 + run_len - 1); run j of the batch:
+// b = j / (strips * runs_col), then strip, then run within the strip's column.
+struct ConvRuns {
+    int strips, runs_col, run_len, total;
+};
+
+__global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
+                                                            const __nv_bfloat16 *__restrict__ V,
+                                                            const float *__restrict__ bias,
+                                                            __nv_bfloat16 *__restrict__ out, int B, int H, int W,
+                                                            ConvRuns RN)
+{
+    extern __shared__ __align__(1024) unsigned char ctsm[];
+    unsigned char *s_ring = ctsm, *s_w = ctsm + kCRing * kCRowBytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(s_w + kCWBytes);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + 2);
+    volatile int *s_err = reinterpret_cast<volatile int *>(mbar + 3);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)), "r"(64)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mbar + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_err = 0;
+    }
+    // weights: V[tap][co][ci] -> [tap][ci group][co][8]
+    for (int i = tid; i < 9 * kC * kCGrp; i += 128) {
+        const int g = i & 3, co = (i >> 2) & (kC - 1), tap = i >> 7;
+        *reinterpret_cast<uint4 *>(s_w + ((tap * kCGrp + g) * kC + co) * 16) =
+            *reinterpret_cast<const uint4 *>(V + (tap * kC + co) * kC + g * 8);
+    }
+    float bv[kC];
+#pragma unroll
+    for (int c = 0; c < kC; c++) bv[c] = bias[c];
+    // cp.async of image row yy (zero outside the image) of strip x0 into ring
+    // slot yy mod kCRing, then one commit group (empty when yy is past the run)
+    auto load_row = [&](int b, int yy, int x0, bool needed) {
+        if (needed) {
+            const uint32_t dst = su32(s_ring + ((yy + kCRing) % kCRing) * kCRowBytes);
+            for (int i = tid; i < kCPix * kCGrp; i += 128) {
+                const int g = i & 3, p = i >> 2, xx = x0 + p - 1;
+                const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
+                const __nv_bfloat16 *src = inside ? in + (((size_t)b * H + yy) * W + xx) * kC + g * 8 : in;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + (uint32_t)(g * kCPix + p) * 16),
+                             "l"(src), "r"(inside ? 16 : 0)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // the product of output row y (rows y-1 .. y+1 staged) into accumulator buf (thread 0)
+    auto issue = [&](int y, int buf) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = *s_tmem + (uint32_t)(buf * kC);
+        const uint32_t rb = su32(s_ring), wb = su32(s_w);
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            const int dy = tap / 3, dx = tap % 3; // row y + dy - 1, pixel offset dx
+            const uint32_t row = rb + ((y + dy - 1 + kCRing) % kCRing) * kCRowBytes;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint64_t ad = cdesc(row + 2 * h * kCPix * 16 + dx * 16, kCPix * 16, 128);
+                const uint64_t bd = cdesc(wb + ((tap * kCGrp + 2 * h) * kC) * 16, kC * 16, 128);
+                const uint32_t acc = (tap | h) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                             "l"(ad), "l"(bd), "r"(kConvIdesc), "r"(acc)
+                             : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(mbar + buf))
+                     : "memory");
+    };
+    int issued = 0; // products issued by this CTA (thread 0's count; buffer = count & 1)
+    int done = 0;   // products waited for
+    for (int run = blockIdx.x; run < RN.total && !*s_err; run += gridDim.x) {
+        const int b = run / (RN.strips * RN.runs_col), rem = run - b * RN.strips * RN.runs_col;
+        const int sx = rem / RN.runs_col, ry = rem - sx * RN.runs_col;
+        const int x0 = sx * kCT, y0 = ry * RN.run_len, y1 = min(H, y0 + RN.run_len);
+        // input rows y0 - 1 .. y1 are needed; rows y0 - 1 .. y0 + kCRing - 3 go in flight now
+        for (int k = 0; k < kCRing - 1; k++) load_row(b, y0 - 1 + k, x0, y0 - 1 + k <= y1);
+        // the first product's three rows have landed when at most kCRing - 4 groups are pending
+        asm volatile("cp.async.wait_group %0;" ::"n"(kCRing - 4) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) issue(y0, issued & 1);
+        issued++;
+        for (int y = y0; y < y1; y++) {
+            const int buf = done & 1;
+            // row y + kCRing - 2 into the slot of row y - 2, whose last product (y - 1) has completed
+            load_row(b, y + kCRing - 2, x0, y + kCRing - 2 <= y1);
+            // row y + 2 (the next product's last) has landed: rows y + 3 .. y + kCRing - 2
+            // (kCRing - 4 groups) may still be in flight
+            asm volatile("cp.async.wait_group %0;" ::"n"(kCRing - 4) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const bool ok = cbar_wait(su32(mbar + buf), (done >> 1) & 1);
+            done++;
+            if (!ok && lane == 0) {
+                *s_err = 1;
+                atomicAdd(&g_conv_timeouts, 1ull);
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (*s_err) break;
+            if (y + 1 < y1) {
+                if (tid == 0) issue(y + 1, issued & 1);
+                issued++;
+            }
+            uint32_t v[32];
+            const uint32_t taddr = *s_tmem + (uint32_t)(buf * kC) + ((uint32_t)(warp * 32) << 16);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+                         "tcgen05.wait::ld.sync.aligned;"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                         : "r"(taddr)
+                         : "memory");
+            const int x = x0 + warp * 32 + lane;
+            if (x < W) {
+                uint4 *o = reinterpret_cast<uint4 *>(out + (((size_t)b * H + y) * W + x) * kC);
+#pragma unroll
+                for (int q = 0; q < kC / 8; q++) {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int c = 8 * q + 2 * j;
+                        __nv_bfloat162 t = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[c]) + bv[c], 0.f),
+                                                                 fmaxf(__uint_as_float(v[c + 1]) + bv[c + 1], 0.f));
+                        h[j] = *reinterpret_cast<uint32_t *>(&t);
+                    }
+                    o[q] = make_uint4(h[0], h[1], h[2], h[3]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        // the ring is restaged by the next run: no copy may still be landing
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // after a timeout a product may still run: let it finish before its
+    // accumulators are released
+    if (tid == 0 && *s_err && issued > done) cbar_wait(su32(mbar + ((issued - 1) & 1)), ((issued - 1) >> 1) & 1);
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tmem), "r"(64) : "memory");
+}
+
+// Last layer, 32 -> 1: r = b + sum W8 x7; pilot = Z - r.  A CTA of 256
+// threads covers kLX pixels of kThinRows rows: it stages its x7 tile with
+// the 1-pixel halo in shared memory (cp.async 16-byte copies, zero outside
+// the image), then eight lanes per pixel each take four channels of every
+// tap against the 36 weights they hold in registers, and a shuffle sums the
+// eight.  With a target: the loss gradient g8 = dL/dr = -2 (pilot - Y1) / n
+// and one partial sum of (pilot - Y1)^2 / n per kLX-pixel row segment
+// (reduced later in a fixed order).
+constexpr int kLX = 32;
+constexpr int kLTile = (kThinRows + 2) * (kLX + 2) * kC * 2; // bytes of the staged x7 tile
+
+__global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16 *__restrict__ x7, const float *__restrict__ w8r,
                                                    const float *__restrict__ theta, const float *__restrict__ Z,
                                                    int zpitch, long long zbatch, const float *__restrict__ Y1,
                                                    float *__restrict__ pilot, int ppitch, long long pbatch,
                                                    float *__restrict__ g8, float *__restrict__ loss_part, float inv_n,
                                                    int H, int W)
 {
-    __shared__ float sw[kW8];
-    __shared__ float red[4];
-    for (int i = threadIdx.x; i < kW8; i += blockDim.x) sw[i] = w8r[i];
-    __syncthreads();
-    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
-    float e2 = 0.f;
-    if (x < W) {
-        float r = theta[kOffB8];
-        for (int tap = 0; tap < 9; tap++) {
-            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-            const float4 *v = reinterpret_cast<const float4 *>(x7 + (((size_t)b * H + yy) * W + xx) * kC);
+    __shared__ __align__(16) unsigned char st[kLTile];
+    __shared__ float red[kThinRows][8];
+    const int tid = threadIdx.x, b = blockIdx.z, xb = blockIdx.x * kLX, yb = blockIdx.y * kThinRows;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(st);
+    for (int i = tid; i < (kThinRows + 2) * (kLX + 2) * 4; i += 256) {
+        const int q = i & 3, pr = i >> 2, r = pr / (kLX + 2), c = pr - r * (kLX + 2);
+        const int yy = yb + r - 1, xx = xb + c - 1;
+        const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        const __nv_bfloat16 *src = inside ? x7 + (((size_t)b * H + yy) * W + xx) * kC + q * 8 : x7;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sbase + (uint32_t)i * 16), "l"(src),
+                     "r"(inside ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int cq = tid & 7, px = tid >> 3; // channels 4 cq .. 4 cq + 3 of pixel px
+    float4 w[9];
 #pragma unroll
-            for (int q = 0; q < kC / 4; q++) {
-                const float4 u = v[q];
-                const float *wq = sw + tap * kC + 4 * q;
-                r = fmaf(u.x, wq[0], fmaf(u.y, wq[1], fmaf(u.z, wq[2], fmaf(u.w, wq[3], r))));
+    for (int tap = 0; tap < 9; tap++) w[tap] = reinterpret_cast<const float4 *>(w8r + tap * kC)[cq];
+    const float b8 = theta[kOffB8];
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int x = xb + px, rows = min(kThinRows, H - yb);
+    for (int r = 0; r < rows; r++) {
+        float part = 0.f;
+#pragma unroll
+        for (int tap = 0; tap < 9; tap++) {
+            const float4 u = ld_bf16x4(reinterpret_cast<const __nv_bfloat16 *>(
+                                           st + ((r + tap / 3) * (kLX + 2) + px + tap % 3) * kC * 2) +
+                                       4 * cq);
+            part = fmaf(u.x, w[tap].x, fmaf(u.y, w[tap].y, fmaf(u.z, w[tap].z, fmaf(u.w, w[tap].w, part))));
+        }
+        // sum over the pixel's eight lanes (fixed order)
+        part += __shfl_xor_sync(0xffffffffu, part, 4);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        const int y = yb + r;
+        float e2 = 0.f;
+        if (x < W && cq == 0) {
+            const float pv = Z[b * zbatch + (long long)y * zpitch + x] - (b8 + part);
+            if (pilot) pilot[b * pbatch + (long long)y * ppitch + x] = pv;
+            if (Y1) {
+                const float d = pv - Y1[((size_t)b * H + y) * W + x];
+                g8[((size_t)b * H + y) * W + x] = -2.f * d * inv_n;
+                e2 = d * d * inv_n; // partial sums of the mean
             }
         }
-        const float pv = Z[b * zbatch + (long long)y * zpitch + x] - r;
-        if (pilot) pilot[b * pbatch + (long long)y * ppitch + x] = pv;
         if (Y1) {
-            const float d = pv - Y1[((size_t)b * H + y) * W + x];
-            g8[((size_t)b * H + y) * W + x] = -2.f * d * inv_n;
-            e2 = d * d * inv_n; // partial sums of the mean
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+            if ((tid & 31) == 0) red[r][tid >> 5] = e2;
         }
     }
     if (!Y1) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
     __syncthreads();
-    if (threadIdx.x == 0)
-        loss_part[((size_t)b * H + y) * gridDim.x + blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+    if (tid < rows) {
+        const float *q = red[tid];
+        loss_part[((size_t)b * H + yb + tid) * gridDim.x + blockIdx.x] =
+            ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
+    }
 }
 
-// Backward of the last layer: g7[p][ci] = (sum_tap g8[p - off(tap)] W8[tap][ci]) * (x7[p][ci] > 0).
+// Backward of the last layer: g7[p][ci] = (sum_tap g8[p - off(tap)] W8[tap][ci]) * (x7[p][ci] > 0);
+// eight lanes per pixel, four channels each (coalesced rows), 16 pixels of
+// kThinRows rows per CTA.
 __global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, const float *__restrict__ w8r,
-                                                  const float *__restrict__ x7, float *__restrict__ g7, int H, int W)
+                                                  const __nv_bfloat16 *__restrict__ x7, float *__restrict__ g7, int H,
+                                                  int W)
 {
-    __shared__ float sw[kW8];
-    for (int i = threadIdx.x; i < kW8; i += blockDim.x) sw[i] = w8r[i];
-    __syncthreads();
-    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
+    const int cq = threadIdx.x & 7;
+    const int x = blockIdx.x * 16 + (threadIdx.x >> 3), b = blockIdx.z;
     if (x >= W) return;
-    float acc[kC];
+    float4 w[9];
 #pragma unroll
-    for (int c = 0; c < kC; c++) acc[c] = 0.f;
-    for (int tap = 0; tap < 9; tap++) {
-        const int yy = y - (tap / 3 - 1), xx = x - (tap % 3 - 1);
-        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-        const float gv = g8[((size_t)b * H + yy) * W + xx];
+    for (int tap = 0; tap < 9; tap++) w[tap] = reinterpret_cast<const float4 *>(w8r + tap * kC)[cq];
+    const int y1 = min(H, (blockIdx.y + 1) * kThinRows);
+    for (int y = blockIdx.y * kThinRows; y < y1; y++) {
+        float gv[9];
 #pragma unroll
-        for (int c = 0; c < kC; c++) acc[c] = fmaf(gv, sw[tap * kC + c], acc[c]);
-    }
-    const size_t p = ((size_t)b * H + y) * W + x;
-    const float4 *m = reinterpret_cast<const float4 *>(x7 + p * kC);
-    float4 *o = reinterpret_cast<float4 *>(g7 + p * kC);
+        for (int tap = 0; tap < 9; tap++) {
+            const int yy = y - (tap / 3 - 1), xx = x - (tap % 3 - 1);
+            gv[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? g8[((size_t)b * H + yy) * W + xx] : 0.f;
+        }
+        const size_t p = ((size_t)b * H + y) * W + x;
+        const float4 mk = ld_bf16x4(x7 + p * kC + 4 * cq);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < kC / 4; q++) {
-        const float4 mk = m[q];
-        o[q] = make_float4(mk.x > 0.f ? acc[4 * q] : 0.f, mk.y > 0.f ? acc[4 * q + 1] : 0.f,
-                           mk.z > 0.f ? acc[4 * q + 2] : 0.f, mk.w > 0.f ? acc[4 * q + 3] : 0.f);
+        for (int tap = 0; tap < 9; tap++) {
+            acc[0] = fmaf(gv[tap], w[tap].x, acc[0]);
+            acc[1] = fmaf(gv[tap], w[tap].y, acc[1]);
+            acc[2] = fmaf(gv[tap], w[tap].z, acc[2]);
+            acc[3] = fmaf(gv[tap], w[tap].w, acc[3]);
+        }
+        reinterpret_cast<float4 *>(g7 + p * kC)[cq] =
+            make_float4(mk.x > 0.f ? acc[0] : 0.f, mk.y > 0.f ? acc[1] : 0.f, mk.z > 0.f ? acc[2] : 0.f,
+                        mk.w > 0.f ? acc[3] : 0.f);
     }
 }
 
@@ -334,8 +607,11 @@ __global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, 
 // k_reduce adds the CTAs' partials in a fixed order.
 constexpr int kGX = 64;
 
-template <int CI, int CO>
-__global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const float *__restrict__ x, const float *__restrict__ g, int B,
+__device__ __forceinline__ float ldf(const float *p) { return *p; }
+__device__ __forceinline__ float ldf(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+template <int CI, int CO, typename TX>
+__global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, const float *__restrict__ g, int B,
                                                       int H, int W, float *__restrict__ part)
 {
     __shared__ float sx[3][kGX + 2][CI];
@@ -355,7 +631,7 @@ __global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const float *__restrict__ 
         for (int i = tid; i < 3 * (kGX + 2) * CI; i += nthr) {
             const int r = i / ((kGX + 2) * CI), rem = i - r * (kGX + 2) * CI, c = rem / CI, ch = rem - c * CI;
             const int yy = y + r - 1, xx = xb + c - 1;
-            sx[r][c][ch] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[(((size_t)b * H + yy) * W + xx) * CI + ch] : 0.f;
+            sx[r][c][ch] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? ldf(x + (((size_t)b * H + yy) * W + xx) * CI + ch) : 0.f;
         }
         for (int i = tid; i < kGX * CO; i += nthr) {
             const int c = i / CO, co = i - c * CO, xx = xb + c;
@@ -386,6 +662,22 @@ __global__ void k_reduce(const float *__restrict__ src, int nparts, int len, flo
     float s = 0.f;
     for (int c = 0; c < nparts; c++) s += src[(size_t)c * len + i];
     dst[i] = s;
+}
+
+// Sum of n values in a fixed order by one CTA of 1024 threads: strided
+// per-thread sums, then a fixed shared-memory tree (deterministic).
+__global__ void __launch_bounds__(1024) k_sum(const float *__restrict__ src, int n, float *__restrict__ dst)
+{
+    __shared__ float red[1024];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += 1024) s += src[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *dst = red[0];
 }
 
 // Adam on the flat parameter vector (step t >= 1, bias-corrected).
@@ -421,7 +713,7 @@ PilotLayout pilot_layout(int B, int H, int W, bool train)
     PilotLayout L{};
     const size_t P = (size_t)B * H * W;
     L.plane = P;
-    L.lparts = B * H * ((W + 127) / 128);
+    L.lparts = B * H * ((W + kLX - 1) / kLX);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
@@ -432,9 +724,9 @@ PilotLayout pilot_layout(int B, int H, int W, bool train)
     L.wb = take((size_t)kMid * kWm * 2);
     L.w1r = take(kW1 * 4);
     L.w8r = take(kW8 * 4);
-    L.x0 = take(P * 2 * 4);
+    L.x0 = train ? take(P * 2 * 4) : 0; // (Z, sigma) for the first layer's weight gradient
     // activations x1..x7 when training (kept for the backward pass), else two ping-pong buffers
-    L.act = take(P * kC * 4 * (train ? 7 : 2));
+    L.act = take(P * kC * 2 * (train ? 7 : 2)); // BF16
     if (train) {
         L.g8 = take(P * 4);
         L.ga = take(P * kC * 4);
@@ -468,11 +760,35 @@ int conv_ctas(const ConvTiles &T)
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             nsm = 148;
-        cudaFuncSetAttribute(k_conv_mid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
-        cudaFuncSetAttribute(k_conv_mid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+        cudaFuncSetAttribute(k_conv_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
         per_dev = 4 * nsm;
     }
     return T.total < per_dev ? T.total : per_dev;
+}
+
+// Grid of the tensor-core forward convolution: runs of rows of each 128-pixel
+// strip, sized so that the runs fill kCTcPerSm CTAs per SM (shared memory)
+// once, and one CTA per run.
+int conv_tc_ctas(int B, int H, int W, ConvRuns &RN)
+{
+    static int per_dev = 0;
+    if (!per_dev) {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 148;
+        cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kCTcSmem);
+        per_dev = kCTcPerSm * nsm;
+    }
+    RN.strips = (W + kCT - 1) / kCT;
+    const long long cols = (long long)B * RN.strips; // strips in the batch
+    // rows per run: the strips' rows spread over about per_dev runs (at least 4 rows)
+    long long len = (cols * H + per_dev - 1) / per_dev;
+    if (len < 4) len = 4;
+    if (len > H) len = H;
+    RN.run_len = (int)len;
+    RN.runs_col = (H + RN.run_len - 1) / RN.run_len;
+    RN.total = (int)(cols * RN.runs_col);
+    return RN.total < per_dev ? RN.total : per_dev;
 }
 
 int wgrad_ctas()
@@ -495,23 +811,24 @@ cudaError_t pilot_forward(const float *Z, int B, int H, int W, int zpitch, long 
     __nv_bfloat16 *wf = (__nv_bfloat16 *)(ws + L.wf), *wb = (__nv_bfloat16 *)(ws + L.wb);
     float *w1r = (float *)(ws + L.w1r), *w8r = (float *)(ws + L.w8r);
     k_pack<<<(kMid * kWm + 255) / 256, 256, 0, st>>>(theta, wf, wb, w1r, w8r);
-    float2 *x0 = (float2 *)(ws + L.x0);
-    k_input<<<dim3((W + 31) / 32, (H + 7) / 8, B), 256, 0, st>>>(Z, zpitch, zbatch, sigma, x0, H, W);
-    float *act = (float *)(ws + L.act);
+    if (train) // x0 = (Z, sigma) for the first layer's weight gradient
+        k_input<<<dim3((W + 31) / 32, (H + 7) / 8, B), 256, 0, st>>>(Z, zpitch, zbatch, sigma, (float2 *)(ws + L.x0),
+                                                                    H, W);
+    __nv_bfloat16 *act = (__nv_bfloat16 *)(ws + L.act);
     auto X = [&](int l) { // x_l, l = 1..7
         return act + (size_t)(train ? l - 1 : (l - 1) & 1) * L.plane * kC;
     };
-    const dim3 g128((W + 127) / 128, H, B);
-    const ConvTiles T = conv_tiles(B, H, W);
-    const int gm = conv_ctas(T);
-    k_conv_first<<<g128, 128, 0, st>>>(x0, w1r, theta, X(1), H, W);
+    k_conv_first<<<dim3((W + 15) / 16, (H + kThinRows - 1) / kThinRows, B), 256, 0, st>>>(
+        Z, zpitch, zbatch, sigma, w1r, theta, X(1), H, W);
+    ConvRuns RN;
+    const int gtc = conv_tc_ctas(B, H, W, RN);
     for (int m = 0; m < kMid; m++)
-        k_conv_mid<true><<<gm, 128, kConvSmem, st>>>(X(m + 1), wf + (size_t)m * kWm, theta + off_bm(m), nullptr,
-                                                     X(m + 2), H, W, T);
+        k_conv_tc<<<gtc, 128, kCTcSmem, st>>>(X(m + 1), wf + (size_t)m * kWm, theta + off_bm(m), X(m + 2), B, H, W,
+                                             RN);
     const float inv_n = 1.f / (float)L.plane;
-    k_conv_last<<<g128, 128, 0, st>>>(X(7), w8r, theta, Z, zpitch, zbatch, Y1, pilot, ppitch, pbatch,
-                                      train ? (float *)(ws + L.g8) : nullptr,
-                                      train ? (float *)(ws + L.lpart) : nullptr, inv_n, H, W);
+    k_conv_last<<<dim3((W + kLX - 1) / kLX, (H + kThinRows - 1) / kThinRows, B), 256, 0, st>>>(
+        X(7), w8r, theta, Z, zpitch, zbatch, Y1, pilot, ppitch, pbatch, train ? (float *)(ws + L.g8) : nullptr,
+        train ? (float *)(ws + L.lpart) : nullptr, inv_n, H, W);
     return cudaGetLastError();
 }
 
@@ -519,32 +836,33 @@ cudaError_t pilot_forward(const float *Z, int B, int H, int W, int zpitch, long 
 // loss into ws loss.
 cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, cudaStream_t st)
 {
-    float *act = (float *)(ws + L.act), *grad = (float *)(ws + L.grad), *part = (float *)(ws + L.part);
+    const __nv_bfloat16 *act = (const __nv_bfloat16 *)(ws + L.act);
+    float *grad = (float *)(ws + L.grad), *part = (float *)(ws + L.part);
     auto X = [&](int l) { return act + (size_t)(l - 1) * L.plane * kC; };
     const __nv_bfloat16 *wb = (const __nv_bfloat16 *)(ws + L.wb);
     const float *w8r = (const float *)(ws + L.w8r);
     float *g8 = (float *)(ws + L.g8), *ga = (float *)(ws + L.ga), *gb = (float *)(ws + L.gb);
     const int nc = wgrad_ctas();
     // loss = sum of the scaled partials (their rows hold (pilot - Y1)^2 / n)
-    k_reduce<<<1, 32, 0, st>>>((const float *)(ws + L.lpart), L.lparts, 1, (float *)(ws + L.loss));
+    k_sum<<<1, 1024, 0, st>>>((const float *)(ws + L.lpart), L.lparts, (float *)(ws + L.loss));
     // last layer
-    k_wgrad<32, 1><<<nc, 9 * 32 + 1, 0, st>>>(X(7), g8, B, H, W, part);
+    k_wgrad<32, 1, __nv_bfloat16><<<nc, 9 * 32 + 1, 0, st>>>(X(7), g8, B, H, W, part);
     k_reduce<<<(kW8 + 1 + 255) / 256, 256, 0, st>>>(part, nc, kW8 + 1, grad + kOffW8);
-    const dim3 g128((W + 127) / 128, H, B);
+    const dim3 g128((W + 15) / 16, (H + kThinRows - 1) / kThinRows, B); // 16 x kThinRows pixels per CTA
     const ConvTiles T = conv_tiles(B, H, W);
     const int gm = conv_ctas(T);
     k_last_bwd<<<g128, 128, 0, st>>>(g8, w8r, X(7), ga, H, W);
     float *gcur = ga, *gnext = gb;
     for (int m = kMid - 1; m >= 0; m--) { // layer m + 2: x_{m+1} -> x_{m+2}; gcur = dL/dpre_{m+2}
-        k_wgrad<32, 32><<<nc, 9 * 32 + 1, 0, st>>>(X(m + 1), gcur, B, H, W, part);
+        k_wgrad<32, 32, __nv_bfloat16><<<nc, 9 * 32 + 1, 0, st>>>(X(m + 1), gcur, B, H, W, part);
         k_reduce<<<(kWm + kC + 255) / 256, 256, 0, st>>>(part, nc, kWm + kC, grad + off_wm(m));
-        k_conv_mid<false><<<gm, 128, kConvSmem, st>>>(gcur, wb + (size_t)m * kWm, nullptr, X(m + 1), gnext, H, W, T);
+        k_conv_bwd<<<gm, 128, kConvSmem, st>>>(gcur, wb + (size_t)m * kWm, X(m + 1), gnext, H, W, T);
         float *t = gcur;
         gcur = gnext;
         gnext = t;
     }
     // first layer (gcur = dL/dpre_1)
-    k_wgrad<2, 32><<<nc, 9 * 2 + 1, 0, st>>>((const float *)(ws + L.x0), gcur, B, H, W, part);
+    k_wgrad<2, 32, float><<<nc, 9 * 2 + 1, 0, st>>>((const float *)(ws + L.x0), gcur, B, H, W, part);
     k_reduce<<<(kW1 + kC + 255) / 256, 256, 0, st>>>(part, nc, kW1 + kC, grad + kOffW1);
     return cudaGetLastError();
 }
