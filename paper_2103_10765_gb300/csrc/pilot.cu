@@ -284,11 +284,14 @@ __global__ void __launch_bounds__(128, 4) k_conv_bwd(const float *__restrict__ i
 // starts at the tap's row and pixel.  The weights sit once per CTA in the
 // same layout ([tap][channel group][output channel][8]).
 // Each CTA walks a vertical run of tiles (one 128-pixel column strip, rows
-// y0 .. y1) with a ring of kCRing staged rows filled by cp.async 16-byte
-// copies kCRing - 3 rows ahead of the tensor cores (zero-filled outside the
-// image); per tile the epilogue (tcgen05.ld, bias, ReLU, BF16 store) drains
-// one of two 32-column accumulator buffers while the next tile's product
-// fills the other.  Every mbarrier wait is bounded; a wait that gives up
+// y0 .. y1) with a ring of 4 staged rows.  A run's first three rows arrive
+// by cp.async; after that, each tile's step stores the row fetched into
+// registers during the previous step (coalesced 16-byte loads; a cp.async
+// here would scatter the two halves of every 32-byte sector to different
+// channel groups, doubling the L2 traffic and the shared-memory wavefronts)
+// and fetches the next.  Per tile the epilogue (tcgen05.ld, bias, ReLU, BF16
+// store) drains one of two 32-column accumulator buffers while the next
+// tile's product fills the other.  Every mbarrier wait is bounded; a wait that gives up
 // counts in g_conv_timeouts and ends the CTA's work.
 __device__ unsigned long long g_conv_timeouts = 0;
 
@@ -296,14 +299,15 @@ constexpr int kCT = 128;                        // pixels per tile (one row segm
 constexpr int kCPix = kCT + 2;                  // staged pixels per row
 constexpr int kCGrp = kC / 8;                   // channel groups of 8
 constexpr int kCRowBytes = kCGrp * kCPix * 16;  // one staged row (4 groups x 130 pixels x 16 bytes)
-constexpr int kCRing = 6;                       // staged rows: 3 in use, kCRing - 3 in flight
+constexpr int kCRing = 4;                       // staged rows: 3 in use, 1 being stored
 constexpr int kCWBytes = 9 * kCGrp * kC * 16;   // the weights
 constexpr int kCTcSmem = kCRing * kCRowBytes + kCWBytes + 64;
-constexpr int kCTcPerSm = 3;                    // CTAs per SM (shared memory: 3 x 68.5 KB)
+constexpr int kCTcPerSm = 4;                    // CTAs per SM (shared memory: 4 x 51.8 KB)
+constexpr int kCLd = (kCPix * kCGrp + 127) / 128; // 16-byte chunks of a row per thread (5)
 constexpr uint32_t kConvIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
                                 ((uint32_t)(kCT >> 4) << 24); // D FP32, A/B BF16, K-major, N 32, M 128
 constexpr int kCSpin = 1 << 22;
-static_assert(kCRing >= 4, "the ring holds the three rows of a product and at least one in flight");
+static_assert(kCRing == 4, "ring slots are row & 3");
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -364,21 +368,43 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
     float bv[kC];
 #pragma unroll
     for (int c = 0; c < kC; c++) bv[c] = bias[c];
-    // cp.async of image row yy (zero outside the image) of strip x0 into ring
-    // slot yy mod kCRing, then one commit group (empty when yy is past the run)
-    auto load_row = [&](int b, int yy, int x0, bool needed) {
-        if (needed) {
-            const uint32_t dst = su32(s_ring + ((yy + kCRing) % kCRing) * kCRowBytes);
-            for (int i = tid; i < kCPix * kCGrp; i += 128) {
-                const int g = i & 3, p = i >> 2, xx = x0 + p - 1;
-                const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
-                const __nv_bfloat16 *src = inside ? in + (((size_t)b * H + yy) * W + xx) * kC + g * 8 : in;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + (uint32_t)(g * kCPix + p) * 16),
-                             "l"(src), "r"(inside ? 16 : 0)
-                             : "memory");
-            }
+    // chunk i of a staged row: channel group i & 3 of pixel i >> 2 (x0 - 1 + i >> 2)
+    auto src_of = [&](int b, int yy, int x0, int i, bool &inside) {
+        const int xx = x0 + (i >> 2) - 1;
+        inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        return inside ? in + (((size_t)b * H + yy) * W + xx) * kC + (i & 3) * 8 : in;
+    };
+    auto dst_of = [&](int yy, int i) { // [group][pixel][16 bytes] in ring slot yy & 3
+        return s_ring + (yy & (kCRing - 1)) * kCRowBytes + ((i & 3) * kCPix + (i >> 2)) * 16;
+    };
+    // a run's first rows: cp.async (zero-filled outside the image)
+    auto copy_row = [&](int b, int yy, int x0) {
+        for (int i = tid; i < kCPix * kCGrp; i += 128) {
+            bool inside;
+            const __nv_bfloat16 *src = src_of(b, yy, x0, i, inside);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst_of(yy, i))), "l"(src),
+                         "r"(inside ? 16 : 0)
+                         : "memory");
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // later rows: fetched into registers one step ahead, then stored
+    uint4 pre[kCLd];
+    auto fetch_row = [&](int b, int yy, int x0) {
+#pragma unroll
+        for (int j = 0; j < kCLd; j++) {
+            const int i = tid + 128 * j;
+            pre[j] = make_uint4(0, 0, 0, 0);
+            bool inside = false;
+            const __nv_bfloat16 *src = i < kCPix * kCGrp ? src_of(b, yy, x0, i, inside) : in;
+            if (inside) pre[j] = __ldg(reinterpret_cast<const uint4 *>(src));
+        }
+    };
+    auto put_row = [&](int yy) {
+#pragma unroll
+        for (int j = 0; j < kCLd; j++) {
+            const int i = tid + 128 * j;
+            if (i < kCPix * kCGrp) *reinterpret_cast<uint4 *>(dst_of(yy, i)) = pre[j];
+        }
     };
     // the product of output row y (rows y-1 .. y+1 staged) into accumulator buf (thread 0)
     auto issue = [&](int y, int buf) {
@@ -388,7 +414,7 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
 #pragma unroll 1
         for (int tap = 0; tap < 9; tap++) {
             const int dy = tap / 3, dx = tap % 3; // row y + dy - 1, pixel offset dx
-            const uint32_t row = rb + ((y + dy - 1 + kCRing) % kCRing) * kCRowBytes;
+            const uint32_t row = rb + ((y + dy - 1) & (kCRing - 1)) * kCRowBytes;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const uint64_t ad = cdesc(row + 2 * h * kCPix * 16 + dx * 16, kCPix * 16, 128);
@@ -410,21 +436,25 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
         const int b = run / (RN.strips * RN.runs_col), rem = run - b * RN.strips * RN.runs_col;
         const int sx = rem / RN.runs_col, ry = rem - sx * RN.runs_col;
         const int x0 = sx * kCT, y0 = ry * RN.run_len, y1 = min(H, y0 + RN.run_len);
-        // input rows y0 - 1 .. y1 are needed; rows y0 - 1 .. y0 + kCRing - 3 go in flight now
-        for (int k = 0; k < kCRing - 1; k++) load_row(b, y0 - 1 + k, x0, y0 - 1 + k <= y1);
-        // the first product's three rows have landed when at most kCRing - 4 groups are pending
-        asm volatile("cp.async.wait_group %0;" ::"n"(kCRing - 4) : "memory");
+        // input rows y0 - 1 .. y1 are needed: the first three by cp.async, row y0 + 2 into registers
+        copy_row(b, y0 - 1, x0);
+        copy_row(b, y0, x0);
+        copy_row(b, y0 + 1, x0);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (y0 + 2 <= y1) fetch_row(b, y0 + 2, x0);
+        asm volatile("cp.async.wait_all;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) issue(y0, issued & 1);
         issued++;
         for (int y = y0; y < y1; y++) {
             const int buf = done & 1;
-            // row y + kCRing - 2 into the slot of row y - 2, whose last product (y - 1) has completed
-            load_row(b, y + kCRing - 2, x0, y + kCRing - 2 <= y1);
-            // row y + 2 (the next product's last) has landed: rows y + 3 .. y + kCRing - 2
-            // (kCRing - 4 groups) may still be in flight
-            asm volatile("cp.async.wait_group %0;" ::"n"(kCRing - 4) : "memory");
+            // row y + 2 (the next product's last) into the slot of row y - 2, whose last
+            // product (y - 1) has completed; then row y + 3 into registers
+            if (y + 1 < y1) {
+                put_row(y + 2);
+                if (y + 3 <= y1) fetch_row(b, y + 3, x0);
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             const bool ok = cbar_wait(su32(mbar + buf), (done >> 1) & 1);
             done++;
@@ -470,11 +500,8 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
-        // the ring is restaged by the next run: no copy may still be landing
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
+        __syncthreads(); // the ring is restaged by the next run
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
     // after a timeout a product may still run: let it finish before its
     // accumulators are released
     if (tid == 0 && *s_err && issued > done) cbar_wait(su32(mbar + ((issued - 1) & 1)), ((issued - 1) >> 1) & 1);
