@@ -32,7 +32,9 @@
 //     re-matched by the direct kernel (k_match_fix).
 //
 // Work split: a CTA of 4 warps (two CTAs per SM); warp w owns tensor-memory
-// lanes 32w..32w+31, i.e. references 32w..32w+31.  Every thread also builds
+// lanes 32w..32w+31, i.e. references 32w..32w+31, an 8-row x 4-column block
+// of the tile, and selects only on the chunks and 8-column steps that its
+// references' windows reach.  Every thread also builds
 // one candidate row of the FP16 operand tiles (core-matrix layout, no
 // swizzle) and thread 0 issues the MMAs.  Two accumulator buffers of 128
 // columns alternate: the MMAs of chunk c+1 run while the warps select on
@@ -408,8 +410,11 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     const float nms = -mu * sc; // fma(x, sc, nms) = (x - mu) sc, rounded once
 
     // ---- this thread's reference (tensor-memory lane tid) and its window
+    // warp w owns an 8-row x 4-column block of the tile (rows 8 (w >> 1) ..,
+    // columns 4 (w & 1) ..), so that its references' windows cover about 30
+    // of the tile's chunks and 48 of the 64 candidate columns of each
     const int m = tid;
-    const int rr = m >> 3, rc = m & 7;
+    const int rr = 8 * (m >> 6) + ((m & 31) >> 2), rc = 4 * ((m >> 5) & 1) + (m & 3);
     const bool vref = rr < nP && rc < nQ;
     const int ri = vref ? grid_pos(p0 + rr, s, H, kPatch) : 0;
     const int rj = vref ? grid_pos(q0 + rc, s, W, kPatch) : 0;
@@ -484,7 +489,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         int cw[4];
 #pragma unroll
         for (int w = 0; w < 4; w++) {
-            const int r0 = min(4 * w, nP - 1), r1 = min(4 * w + 3, nP - 1);
+            const int r0 = min(8 * (w >> 1), nP - 1), r1 = min(8 * (w >> 1) + 7, nP - 1);
             const int mid = (grid_pos(p0 + r0, s, H, kPatch) + grid_pos(p0 + r1, s, H, kPatch)) / 2 - uy0;
             cw[w] = min(nch - 1, max(0, mid / kChunkRows));
         }
@@ -549,6 +554,14 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         whi = max(whi, __shfl_xor_sync(kFull, whi, o));
     }
     const int wc_lo = whi >= 0 ? wlo / kChunkRows : 1, wc_hi = whi >= 0 ? whi / kChunkRows : 0;
+    // the warp's candidate columns, in steps of 8: cs_lo .. cs_hi of the chunk row's 8
+    int xlo = vref ? max(0, rj - R) - ux0 : INT_MAX, xhi = vref ? min(W - kPatch, rj + R) - ux0 : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        xlo = min(xlo, __shfl_xor_sync(kFull, xlo, o));
+        xhi = max(xhi, __shfl_xor_sync(kFull, xhi, o));
+    }
+    const int cs_lo = xhi >= 0 ? xlo >> 3 : 0, ncs = xhi >= 0 ? (xhi >> 3) - cs_lo + 1 : 0;
     const float kInf = __int_as_float(0x7f800000);
     // this lane's LP best keys so far, ascending, in registers (static indices only)
     float lkr[LP];
@@ -625,7 +638,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
         // select on chunk c: 8 columns per step; the final step of the last
         // chunk only merges what is still pending (one copy of the merge code)
         const int ch = s_order[c];
-        const int nsteps = (ok && ch >= wc_lo && ch <= wc_hi) ? kNc / 8 : 0;
+        const int nsteps = (ok && ch >= wc_lo && ch <= wc_hi) ? kChunkRows * ncs : 0;
         const int nst = nsteps + (c == nch - 1 ? 1 : 0);
         const uint32_t tcol = tmem + (uint32_t)(b * kNc) + ((uint32_t)(warp * 32) << 16);
         const int pb = (c % 3) * kNc;
@@ -633,9 +646,12 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
 #pragma unroll 1
         for (int st = 0; st < nst; st++) {
             if (st < nsteps) {
-                const int g = st >> 2, j8 = (st & 3) * 8;
-                const int rowl = ch * kChunkRows + (g >> 1);
-                const int h = g & 1;
+                // step st: chunk row st / ncs, columns 8 cs .. 8 cs + 7 of it
+                const int r2 = st >= ncs ? 1 : 0, cs = cs_lo + st - r2 * ncs;
+                const int col8 = r2 * kChunkCols + 8 * cs; // column of the chunk (accumulator, terms)
+                const int j8 = (cs & 3) * 8;
+                const int rowl = ch * kChunkRows + r2;
+                const int h = cs >> 2;
                 unsigned msk = 0u;
                 if (rowl >= ky_lo && rowl <= ky_hi) {
                     msk = h ? colm1 : colm0;
@@ -643,12 +659,12 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
                 }
                 msk >>= j8;
                 uint32_t v[8];
-                tmem_ld8(tcol + (uint32_t)(st * 8), v);
+                tmem_ld8(tcol + (uint32_t)col8, v);
                 // e = |b~|^2 + d (d + (S_a - S_b) / 4) - 2 a~.b~ with d = 8 (m_a - m_b):
                 // the block-centred key, two columns per packed FP32 operation
-                const ulonglong2 *qn = reinterpret_cast<const ulonglong2 *>(nbs + pb + st * 8);
-                const ulonglong2 *qm = reinterpret_cast<const ulonglong2 *>(nbm + pb + st * 8);
-                const ulonglong2 *qt = reinterpret_cast<const ulonglong2 *>(ntb + pb + st * 8);
+                const ulonglong2 *qn = reinterpret_cast<const ulonglong2 *>(nbs + pb + col8);
+                const ulonglong2 *qm = reinterpret_cast<const ulonglong2 *>(nbm + pb + col8);
+                const ulonglong2 *qt = reinterpret_cast<const ulonglong2 *>(ntb + pb + col8);
                 const ulonglong2 n0 = qn[0], n1 = qn[1], m0 = qm[0], m1 = qm[1], t0 = qt[0], t1 = qt[1];
                 const f2 nn[4] = {n0.x, n0.y, n1.x, n1.y}, mm[4] = {m0.x, m0.y, m1.x, m1.y};
                 const f2 tt[4] = {t0.x, t0.y, t1.x, t1.y};
