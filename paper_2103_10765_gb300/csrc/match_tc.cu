@@ -31,10 +31,16 @@
 //     non-finite input, a timed-out wait) is marked by slot 0 = -1 and
 //     re-matched by the direct kernel (k_match_fix).
 //
-// Work split: a CTA of 4 warps (two CTAs per SM); warp w owns tensor-memory
-// lanes 32w..32w+31, i.e. references 32w..32w+31, an 8-row x 4-column block
-// of the tile, and selects only on the chunks and 8-column steps that its
-// references' windows reach.  Every thread also builds
+// Work split: a CTA of 4 selection warps and one issuing warp (two CTAs per
+// SM); selection warp w owns tensor-memory lanes 32w..32w+31, i.e.
+// references 32w..32w+31, an 8-row x 4-column block of the tile, and selects
+// only on the chunks and 8-column steps that its references' windows reach.
+// No CTA-wide barrier per chunk: the selection threads arrive on an
+// mbarrier when they have built the next chunk's operand rows, each warp
+// arrives on another when it has read a chunk's accumulators, and the
+// issuing warp starts the product of chunk c + 1 once chunk c + 1 is built
+// and the buffer it overwrites (chunk c - 1's) is consumed, so warps whose
+// windows miss a chunk run ahead instead of waiting.  Every thread also builds
 // one candidate row of the FP16 operand tiles (core-matrix layout, no
 // swizzle) and thread 0 issues the MMAs.  Two accumulator buffers of 128
 // columns alternate: the MMAs of chunk c+1 run while the warps select on
@@ -60,7 +66,8 @@ constexpr int kChunkRows = 2, kChunkCols = 64, kNc = kChunkRows * kChunkCols; //
 constexpr int kKd = kPatch * kPatch;                       // contraction length
 constexpr int kRegStride = kChunkCols + kPatch;            // region row stride (floats)
 constexpr int kOp = kM * kKd * 2;                          // bytes of one FP16 operand tile (128 x 64)
-constexpr int kThreads = 128;                             // 4 warps: warp w owns tensor-memory lanes 32w..32w+31
+constexpr int kThreads = 128;                             // 4 selection warps: warp w owns tensor-memory lanes 32w..32w+31
+constexpr int kCta = kThreads + 32;                        // + one warp that issues the products
 constexpr int kDBuf = 2;                                   // accumulator buffers
 constexpr uint32_t kTmemCols = 256;                        // power-of-two allocation >= kDBuf * kNc
 constexpr int kPend = 24, kFlushAt = 16;                   // per-lane pending keys (checked every 8 columns)
@@ -95,6 +102,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity)
@@ -328,7 +340,7 @@ namespace {
 
 // LP: register list capacity (power of two); LT: keys kept per reference.
 template <int LP, int LT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kCta, 2)
 k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
            TcLayout lay, int32_t *__restrict__ idx, float *__restrict__ dist)
 {
@@ -353,7 +365,9 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     float *ntb = reinterpret_cast<float *>(smem + lay.ntb); // [3][kNc]
     float *pk = reinterpret_cast<float *>(smem + lay.pk);    // [kPend][kM] pending keys
     unsigned short *pi = reinterpret_cast<unsigned short *>(smem + lay.pi); // their candidate numbers
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + lay.misc);        // [2]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + lay.misc);        // [2] products done
+    uint64_t *mb_built = reinterpret_cast<uint64_t *>(smem + lay.misc + 16); // next chunk's operand built
+    uint64_t *mb_used = reinterpret_cast<uint64_t *>(smem + lay.misc + 40);  // [2] accumulators read
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + lay.misc + 32);
     volatile int *s_err = reinterpret_cast<volatile int *>(smem + lay.misc + 36);
     float *s_red = reinterpret_cast<float *>(smem + lay.misc + 64); // [4]
@@ -361,8 +375,13 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     const uint32_t sbase = smem_u32(smem);
 
     if (warp == 0) tmem_alloc(smem_u32(s_tmem), kTmemCols);
+    const bool selw = tid < kThreads; // a selection thread (else the issuing warp)
     if (tid == 0) {
-        for (int b = 0; b < kDBuf; b++) mbar_init(smem_u32(&mbar[b]), 1);
+        for (int b = 0; b < kDBuf; b++) {
+            mbar_init(smem_u32(&mbar[b]), 1);
+            mbar_init(smem_u32(&mb_used[b]), kThreads / 32);
+        }
+        mbar_init(smem_u32(mb_built), kThreads);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_err = 0;
     }
@@ -370,7 +389,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     // ---- search region (raw pixels, zero outside the image) and its mean
     const int vrows = UH + kPatch - 1, vcols = UW + kPatch - 1; // pixels of the union's blocks
     float sum = 0.f;
-    for (int e = tid; e < rrows * kRegStride; e += kThreads) {
+    for (int e = tid; selw && e < rrows * kRegStride; e += kThreads) {
         const int y = e / kRegStride, x = e - y * kRegStride;
         const int gy = uy0 + y, gx = ux0 + x;
         float v = 0.f;
@@ -380,7 +399,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-    if (lane == 0) s_red[warp] = sum;
+    if (lane == 0 && selw) s_red[warp] = sum;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -389,14 +408,14 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     for (int w = 0; w < kThreads / 32; w++) mu += s_red[w];
     mu /= (float)(vrows * vcols);
     float mx = 0.f;
-    for (int e = tid; e < vrows * vcols; e += kThreads) {
+    for (int e = tid; selw && e < vrows * vcols; e += kThreads) {
         const int y = e / vcols, x = e - y * vcols;
         mx = fmaxf(mx, fabsf(reg[y * kRegStride + x] - mu));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
     __syncthreads(); // every thread has read the sums
-    if (lane == 0) s_red[warp] = mx;
+    if (lane == 0 && selw) s_red[warp] = mx;
     __syncthreads();
     float maxabs = 0.f;
     for (int w = 0; w < kThreads / 32; w++) maxabs = fmaxf(maxabs, s_red[w]);
@@ -473,7 +492,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
 
     // ---- reference operand A (thread m builds reference m) and the chunk order
     float ra2 = 0.f, a8 = 0.f, ta = 0.f; // reference: centred norm, 8 m_a, 8 m_a + S_a / 4
-    if (!bad) {
+    if (!bad && selw) {
         float mean, ssum;
         // a padding lane (no reference) reads the region's first block, which
         // is in bounds, and zeroes it
@@ -612,28 +631,36 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     };
 
     // ---- pipeline: MMA(c + 1) runs while the warps select on chunk c
-    int last_issued = -1; // thread 0 only
+    const bool issuer = tid == kThreads; // lane 0 of the issuing warp
+    int last_issued = -1;                // issuer only
     if (!bad) {
-        build(s_order[0], 0);
+        if (selw) build(s_order[0], 0);
         fence_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
             issue(0);
             last_issued = 0;
         }
     }
-    for (int c = 0; c < (bad ? 0 : nch); c++) {
+    if (!bad && issuer) {
+        // product c + 1 into buffer (c + 1) & 1: its operand rows are built
+        // (phase c of mb_built) and chunk c - 1, which used that buffer, is read
+        for (int c = 0; c + 1 < nch; c++) {
+            if (!mbar_wait(smem_u32(mb_built), c & 1, s_err)) break;
+            if (c >= 1 && !mbar_wait(smem_u32(&mb_used[(c + 1) & 1]), ((c - 1) >> 1) & 1, s_err)) break;
+            issue((c + 1) & 1);
+            last_issued = c + 1;
+        }
+    }
+    for (int c = 0; c < (bad || !selw ? 0 : nch); c++) {
         const int b = c & 1;
         const bool ok = __all_sync(kFull, mbar_wait(smem_u32(&mbar[b]), (c >> 1) & 1, s_err));
         tc_fence_after();
         // the product of chunk c is done: its operand tile is free for chunk c + 1
-        if (c + 1 < nch && !*s_err) build(s_order[c + 1], (c + 1) % 3);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0 && c + 1 < nch && !*s_err) {
-            issue((c + 1) & 1);
-            last_issued = c + 1;
+        if (c + 1 < nch) {
+            if (!*s_err) build(s_order[c + 1], (c + 1) % 3);
+            fence_async_smem();
+            mbar_arrive(smem_u32(mb_built));
         }
         // select on chunk c: 8 columns per step; the final step of the last
         // chunk only merges what is still pending (one copy of the merge code)
@@ -690,12 +717,14 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
             if (__any_sync(kFull, np >= kFlushAt || (st == nsteps && np > 0))) flush();
         }
         tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&mb_used[b]));
     }
 
     // ---- the lists move to shared memory (over the operand tiles, whose last
     // product has completed); after a timeout the last product may still be running: let it finish
     // before its operand tiles are overwritten and its accumulators released
-    if (tid == 0 && *s_err && last_issued >= 0)
+    if (issuer && *s_err && last_issued >= 0)
         mbar_wait(smem_u32(&mbar[last_issued & 1]), (last_issued >> 1) & 1, nullptr);
     fence_async_smem();
     __syncthreads();
@@ -703,18 +732,20 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     float *lk = reinterpret_cast<float *>(smem + lay.lk); // [LT][kM] keys, then exact distances
     int *li = reinterpret_cast<int *>(smem + lay.li);
     int cnt = 0;
+    if (selw) { // (the issuing warp holds no list)
 #pragma unroll
-    for (int t = 0; t < LT; t++) {
-        lk[t * kM + m] = lkr[t];
-        li[t * kM + m] = lir[t];
-        cnt += lkr[t] < kInf ? 1 : 0;
-    }
-    // the smallest dropped key joins the exact re-rank (slot LT; it is not
-    // below any kept key: the list only ever takes smaller keys)
-    if (x1 < kInf) {
-        lk[LT * kM + m] = x1;
-        li[LT * kM + m] = i1;
-        cnt++;
+        for (int t = 0; t < LT; t++) {
+            lk[t * kM + m] = lkr[t];
+            li[t * kM + m] = lir[t];
+            cnt += lkr[t] < kInf ? 1 : 0;
+        }
+        // the smallest dropped key joins the exact re-rank (slot LT; it is not
+        // below any kept key: the list only ever takes smaller keys)
+        if (x1 < kInf) {
+            lk[LT * kM + m] = x1;
+            li[LT * kM + m] = i1;
+            cnt++;
+        }
     }
 
     if (vref) {
@@ -847,7 +878,7 @@ cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, i
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.bytes);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kTileX - 1) / kTileX, (By + kTileY - 1) / kTileY);
-    kern<<<grid, kThreads, lay.bytes, st>>>(img, H, W, pitch, By, Bx, s, R, K, lay, idx, dist);
+    kern<<<grid, kCta, lay.bytes, st>>>(img, H, W, pitch, By, Bx, s, R, K, lay, idx, dist);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_match_fix(img, H, W, pitch, By, Bx, s, R, K, idx, dist, st);
 }
