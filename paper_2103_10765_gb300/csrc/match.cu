@@ -190,11 +190,37 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
     float *buf_d = sm + bufs_off;
     int *buf_i = reinterpret_cast<int *>(buf_d + kRefs * kBuf);
     const int t0 = kRefs == 1 ? (threadIdx.x & 31) : threadIdx.x, nt = kRefs == 1 ? 32 : blockDim.x;
-    for (int e = t0; e < rhp * rw; e += nt) {
-        const int y = e / rw, x = e - y * rw;
-        const float v = (y < rh && x < rwd) ? __ldg(img + (size_t)(ry0 + y) * pitch + rx0 + x) : 0.f;
-        sm[e] = v;
-        smB[e + 1] = v;
+    { // the region, eight loads per thread in flight before their stores; element
+      // e = y rw + x advances by nt per load (nt < rw never holds more than one wrap
+      // for nt = 32; for the CTA's nt the row step is split off once)
+        constexpr int kLd = 8;
+        const int total = rhp * rw, dy = nt / rw, dx = nt - dy * rw;
+        int y = t0 / rw, x = t0 - y * rw;
+        for (int e0 = t0; e0 < total; e0 += kLd * nt) {
+            float v[kLd];
+            int yy = y, xx = x;
+#pragma unroll
+            for (int u = 0; u < kLd; u++) {
+                const int e = e0 + u * nt;
+                v[u] = (e < total && yy < rh && xx < rwd) ? __ldg(img + (size_t)(ry0 + yy) * pitch + rx0 + xx) : 0.f;
+                yy += dy;
+                xx += dx;
+                if (xx >= rw) {
+                    xx -= rw;
+                    yy++;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kLd; u++) {
+                const int e = e0 + u * nt;
+                if (e < total) {
+                    sm[e] = v[u];
+                    smB[e + 1] = v[u];
+                }
+            }
+            y = yy;
+            x = xx;
+        }
     }
     if (t0 == 0) smB[0] = 0.f;
     if (kRefs == 1)
