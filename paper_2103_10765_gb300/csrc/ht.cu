@@ -234,22 +234,22 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t E = (size_t)Zc * Yc * Xc;
 
-    { // one warp per (band, halo row); all of a thread's loads in flight before any store
-        constexpr int NR = 8 * HY / 8; // rows per warp
+    { // warp w loads band w (eight warps, eight bands): its HY halo rows, all of a
+      // thread's loads in flight before any store
+        const int band = warp;
         const int xa = pwrap(x0 - 2 + lane, Xc), xb = pwrap(x0 - 2 + 32 + (lane & 3), Xc);
-        float va[NR], vb[NR];
+        const float *bsrc = coef + band * E + (size_t)m * Yc * Xc;
+        float va[HY], vb[HY];
 #pragma unroll
-        for (int j = 0; j < NR; j++) {
-            const int rr = warp + 8 * j, band = rr / HY, yy = rr - band * HY;
-            const float *src = coef + band * E + ((size_t)m * Yc + pwrap(y0 - 2 + yy, Yc)) * Xc;
-            va[j] = __ldg(src + xa);
-            vb[j] = lane < HX - 32 ? __ldg(src + xb) : 0.f;
+        for (int yy = 0; yy < HY; yy++) {
+            const float *src = bsrc + (size_t)pwrap(y0 - 2 + yy, Yc) * Xc;
+            va[yy] = __ldg(src + xa);
+            vb[yy] = lane < HX - 32 ? __ldg(src + xb) : 0.f;
         }
 #pragma unroll
-        for (int j = 0; j < NR; j++) {
-            const int rr = warp + 8 * j, band = rr / HY, yy = rr - band * HY;
-            s_b[band][yy][lane] = va[j];
-            if (lane < HX - 32) s_b[band][yy][32 + lane] = vb[j];
+        for (int yy = 0; yy < HY; yy++) {
+            s_b[band][yy][lane] = va[yy];
+            if (lane < HX - 32) s_b[band][yy][32 + lane] = vb[yy];
         }
     }
     __syncthreads();

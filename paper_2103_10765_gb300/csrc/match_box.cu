@@ -152,9 +152,27 @@ __global__ void __launch_bounds__(kThr, 2) k_match_box(BoxArgs A)
     int *qi = reinterpret_cast<int *>(qk + kQCap * kThr); // [kQCap][kThr] queued indices
     const int sxs = kDX * kTQ * TH;                   // floats of one row-sum buffer
 
-    for (int e = tid; e < RH * RWd; e += kThr) {
-        const int y = e / RWd, x = e - y * RWd, gy = ry0 + y, gx = rx0 + x;
-        reg[y * RW + x] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? __ldg(A.img + (size_t)gy * A.pitch + gx) : 0.f;
+    { // eight loads per thread in flight before their stores
+        constexpr int kLd = 8;
+        for (int e0 = tid; e0 < RH * RWd; e0 += kLd * kThr) {
+            float v[kLd];
+#pragma unroll
+            for (int u = 0; u < kLd; u++) {
+                const int e = e0 + u * kThr;
+                const int y = e / RWd, x = e - y * RWd, gy = ry0 + y, gx = rx0 + x;
+                v[u] = (e < RH * RWd && gy >= 0 && gy < H && gx >= 0 && gx < W)
+                           ? __ldg(A.img + (size_t)gy * A.pitch + gx)
+                           : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kLd; u++) {
+                const int e = e0 + u * kThr;
+                if (e < RH * RWd) {
+                    const int y = e / RWd, x = e - y * RWd;
+                    reg[y * RW + x] = v[u];
+                }
+            }
+        }
     }
     __syncthreads();
 

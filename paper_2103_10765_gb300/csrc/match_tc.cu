@@ -389,13 +389,29 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     // ---- search region (raw pixels, zero outside the image) and its mean
     const int vrows = UH + kPatch - 1, vcols = UW + kPatch - 1; // pixels of the union's blocks
     float sum = 0.f;
-    for (int e = tid; selw && e < rrows * kRegStride; e += kThreads) {
-        const int y = e / kRegStride, x = e - y * kRegStride;
-        const int gy = uy0 + y, gx = ux0 + x;
-        float v = 0.f;
-        if (gy < H && gx < W) v = __ldg(img + (size_t)gy * pitch + gx);
-        reg[e] = v;
-        if (y < vrows && x < vcols) sum += v;
+    { // eight loads per thread in flight before their stores (the same element
+      // order per thread, so the same sum)
+        constexpr int kLd = 8;
+        const int total = rrows * kRegStride;
+        for (int e0 = tid; selw && e0 < total; e0 += kLd * kThreads) {
+            float v[kLd];
+#pragma unroll
+            for (int u = 0; u < kLd; u++) {
+                const int e = e0 + u * kThreads;
+                const int y = e / kRegStride, x = e - y * kRegStride;
+                const int gy = uy0 + y, gx = ux0 + x;
+                v[u] = (e < total && gy < H && gx < W) ? __ldg(img + (size_t)gy * pitch + gx) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kLd; u++) {
+                const int e = e0 + u * kThreads;
+                if (e < total) {
+                    const int y = e / kRegStride, x = e - y * kRegStride;
+                    reg[e] = v[u];
+                    if (y < vrows && x < vcols) sum += v[u];
+                }
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
