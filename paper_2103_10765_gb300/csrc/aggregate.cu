@@ -107,10 +107,37 @@ __global__ void k_fill(const int32_t *__restrict__ idx, int n, int H, int W, int
     list[off[pos] + slot] = e;
 }
 
-// Sort each bucket ascending (fixes the summation order).
-__global__ void k_sort(const int *__restrict__ off, int npos, int *__restrict__ list)
+// Sort each bucket ascending (fixes the summation order).  A CTA of 256
+// positions stages their entries (one contiguous range) in shared memory,
+// each thread insertion-sorts its position's bucket there, and the CTA writes
+// the range back; a range larger than kSortCap is sorted in place in global
+// memory instead.
+constexpr int kSortCap = 4096;
+
+__global__ void __launch_bounds__(256) k_sort(const int *__restrict__ off, int npos, int *__restrict__ list)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int sl[kSortCap];
+    const int p0 = blockIdx.x * 256, p = p0 + threadIdx.x, pe = min(p0 + 256, npos);
+    const int B0 = off[p0], n = off[pe] - B0;
+    if (n <= kSortCap) {
+        for (int i = threadIdx.x; i < n; i += 256) sl[i] = list[B0 + i];
+        __syncthreads();
+        if (p < npos) {
+            const int b0 = off[p] - B0, b1 = off[p + 1] - B0;
+            for (int i = b0 + 1; i < b1; i++) {
+                const int v = sl[i];
+                int j = i - 1;
+                while (j >= b0 && sl[j] > v) {
+                    sl[j + 1] = sl[j];
+                    j--;
+                }
+                sl[j + 1] = v;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += 256) list[B0 + i] = sl[i];
+        return;
+    }
     if (p >= npos) return;
     const int b0 = off[p], b1 = off[p + 1];
     for (int i = b0 + 1; i < b1; i++) {
