@@ -71,6 +71,7 @@ constexpr int kCta = kThreads + 32;                        // + one warp that is
 constexpr int kDBuf = 2;                                   // accumulator buffers
 constexpr uint32_t kTmemCols = 256;                        // power-of-two allocation >= kDBuf * kNc
 constexpr int kPend = 24, kFlushAt = 16;                   // per-lane pending keys (checked every 8 columns)
+static_assert(kFlushAt - 1 + 8 <= kPend && kPend - 1 - 16 < kFlushAt, "one 16-key merge per flush keeps the queue bounded");
 constexpr int kSpin = 1 << 20;                             // bounded mbarrier polling
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -622,9 +623,12 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     int i1 = 0;                 // the candidate of x1
     int np = 0;         // pending keys of this lane (shared memory)
 
-    // merges every lane's pending keys into its list, sixteen at a time
-    auto flush = [&]() {
-        while (__any_sync(kFull, np > 0)) {
+    // merges every lane's sixteen oldest pending keys into its list: once when
+    // a lane's queue reached kFlushAt (at most 23 pending, at most 7 left, so
+    // the queue of kPend = 24 never overflows and the next merge waits until
+    // more lanes have keys), until every queue is empty when drain is set
+    auto flush = [&](bool drain) {
+        do {
             float pkr[16];
             int pir[16];
 #pragma unroll
@@ -643,7 +647,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
             merge16<LP>(lkr, lir, pkr, pir, x1, i1, x2);
             thr = lkr[LT - 1];
             thr_q = thr < kInf ? thr + 2.5f * delta(thr) : kInf;
-        }
+        } while (drain && __any_sync(kFull, np > 0));
     };
 
     // ---- pipeline: MMA(c + 1) runs while the warps select on chunk c
@@ -730,7 +734,8 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
                     }
                 }
             }
-            if (__any_sync(kFull, np >= kFlushAt || (st == nsteps && np > 0))) flush();
+            const bool fin = st == nsteps; // the last chunk's final step drains every queue
+            if (__any_sync(kFull, np >= kFlushAt || (fin && np > 0))) flush(fin);
         }
         tc_fence_before();
         __syncwarp();
