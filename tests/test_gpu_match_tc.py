@@ -26,7 +26,11 @@ def _both(g, img, K, **kw):
         p = p.replace(**kw)
     i1, d1 = g.match(img, K, p.replace(match_engine=1), with_dist=True)
     i2, d2 = g.match(img, K, p.replace(match_engine=2), with_dist=True)
+    # the same engine without a distance output returns the same indices
+    i3, _ = g.match(img, K, p.replace(match_engine=2), with_dist=False)
     torch.cuda.synchronize()
+    nd = int((i3 != i2).any(dim=1).sum())
+    assert nd == 0, f"{nd} references differ without distances"
     return i1, d1, i2, d2
 
 
