@@ -170,8 +170,11 @@ struct MatchArgs {
 // reference, their common search region in shared memory sm.  kRefs ==
 // kRefsPerCta: every thread of the CTA calls it (the region load ends in a
 // __syncthreads); kRefs == 1: one warp calls it for one reference, with its
-// own region (the load ends in a __syncwarp).
-template <int N, int kRefs>
+// own region (the load ends in a __syncwarp) -- or, with kSplit > 1, the
+// CTA's kSplit warps share the one reference: warp w scans candidate units
+// w, w + kSplit, ..., and warp 0 merges their sorted lists (the same K - 1
+// smallest (distance, index) pairs; the others return early).
+template <int N, int kRefs, int kSplit = 1>
 __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, float *sm)
 {
     const float *__restrict__ img = A.img;
@@ -188,8 +191,9 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
     const int rhp = rh + kVB; // zero rows below absorb the last vertical block
     float *smB = sm + copy_off; // the region again, one float later: smB[e] = sm[e - 1]
     float *buf_d = sm + bufs_off;
-    int *buf_i = reinterpret_cast<int *>(buf_d + kRefs * kBuf);
-    const int t0 = kRefs == 1 ? (threadIdx.x & 31) : threadIdx.x, nt = kRefs == 1 ? 32 : blockDim.x;
+    int *buf_i = reinterpret_cast<int *>(buf_d + (kRefs > kSplit ? kRefs : kSplit) * kBuf); // a buffer per warp
+    constexpr bool kLone = kRefs == 1 && kSplit == 1; // one warp on its own
+    const int t0 = kLone ? (threadIdx.x & 31) : threadIdx.x, nt = kLone ? 32 : blockDim.x;
     { // the region, eight loads per thread in flight before their stores; element
       // e = y rw + x advances by nt per load (nt < rw never holds more than one wrap
       // for nt = 32; for the CTA's nt the row step is split off once)
@@ -223,17 +227,18 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
         }
     }
     if (t0 == 0) smB[0] = 0.f;
-    if (kRefs == 1)
+    if (kLone)
         __syncwarp();
     else
         __syncthreads();
 
     const int warp = kRefs == 1 ? 0 : threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int part = kSplit > 1 ? threadIdx.x >> 5 : 0; // this warp's share of the units
     const int q = q0 + warp;
-    if (q >= Bx) return;
+    if (q >= Bx) return; // (never with kSplit > 1: the reference exists)
     const int j = grid_pos(q, s, W, N);
-    float *wb_d = buf_d + warp * kBuf;
-    int *wb_i = buf_i + warp * kBuf;
+    float *wb_d = buf_d + (kSplit > 1 ? part : warp) * kBuf;
+    int *wb_i = buf_i + (kSplit > 1 ? part : warp) * kBuf;
 
     // negated reference block rows a0 .. a0+NA-1, column pairs (b, b+1) packed:
     // all of it for N = 8, four rows at a time for N = 16
@@ -265,7 +270,7 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
     int thr_i = INT_MAX;
     int cnt = 0; // entries in the warp buffer (warp-uniform)
 
-    for (int u0 = 0; u0 < nunits; u0 += 32) {
+    for (int u0 = 32 * part; u0 < nunits; u0 += 32 * kSplit) {
         const int u = u0 + lane;
         const bool vu = u < nunits;
         int kb = 0, dl = 0;
@@ -383,6 +388,16 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
         bitonic_sort32(bd, bi, lane);
         merge32(ld, li, bd, bi, lane);
     }
+    if (kSplit > 1) { // the warps' lists, over the region (no longer read), merged by warp 0
+        __syncthreads();
+        float *md = sm;
+        int *mi = reinterpret_cast<int *>(sm + kSplit * 32);
+        md[part * 32 + lane] = ld;
+        mi[part * 32 + lane] = li;
+        __syncthreads();
+        if (part != 0) return;
+        for (int w = 1; w < kSplit; w++) merge32(ld, li, md[w * 32 + lane], mi[w * 32 + lane], lane);
+    }
 
     const size_t gi = ((size_t)p * Bx + q) * K;
     if (lane < Kc) {
@@ -408,23 +423,31 @@ __global__ void __launch_bounds__(kRefsPerCta * 32, N <= 8 ? 3 : 2) k_match(Matc
 // w + nw, w + 2 nw, ... (so that marked references, which cluster in smooth
 // image regions, spread over all warps), tests 32 of them per load and
 // matches each marked one exactly as k_match does, in its own region.
+// Re-matches the references the tensor-core pass marked (slot 0 = -1): CTA b
+// scans references b, b + gridDim.x, ... (kFixThreads at a time; marked
+// references cluster in space, so neighbours go to different CTAs) and matches
+// every marked one it found with all its warps (match_group with kSplit =
+// kFixThreads / 32).
+constexpr int kFixThreads = 256;
+
 template <int N>
-__global__ void __launch_bounds__(32) k_match_fix(MatchArgs a, int G)
+__global__ void __launch_bounds__(kFixThreads) k_match_fix(MatchArgs a, int G)
 {
     extern __shared__ float sm[];
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x, w = blockIdx.x;
-    for (int b0 = 0; (long long)b0 * nw < G; b0 += 32) {
-        const long long g = w + (long long)(b0 + lane) * nw;
-        const bool marked = g < G && a.idx[g * a.K] < 0;
-        unsigned mk = __ballot_sync(0xffffffffu, marked);
-        while (mk) {
-            const int t = __ffs(mk) - 1;
-            mk &= mk - 1;
-            const int gg = (int)(w + (long long)(b0 + t) * nw);
+    __shared__ int s_list[kFixThreads];
+    __shared__ int s_n;
+    for (long long j0 = 0; j0 * gridDim.x + blockIdx.x < G; j0 += kFixThreads) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        const long long g = blockIdx.x + (j0 + threadIdx.x) * gridDim.x;
+        if (g < G && a.idx[g * a.K] < 0) s_list[atomicAdd(&s_n, 1)] = (int)g; // any order: outputs are per reference
+        __syncthreads();
+        const int n = s_n;
+        for (int t = 0; t < n; t++) {
+            const int gg = s_list[t];
             const int p = gg / a.Bx;
-            match_group<N, 1>(a, p, gg - p * a.Bx, sm);
-            __syncwarp();
+            match_group<N, 1, kFixThreads / 32>(a, p, gg - p * a.Bx, sm);
+            __syncthreads();
         }
     }
 }
@@ -488,18 +511,19 @@ cudaError_t launch_match_fix(const float *img, int H, int W, int pitch, int By, 
                              int32_t *idx, float *dist, cudaStream_t st)
 {
     const MatchGeom g = match_geom(s, R, kPatch, 1);
-    const size_t smem = (size_t)g.bufs_off * sizeof(float) + (size_t)kBuf * (sizeof(float) + sizeof(int));
+    const size_t smem =
+        (size_t)g.bufs_off * sizeof(float) + (size_t)(kFixThreads / 32) * kBuf * (sizeof(float) + sizeof(int));
     cudaError_t e = cudaFuncSetAttribute(k_match_fix<kPatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int G = By * Bx;
-    int blocks = 8 * nsm;
+    int blocks = 2 * nsm; // all resident at once (registers allow two CTAs per SM)
     if (blocks > G) blocks = G;
     if (blocks < 1) blocks = 1;
     const MatchArgs a{img, H, W, pitch, Bx, s, R, K, g.col_pad, g.rw, g.copy_off, g.bufs_off, idx, dist};
-    k_match_fix<kPatch><<<blocks, 32, smem, st>>>(a, G);
+    k_match_fix<kPatch><<<blocks, kFixThreads, smem, st>>>(a, G);
     return cudaGetLastError();
 }
 
