@@ -168,12 +168,13 @@ struct MatchArgs {
 
 // Matches the references q0 .. q0+kRefs-1 of grid row p: one warp per
 // reference, their common search region in shared memory sm.  kRefs ==
-// kRefsPerCta: every thread of the CTA calls it (the region load ends in a
-// __syncthreads); kRefs == 1: one warp calls it for one reference, with its
-// own region (the load ends in a __syncwarp) -- or, with kSplit > 1, the
-// CTA's kSplit warps share the one reference: warp w scans candidate units
+// kRefsPerCta (k_match): every thread of the CTA calls it (the region load
+// ends in a __syncthreads).  kRefs == 1 with kSplit > 1 (k_match_fix): the
+// CTA's kSplit warps share the one reference -- warp w scans candidate units
 // w, w + kSplit, ..., and warp 0 merges their sorted lists (the same K - 1
-// smallest (distance, index) pairs; the others return early).
+// smallest (distance, index) pairs; the others return early).  kRefs ==
+// kSplit == 1: one warp alone, with its own region (the load ends in a
+// __syncwarp).
 template <int N, int kRefs, int kSplit = 1>
 __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, float *sm)
 {
@@ -195,8 +196,8 @@ __device__ __forceinline__ void match_group(const MatchArgs &A, int p, int q0, f
     constexpr bool kLone = kRefs == 1 && kSplit == 1; // one warp on its own
     const int t0 = kLone ? (threadIdx.x & 31) : threadIdx.x, nt = kLone ? 32 : blockDim.x;
     { // the region, eight loads per thread in flight before their stores; element
-      // e = y rw + x advances by nt per load (nt < rw never holds more than one wrap
-      // for nt = 32; for the CTA's nt the row step is split off once)
+      // e = y rw + x advances by nt per load: dy = nt / rw rows and dx = nt mod rw
+      // columns, with at most one carry from the columns into the rows
         constexpr int kLd = 8;
         const int total = rhp * rw, dy = nt / rw, dx = nt - dy * rw;
         int y = t0 / rw, x = t0 - y * rw;
@@ -417,12 +418,6 @@ __global__ void __launch_bounds__(kRefsPerCta * 32, N <= 8 ? 3 : 2) k_match(Matc
     match_group<N, kRefsPerCta>(a, blockIdx.y, blockIdx.x * kRefsPerCta, sm);
 }
 
-// Exact re-run of the references whose slot 0 is negative: the tensor-core
-// matcher marks that way the references whose candidate list it could not
-// certify.  One warp per CTA; warp w of nw takes the references g = w,
-// w + nw, w + 2 nw, ... (so that marked references, which cluster in smooth
-// image regions, spread over all warps), tests 32 of them per load and
-// matches each marked one exactly as k_match does, in its own region.
 // Re-matches the references the tensor-core pass marked (slot 0 = -1): CTA b
 // scans references b, b + gridDim.x, ... (kFixThreads at a time; marked
 // references cluster in space, so neighbours go to different CTAs) and matches
