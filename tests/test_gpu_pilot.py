@@ -112,7 +112,7 @@ def test_trained_pilot_against_plain_method(orc, sigma):
     wavelet filtering, aggregation) by one forward pass.  At 1024^2 the
     learned form must be faster than the plain GPU form, its PSNR within
     0.3 dB of it, and on a 256^2 crop within 0.3 dB of the FP64 oracle's
-    plain two-stage result (the oracle as judge)."""
+    plain two-stage result (the oracle as the reference)."""
     s = sigma / 255
     theta = np.fromfile(THETA_FILE, dtype="<f4")
     net = gbm3d.PilotNet(theta, DEV)
