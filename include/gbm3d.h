@@ -314,10 +314,13 @@ int gbm3d_pnp_gemm_config(gbm3d_pnp_plan plan, int image, int *cfg_k_h, int *cfg
  * mean (pilot - Y1)^2.  Parameters: one flat FP32 vector theta of
  * gbm3d_pilot_param_count() values, per layer the weights W[tap][ci][co]
  * (tap = 3 (dy + 1) + (dx + 1)) then the biases.  Convolutions use the
- * weights rounded to BF16 and accumulate in FP32; the six 32 -> 32 layers
- * run on the tensor cores with their inputs rounded to BF16.
+ * weights rounded to BF16 and accumulate in FP32; the hidden activations
+ * (outputs of the first seven layers) are stored in BF16, rounded to
+ * nearest-even, and the six 32 -> 32 layers run on the tensor cores.
  * Batches: B images of H x W, contiguous ([B][H][W] float, device);
- * sigma: device array of B noise levels. */
+ * sigma: device array of B noise levels.  EINVAL for an empty or oversized
+ * batch, a NULL pointer or a ws not 256-byte aligned; ECUDA if a launch
+ * fails. */
 int gbm3d_pilot_param_count(void);
 /* Scratch of a forward pass (train = 0) or a gradient / training step (1). */
 int gbm3d_pilot_workspace_bytes(int B, int H, int W, int train, size_t *bytes);
