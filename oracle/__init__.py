@@ -74,7 +74,7 @@ def _declare(lib):
     lib.orc_dwt3.argtypes = [_f64p, c_int, c_int, c_int, c_int, vp]
     lib.orc_idwt3.argtypes = [_f64p, c_int, c_int, c_int, c_int]
     lib.orc_filter_ht.argtypes = [_f64p, c_int, c_int, _i32p, c_int, c_int, c_int, c_int, c_double, c_int, c_int,
-                                  c_double, c_double, c_double, _f64p, _f64p]
+                                  c_double, c_double, c_double, _f64p, _f64p, c_int]
     lib.orc_dct2.argtypes = [_f64p, c_int, c_int]
     lib.orc_haar.argtypes = [_f64p, c_int, c_int]
     lib.orc_filter_wiener.argtypes = [_f64p, _f64p, c_int, c_int, _i32p, c_int, c_int, c_int, c_double, c_double,
@@ -224,14 +224,14 @@ def idwt3(v, L=3):
     return v
 
 
-def filter_ht(Z, idx, sigma, By, Bx, N=8, K=16, L=3, C=2, tau_a=3.6, tau_b=0.3, eps_w=1e-8):
+def filter_ht(Z, idx, sigma, By, Bx, N=8, K=16, L=3, C=2, tau_a=3.6, tau_b=0.3, eps_w=1e-8, nthreads=1):
     Z = _f64(Z)
     H, W = Z.shape
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     groups = np.zeros((By * Bx, K, N, N))
     w = np.zeros(By * Bx)
-    _check(_get().orc_filter_ht(Z, H, W, idx, By, Bx, N, K, float(sigma), L, C, tau_a, tau_b, eps_w, groups, w),
-           "orc_filter_ht")
+    _check(_get().orc_filter_ht(Z, H, W, idx, By, Bx, N, K, float(sigma), L, C, tau_a, tau_b, eps_w, groups, w,
+                                nthreads), "orc_filter_ht")
     return groups, w
 
 

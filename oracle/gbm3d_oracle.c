@@ -278,29 +278,44 @@ int orc_idwt1(const double *lo, const double *hi, int n, int kind, double *x)
  * Reading: Mallat 3-D decomposition -- each level splits the current
  * approximation cube along y and x (bior1.5) and z (Haar); the next level
  * recurses on the low-low-low cube. */
-static void lines(double *v, int Y, int X, int Z, int h, int w, int k, int axis, int kind, int inverse,
-                  double *buf_in, double *buf_out)
+static int lines(double *v, int Y, int X, int Z, int h, int w, int k, int axis, int kind, int inverse, int nt)
 {
     /* Applies the 1-D transform to every line along `axis` inside the
-     * sub-cube [0,h) x [0,w) x [0,k). */
+     * sub-cube [0,h) x [0,w) x [0,k).  Lines are independent: with nt > 1
+     * they are shared among threads, each line still transformed by the
+     * same operations in the same order. */
     int n = axis == 0 ? h : axis == 1 ? w : k;
     int stride = axis == 0 ? X * Z : axis == 1 ? Z : 1;
     int c1 = axis == 0 ? w : h, c2 = axis == 2 ? w : k;
-    for (int u = 0; u < c1; u++)
-        for (int t = 0; t < c2; t++) {
-            size_t base;
-            if (axis == 0) base = (size_t)u * Z + t;                  /* (x=u, z=t) */
-            else if (axis == 1) base = (size_t)u * X * Z + t;         /* (y=u, z=t) */
-            else base = (size_t)u * X * Z + (size_t)t * Z;            /* (y=u, x=t) */
-            for (int e = 0; e < n; e++) buf_in[e] = v[base + (size_t)e * stride];
-            if (!inverse) {
-                ana1(buf_in, n, 1, kind, buf_out, buf_out + n / 2, 1);
-            } else {
-                syn1(buf_in, buf_in + n / 2, 1, n, kind, buf_out, 1);
-            }
-            for (int e = 0; e < n; e++) v[base + (size_t)e * stride] = buf_out[e];
+    int failed = 0;
+#pragma omp parallel num_threads(nt > 0 ? nt : 1)
+    {
+        double *buf_in = malloc(sizeof(double) * n), *buf_out = malloc(sizeof(double) * n);
+        if (!buf_in || !buf_out) {
+#pragma omp atomic write
+            failed = 1;
         }
+#pragma omp for collapse(2) schedule(static)
+        for (int u = 0; u < c1; u++)
+            for (int t = 0; t < c2; t++) {
+                if (!buf_in || !buf_out) continue;
+                size_t base;
+                if (axis == 0) base = (size_t)u * Z + t;                  /* (x=u, z=t) */
+                else if (axis == 1) base = (size_t)u * X * Z + t;         /* (y=u, z=t) */
+                else base = (size_t)u * X * Z + (size_t)t * Z;            /* (y=u, x=t) */
+                for (int e = 0; e < n; e++) buf_in[e] = v[base + (size_t)e * stride];
+                if (!inverse) {
+                    ana1(buf_in, n, 1, kind, buf_out, buf_out + n / 2, 1);
+                } else {
+                    syn1(buf_in, buf_in + n / 2, 1, n, kind, buf_out, 1);
+                }
+                for (int e = 0; e < n; e++) v[base + (size_t)e * stride] = buf_out[e];
+            }
+        free(buf_in);
+        free(buf_out);
+    }
     (void)Y;
+    return failed ? ORC_ENOMEM : ORC_OK;
 }
 
 /* Hard threshold Upsilon (Sec. 3.1): keep alpha if |alpha| >= lambda. */
@@ -315,18 +330,15 @@ double orc_upsilon(double a, double lam) { return upsilon(a, lam); }
  * coefficient of level l (1 = finest) with tau[l-1]; the final approximation
  * cube is kept.  Reading: all seven detail bands of each level are
  * thresholded; the coarsest approximation is not. */
-static int dwt3_forward(double *v, int Y, int X, int Z, int L, const double *tau)
+static int dwt3_forward(double *v, int Y, int X, int Z, int L, const double *tau, int nt)
 {
-    int mx = Y > X ? Y : X;
-    if (Z > mx) mx = Z;
-    double *bi = malloc(sizeof(double) * mx), *bo = malloc(sizeof(double) * mx);
-    if (!bi || !bo) { free(bi); free(bo); return ORC_ENOMEM; }
-    int h = Y, w = X, k = Z;
-    for (int lev = 1; lev <= L; lev++) {
-        lines(v, Y, X, Z, h, w, k, 0, WAV_BIOR15, 0, bi, bo);
-        lines(v, Y, X, Z, h, w, k, 1, WAV_BIOR15, 0, bi, bo);
-        lines(v, Y, X, Z, h, w, k, 2, WAV_HAAR, 0, bi, bo);
-        if (tau) {
+    int h = Y, w = X, k = Z, st = ORC_OK;
+    for (int lev = 1; lev <= L && st == ORC_OK; lev++) {
+        st = lines(v, Y, X, Z, h, w, k, 0, WAV_BIOR15, 0, nt);
+        if (st == ORC_OK) st = lines(v, Y, X, Z, h, w, k, 1, WAV_BIOR15, 0, nt);
+        if (st == ORC_OK) st = lines(v, Y, X, Z, h, w, k, 2, WAV_HAAR, 0, nt);
+        if (tau && st == ORC_OK) {
+#pragma omp parallel for num_threads(nt > 0 ? nt : 1) schedule(static)
             for (int y = 0; y < h; y++)
                 for (int x = 0; x < w; x++)
                     for (int z = 0; z < k; z++)
@@ -337,24 +349,19 @@ static int dwt3_forward(double *v, int Y, int X, int Z, int L, const double *tau
         }
         h /= 2; w /= 2; k /= 2;
     }
-    free(bi); free(bo);
-    return ORC_OK;
+    return st;
 }
 
-static int dwt3_inverse(double *v, int Y, int X, int Z, int L)
+static int dwt3_inverse(double *v, int Y, int X, int Z, int L, int nt)
 {
-    int mx = Y > X ? Y : X;
-    if (Z > mx) mx = Z;
-    double *bi = malloc(sizeof(double) * mx), *bo = malloc(sizeof(double) * mx);
-    if (!bi || !bo) { free(bi); free(bo); return ORC_ENOMEM; }
-    for (int lev = L; lev >= 1; lev--) {
+    int st = ORC_OK;
+    for (int lev = L; lev >= 1 && st == ORC_OK; lev--) {
         int h = Y >> (lev - 1), w = X >> (lev - 1), k = Z >> (lev - 1);
-        lines(v, Y, X, Z, h, w, k, 2, WAV_HAAR, 1, bi, bo);
-        lines(v, Y, X, Z, h, w, k, 1, WAV_BIOR15, 1, bi, bo);
-        lines(v, Y, X, Z, h, w, k, 0, WAV_BIOR15, 1, bi, bo);
+        st = lines(v, Y, X, Z, h, w, k, 2, WAV_HAAR, 1, nt);
+        if (st == ORC_OK) st = lines(v, Y, X, Z, h, w, k, 1, WAV_BIOR15, 1, nt);
+        if (st == ORC_OK) st = lines(v, Y, X, Z, h, w, k, 0, WAV_BIOR15, 1, nt);
     }
-    free(bi); free(bo);
-    return ORC_OK;
+    return st;
 }
 
 static int dims_ok(int Y, int X, int Z, int L)
@@ -367,13 +374,13 @@ static int dims_ok(int Y, int X, int Z, int L)
 int orc_dwt3(double *v, int Y, int X, int Z, int L, const double *tau)
 {
     if (!v || !dims_ok(Y, X, Z, L)) return ORC_EINVAL;
-    return dwt3_forward(v, Y, X, Z, L, tau);
+    return dwt3_forward(v, Y, X, Z, L, tau, 1);
 }
 
 int orc_idwt3(double *v, int Y, int X, int Z, int L)
 {
     if (!v || !dims_ok(Y, X, Z, L)) return ORC_EINVAL;
-    return dwt3_inverse(v, Y, X, Z, L);
+    return dwt3_inverse(v, Y, X, Z, L, 1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -391,11 +398,14 @@ int orc_idwt3(double *v, int Y, int X, int Z, int L)
  * Weights w_pq = 1 / TV(u^{pq}); reading: anisotropic L1 total variation of
  * forward differences inside the N x N x K block (no wrap), guarded below by
  * eps_w.
- * Outputs groups[g][r][a][b] = U[pN+a, qN+b, r] and w[g], g = p*Bx + q. */
+ * Outputs groups[g][r][a][b] = U[pN+a, qN+b, r] and w[g], g = p*Bx + q.
+ * nthreads: threads that share the independent lines of each 1-D transform
+ * and the independent planes of the volume copies (same arithmetic). */
 int orc_filter_ht(const double *Z, int H, int W, const int32_t *idx, int By, int Bx,
                   int N, int K, double sigma, int L, int C, double tau_a, double tau_b,
-                  double eps_w, double *groups, double *w)
+                  double eps_w, double *groups, double *w, int nthreads)
 {
+    const int nt = nthreads > 0 ? nthreads : 1;
     if (!Z || !idx || !groups || !w || By <= 0 || Bx <= 0 || C <= 0 || sigma < 0) return ORC_EINVAL;
     int Yd = By * N, Xd = Bx * N, Zd = K;
     if (!dims_ok(Yd, Xd, Zd, L)) return ORC_EINVAL;
@@ -418,13 +428,15 @@ int orc_filter_ht(const double *Z, int H, int W, const int32_t *idx, int By, int
 
     int st = ORC_OK;
     for (int h = 0; h < C && st == ORC_OK; h++) {
+#pragma omp parallel for num_threads(nt) schedule(static)
         for (int y = 0; y < Yd; y++)
             for (int x = 0; x < Xd; x++)
                 for (int z = 0; z < Zd; z++)
                     S[((size_t)y * Xd + x) * Zd + z] =
                         V[((size_t)pmod(y - h, Yd) * Xd + pmod(x - h, Xd)) * Zd + pmod(z - h, Zd)];
-        st = dwt3_forward(S, Yd, Xd, Zd, L, tau);
-        if (st == ORC_OK) st = dwt3_inverse(S, Yd, Xd, Zd, L);
+        st = dwt3_forward(S, Yd, Xd, Zd, L, tau, nt);
+        if (st == ORC_OK) st = dwt3_inverse(S, Yd, Xd, Zd, L, nt);
+#pragma omp parallel for num_threads(nt) schedule(static)
         for (int y = 0; y < Yd; y++)
             for (int x = 0; x < Xd; x++)
                 for (int z = 0; z < Zd; z++)
@@ -717,7 +729,7 @@ static int stage1(const double *Z, int H, int W, double sigma, const orc_params 
         st = orc_match(Z, H, W, N, p->step, p->search_radius, K, idx, NULL, nt);
         if (st == ORC_OK)
             st = orc_filter_ht(Z, H, W, idx, By, Bx, N, K, sigma, p->levels, p->cycle_spins, p->tau_a,
-                               p->tau_b, p->eps_w, gr, w);
+                               p->tau_b, p->eps_w, gr, w, nt);
         if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, 0.0, out);
     }
     free(idx); free(gr); free(w);
@@ -835,7 +847,7 @@ static int stage_color(const double *Zo, const double *Y1o, int H, int W, double
         const double sc = sigma * orc_opp_sigma_scale(c);
         if (!Y1o) {
             st = orc_filter_ht(Zo + c * n, H, W, idx, By, Bx, N, K, sc, p->levels, p->cycle_spins, p->tau_a,
-                               p->tau_b, p->eps_w, gr, w);
+                               p->tau_b, p->eps_w, gr, w, nt);
             if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, 0.0, out + c * n);
         } else {
             st = orc_filter_wiener(Zo + c * n, Y1o + c * n, H, W, idx, (int)G, N, K, sc, p->eps_w, gr, w, nt);
