@@ -184,8 +184,10 @@ int gbm3d_aggregate(const float *groups, const float *w, const int32_t *idx, int
  *   12 (H W + 1) + 4 G K bytes); larger sizes return GBM3D_ENOMEM without
  *   launching anything.
  *   The call allocates nothing.  Its first call on a device looks up the
- *   array's device address (cudaGetSymbolAddress) and caches it; make that
- *   first call before any stream capture on that device.
+ *   array's device address (cudaGetSymbolAddress) and caches it for the rest
+ *   of the process; make that first call before any stream capture on that
+ *   device.  Resetting the device (cudaDeviceReset) after that first call is
+ *   not supported: the cached address would belong to the old context.
  *   All calls on a device share the one array, and each call clears the
  *   parts it needs zeroed: calls whose executions overlap on the GPU (other
  *   streams, other host threads) race on it and must be serialised by the
@@ -195,9 +197,9 @@ int gbm3d_aggregate_noalloc(const float *groups, const float *w, const int32_t *
                             gbm3d_stream_t stream);
 
 /* Whole method (Sec. 1.1 BM3D1/BM3D2 with translation averaging, eq.
- * firstEst): input the noisy image and the noise standard deviation, get the
- * denoised image (Sec. 1: "only ... the noisy image and an estimate of the
- * noise level").  Stage 1 with k1, then (stages == 2) stage 2 matching on the
+ * firstEst): the inputs are the noisy image and the noise standard deviation
+ * (Sec. 1 states the problem with just these two inputs), the output is the
+ * denoised image.  Stage 1 with k1, then (stages == 2) stage 2 matching on the
  * stage-1 estimate with k2 and Wiener filtering, each stage averaged over
  * `translations` circular image shifts.
  *   noisy : H x W, pitch;  out : H x W, same pitch (must not alias noisy).

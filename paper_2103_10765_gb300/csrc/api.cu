@@ -284,8 +284,15 @@ static bool side_stream(cudaStream_t st, SideStream **out)
             return false;
         }
         if (cudaEventCreateWithFlags(&ss.ready, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ss.done, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&ss.done, cudaEventDisableTiming) != cudaSuccess) {
+            // back to the empty state, so that a later call retries from scratch
+            // and this one takes the path without overlap
+            if (ss.ready) cudaEventDestroy(ss.ready);
+            if (ss.done) cudaEventDestroy(ss.done);
+            cudaStreamDestroy(ss.s);
+            ss = SideStream{};
             return false;
+        }
     }
     *out = &ss;
     return true;

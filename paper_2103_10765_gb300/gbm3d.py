@@ -276,9 +276,17 @@ def aggregate_noalloc(groups: torch.Tensor, w: torch.Tensor, idx: torch.Tensor, 
     """gbm3d_aggregate_noalloc: aggregation into a caller-provided `out` using
     the library's fixed device scratch (no workspace, no allocation)."""
     p = p or params_default()
-    _, _, pitch = _img(out, "out")
+    oh, ow, pitch = _img(out, "out")
+    if (oh, ow) != (H, W):
+        raise ValueError(f"out is {oh} x {ow}, the image {H} x {W}")
+    for t, name, dt in ((groups, "groups", torch.float32), (w, "w", torch.float32), (idx, "idx", torch.int32)):
+        if t.dtype != dt or t.device != out.device:
+            raise ValueError(f"{name} must be a {dt} tensor on {out.device}")
+    if idx.dim() != 2 or w.numel() != idx.shape[0] or groups.numel() != idx.numel() * p.patch * p.patch:
+        raise ValueError("groups [G, K, N, N], w [G] and idx [G, K] disagree")
+    groups, w, idx = groups.contiguous(), w.contiguous(), idx.contiguous()
     _check(load().gbm3d_aggregate_noalloc(_ptr(groups), _ptr(w), _ptr(idx), idx.shape[1], H, W, pitch,
-                                          ctypes.byref(p), float(window_beta), _ptr(out), _stream(groups)))
+                                          ctypes.byref(p), float(window_beta), _ptr(out), _stream(out)))
     return out
 
 

@@ -46,7 +46,10 @@ def _call_noalloc(groups, w, idx, H, W, beta, out):
 
 
 def test_noalloc_matches_workspace_aggregation_twice():
-    cases = [(96, 80, 32, 2.0, 1), (61, 77, 16, 0.0, 2)]
+    # a larger image after a smaller one and the reverse, so that both a stale
+    # tail and a fresh region of the shared scratch are exercised; 512 x 512
+    # with K = 32 fills the fixed scratch to about 85 %
+    cases = [(96, 80, 32, 2.0, 1), (61, 77, 16, 0.0, 2), (512, 512, 32, 2.0, 3), (40, 48, 32, 0.0, 4)]
     for H, W, K, beta, seed in cases:
         groups, w, idx = _case(H, W, K, seed)
         want = gbm3d.aggregate(groups, w, idx, H, W, window_beta=beta)
@@ -68,3 +71,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                      ctypes.c_float(0.0), ctypes.c_void_p(out.data_ptr()), None)
     assert st == gbm3d.ENOMEM
     assert b"fixed" in lib.gbm3d_last_error_string()
+
+
+def test_noalloc_python_wrapper():
+    """The binding's aggregate_noalloc checks its arguments and gives the
+    workspace aggregation's result."""
+    H, W, K = 72, 64, 16
+    groups, w, idx = _case(H, W, K, 5)
+    want = gbm3d.aggregate(groups, w, idx, H, W)
+    out = gbm3d.aggregate_noalloc(groups, w, idx, H, W, torch.empty((H, W), device="cuda"))
+    torch.cuda.synchronize()
+    assert float((out - want).abs().max()) <= ATOL
+    with pytest.raises(ValueError):
+        gbm3d.aggregate_noalloc(groups, w, idx, H, W, torch.empty((H - 1, W), device="cuda"))
+    with pytest.raises(ValueError):
+        gbm3d.aggregate_noalloc(groups.double(), w, idx, H, W, torch.empty((H, W), device="cuda"))
