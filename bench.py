@@ -43,8 +43,14 @@ _PARAMS = "N=8 s=3 R=19 (39x39 offsets), K1=16 K2=32, 3 levels bior1.5/Haar, 2 c
 # --workload: gray1024 is the metric's configuration (the default); the other
 # two are the larger tensor-core matching configurations
 WORKLOADS = {
-    "gray1024": dict(H=1024, W=1024, C=1, cpu_crop=512, ref_crop=256,
+    "gray1024": dict(H=1024, W=1024, C=1, cpu_crop=None, ref_crop=256,
                      desc="two-stage G-BM3D, 1024x1024 grayscale fp32, sigma 25/255, " + _PARAMS),
+    # the same configuration with the direct FP32 matching engine (the plain
+    # GPU form of Sec. 2's distance; the default engine ranks with Theorem 1's
+    # expansion on the tensor cores and re-ranks exactly)
+    "gray1024_direct": dict(H=1024, W=1024, C=1, cpu_crop=None, ref_crop=256, engine=1,
+                            desc="two-stage G-BM3D, 1024x1024 grayscale fp32, sigma 25/255, direct FP32 matching "
+                                 "engine, " + _PARAMS),
     "gray4096": dict(H=4096, W=4096, C=1, cpu_crop=512, ref_crop=256,
                      desc="two-stage G-BM3D, 4096x4096 grayscale fp32, sigma 25/255, " + _PARAMS),
     "color2048": dict(H=2048, W=2048, C=3, cpu_crop=256, ref_crop=128,
@@ -71,32 +77,35 @@ WORKLOADS = {
 H = W = 1024
 C = 1                   # channels
 PRESET = 0              # library parameter preset of the workload
+ENGINE = 0              # gbm3d_params.match_engine of the workload
 LEARNED = False         # stage 1 replaced by the trained network
 WORKLOAD = WORKLOADS["gray1024"]["desc"]
-CPU_CROP = 512          # cpu_baseline sample: top-left crop of the workload image
+CPU_CROP = None         # cpu_baseline sample: top-left crop of the workload image (None: the whole image)
 REF_CROP = 256          # --impl reference: crop per step
+ST_CROP = 256           # cpu_baseline's single-threaded sample: top-left crop
 
 
 def set_workload(name: str):
-    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP, PRESET, LEARNED
+    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP, PRESET, LEARNED, ENGINE
     w = WORKLOADS[name]
     H, W, C, WORKLOAD, CPU_CROP, REF_CROP = w["H"], w["W"], w["C"], w["desc"], w["cpu_crop"], w["ref_crop"]
     PRESET = w.get("preset", 0)
+    ENGINE = w.get("engine", 0)
     LEARNED = w.get("learned", False)
 
 
 THETA_FILE = os.path.join(ROOT, "paper_2103_10765_gb300", "pilot_theta.f32")
 
 
-def learned_oracle(noisy, theta):
+def learned_oracle(noisy, theta, nthreads):
     """The FP64 oracle of the learned path: the network's forward pass, then
     stage 2 (matching on the pilot, Wiener filter, windowed aggregation)."""
     import oracle
     from oracle import pilot
     pil = pilot.forward(theta, noisy[None], [SIGMA])[0]
     q = oracle.Params()
-    idx, _ = oracle.match(pil, N=q.patch, s=q.step, R=q.search_radius, K=q.k2, nthreads=os.cpu_count() or 1)
-    g, w = oracle.filter_wiener(noisy, pil, idx, SIGMA, N=q.patch, K=q.k2, nthreads=os.cpu_count() or 1)
+    idx, _ = oracle.match(pil, N=q.patch, s=q.step, R=q.search_radius, K=q.k2, nthreads=nthreads)
+    g, w = oracle.filter_wiener(noisy, pil, idx, SIGMA, N=q.patch, K=q.k2, nthreads=nthreads)
     return oracle.aggregate(g, w, idx, noisy.shape[0], noisy.shape[1], N=q.patch, beta=q.kaiser_beta)
 
 
@@ -296,7 +305,7 @@ def run_cpu_oracle(noisy_crop, nthreads):
     import oracle
     t0 = time.perf_counter()
     if LEARNED:
-        out = learned_oracle(noisy_crop, np.fromfile(THETA_FILE, dtype="<f4").astype(np.float64))
+        out = learned_oracle(noisy_crop, np.fromfile(THETA_FILE, dtype="<f4").astype(np.float64), nthreads)
     elif noisy_crop.ndim == 3:
         out = oracle.denoise_color(noisy_crop, SIGMA, oracle_params(), nthreads=nthreads)
     else:
@@ -518,7 +527,7 @@ def main():
     from paper_2103_10765_gb300 import gbm3d
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = gbm3d.params_default(PRESET)
+    p = gbm3d.params_default(PRESET).replace(match_engine=ENGINE)
     seeds = rank_seeds(rank)
     pairs = [make_inputs(s) for s in seeds]
     noisy = [torch.from_numpy(n).to(dev) for _, n in pairs]
@@ -573,7 +582,8 @@ def main():
 
     # output quality on this step's image (PSNR vs the clean scene)
     run(noisy[0])
-    psnr = float(10 * math.log10(1.0 / float(((out.cpu().double() - torch.from_numpy(pairs[0][0]).double())
+    out0 = out.cpu()  # the first timed image's result (the PSNR gate below compares it with the oracle)
+    psnr = float(10 * math.log10(1.0 / float(((out0.double() - torch.from_numpy(pairs[0][0]).double())
                                                 ** 2).mean())))
 
     # e2e: pinned host in -> denoise -> host out, per step
@@ -635,14 +645,43 @@ def main():
         e2e = {"value": job_mpix(world, args.steps, e2e_ms), "unit": "MPix/s",
                "h2d_bytes_per_step": hd.h2d_bytes, "d2h_bytes_per_step": hd.d2h_bytes}
 
+    # the other matching engine on the same images (the direct FP32 form of
+    # Sec. 2's distance next to the tensor-core form, or the reverse)
+    other = None
+    if not LEARNED and C == 1 and PRESET == 0:
+        q = p.replace(match_engine=1 if ENGINE != 1 else 0)
+        outq = torch.empty_like(out)
+        gbm3d.denoise(noisy[0], SIGMA, q, ws, outq)
+        barrier()
+        evq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(min(args.steps, 20))]
+        for i, (a, b) in enumerate(evq):
+            flush.zero_()
+            a.record(stream)
+            gbm3d.denoise(noisy[i % 3], SIGMA, q, ws, outq)
+            b.record(stream)
+        barrier()
+        qms = sum(a.elapsed_time(b) for a, b in evq)
+        gbm3d.denoise(noisy[0], SIGMA, q, ws, outq)
+        pq = float(10 * math.log10(1.0 / float(((outq.cpu().double() - torch.from_numpy(pairs[0][0]).double())
+                                                 ** 2).mean())))
+        other = {"engine": ("direct FP32 sum of squared differences (match_engine 1)" if q.match_engine == 1 else
+                            "tensor cores, certified exact re-rank (match_engine 0)"),
+                 "value": job_mpix(world, len(evq), max_over_ranks(qms, dev)), "unit": "MPix/s",
+                 "ms_per_step": qms / len(evq), "steps": len(evq), "psnr_db": pq,
+                 "same_output_bits": bool(torch.equal(outq.cpu(), out0))}
+        del outq
+
     # roofline of the dominant kernel, the block matcher (both stages' launches)
     mt = [float(np.mean(x)) if x is not None else 0.0 for x in match_ms]
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    derived_tflops = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    fma_scalar, fma_packed = gbm3d.measure_fp32_peak(dev)
+    peak_tflops = max(fma_scalar, fma_packed)
     geo = [gbm3d.params_stage(p, 1), gbm3d.params_stage(p, 2)]
     Ks = (p.k1, p.k2)
-    tc = [tc_supported(H, W, g.patch, g.step, p.search_radius, k) for g, k in zip(geo, Ks)]
+    tc = [ENGINE != 1 and tc_supported(H, W, g.patch, g.step, p.search_radius, k) for g, k in zip(geo, Ks)]
     # 2 N^2 FLOP per (reference, candidate), the Theorem-1 inner-product count
     flops = [2 * g.patch ** 2 * candidate_pairs(H, W, g.patch, g.step, p.search_radius) for g in geo]
     if LEARNED:  # stage 2's matching only
@@ -660,8 +699,10 @@ def main():
                                  "timed step (same stream; with translations the last one's), averaged over the "
                                  "timed steps",
                 "flop_per_launch": {"stage1": flops[0], "stage2": flops[1]},
-                "peak_note": f"FP32 ALU: {N_SM} SMs x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz "
-                             f"(SM clock from MEASURED_PEAKS.json, {peak_kind})"}
+                "peak_note": (f"FP32 ALU, measured on this GPU by the library's FMA-chain kernels (best of "
+                              f"fma.rn.f32 {fma_scalar:.1f} and fma.rn.f32x2 {fma_packed:.1f} TFLOP/s); derived "
+                              f"from unit counts: {N_SM} SMs x {FP32_LANES} lanes x 2 FLOP x {sm_max:.0f} MHz = "
+                              f"{derived_tflops:.1f}")}
     if all(tc) and not LEARNED:
         tc_flop = sum(tc_executed_flop(H, W, g.patch, g.step, p.search_radius) for g in geo) / 2
         f16_peak = float(peaks.get("bf16_tflops", 1900.0))  # FP16 and BF16 share the nominal dense rate
@@ -682,22 +723,41 @@ def main():
                                         "1024x1024" + ("" if H * W == 1024 ** 2 else ", scaled by the pixel count"))
 
     cpu = None
+    psnr_gap = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nt = os.cpu_count() or 1
-        crop = np.ascontiguousarray(pairs[0][1][..., :CPU_CROP, :CPU_CROP])
-        ref, secs = run_cpu_oracle(crop, nt)
-        gin = torch.from_numpy(crop).to(dev)
-        if LEARNED:
-            g = gbm3d.denoise_learned(gin, SIGMA, net, p).cpu().numpy()
+        what = ("FP64 oracle of the learned path (network forward, stage 2)" if LEARNED else
+                "two-stage FP64 oracle")
+        if CPU_CROP is None:
+            # the whole first timed image: its oracle result also gates the PSNR of
+            # the GPU output `out` computed above on that same image
+            ref, secs = run_cpu_oracle(np.ascontiguousarray(pairs[0][1]), nt)
+            g = out0.numpy()
+            clean = pairs[0][0].astype(np.float64)
+            npx, sample = H * W, f"{what} on the whole {H}x{W} first timed image"
         else:
-            g = (gbm3d.denoise(gin, SIGMA, p) if C == 1 else gbm3d.denoise_color(gin, SIGMA, p)).cpu().numpy()
-        clean = pairs[0][0][..., :CPU_CROP, :CPU_CROP].astype(np.float64)
+            crop = np.ascontiguousarray(pairs[0][1][..., :CPU_CROP, :CPU_CROP])
+            ref, secs = run_cpu_oracle(crop, nt)
+            gin = torch.from_numpy(crop).to(dev)
+            if LEARNED:
+                g = gbm3d.denoise_learned(gin, SIGMA, net, p).cpu().numpy()
+            else:
+                g = (gbm3d.denoise(gin, SIGMA, p) if C == 1 else gbm3d.denoise_color(gin, SIGMA, p)).cpu().numpy()
+            clean = pairs[0][0][..., :CPU_CROP, :CPU_CROP].astype(np.float64)
+            npx, sample = CPU_CROP * CPU_CROP, f"{what} on the top-left {CPU_CROP}x{CPU_CROP} crop of the workload image"
         pg = 10 * math.log10(1 / np.mean((g - clean) ** 2))
         po = 10 * math.log10(1 / np.mean((ref - clean) ** 2))
-        cpu = {"value": CPU_CROP * CPU_CROP / secs / 1e6, "unit": "MPix/s", "cores": nt, "kind": "oracle",
-               "sample": ("FP64 oracle of the learned path (network forward, stage 2)" if LEARNED else
-                          "two-stage FP64 oracle") + f" on the top-left {CPU_CROP}x{CPU_CROP} crop of the workload image",
-               "seconds": secs, "psnr_gap_db_on_sample": abs(pg - po)}
+        psnr_gap = {"value_db": pg - po, "gpu_db": pg, "oracle_db": po,
+                    "on": "the whole first timed image" if CPU_CROP is None else
+                          f"the top-left {CPU_CROP}x{CPU_CROP} crop of the first timed image, denoised on its own"}
+        # single-threaded oracle on a smaller crop (the per-core rate)
+        st_crop = np.ascontiguousarray(pairs[0][1][..., :ST_CROP, :ST_CROP])
+        _, st_secs = run_cpu_oracle(st_crop, 1)
+        cpu = {"value": npx / secs / 1e6, "unit": "MPix/s", "cores": nt, "kind": "oracle", "sample": sample,
+               "seconds": secs,
+               "single_thread": {"value": ST_CROP * ST_CROP / st_secs / 1e6, "unit": "MPix/s", "cores": 1,
+                                 "sample": f"{what} on the top-left {ST_CROP}x{ST_CROP} crop, one thread",
+                                 "seconds": st_secs}}
 
     if LEARNED:
         # the network's 11 launches (noise level, weight packing, input, its 8
@@ -712,12 +772,15 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "image": [H, W], "channels": C, "sigma": SIGMA, "parallelism": "replicas",
                        "l2": "flushed between steps (256 MiB write outside the timed events)"},
-            "psnr_db": psnr, "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline,
+            "psnr_db": psnr, "psnr_gap_db": psnr_gap, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk.summary(),
             "step_ms": {"min": min(step_ms), "median": float(np.median(step_ms)), "max": max(step_ms)},
         }
         if plain:
             line["plain_form"] = plain
+        if other:
+            line["other_matching_form"] = other
         print(json.dumps(line))
     if world > 1:
         torch.distributed.barrier()

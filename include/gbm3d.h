@@ -236,6 +236,15 @@ int gbm3d_denoise_color(const float *noisy, int H, int W, int pitch, long long p
  * NULL, ECUDA if the read fails. */
 int gbm3d_match_stats(unsigned long long *timeouts, unsigned long long *rematched);
 
+/* Measurement of the roofline's FP32 denominator (no counterpart in the
+ * paper): runs FMA chains on every SM of the current device (8 CTAs of 256
+ * threads per SM, 8 independent chains per thread) and returns the best of
+ * three timed runs, in TFLOP/s (2 FLOP per FMA), for scalar fma.rn.f32
+ * (*scalar_tflops) and packed fma.rn.f32x2 (*packed_tflops).  Synchronous
+ * (waits for the runs), allocates nothing.  EINVAL for a NULL pointer, ECUDA
+ * if a launch fails. */
+int gbm3d_measure_fp32_peak(double *scalar_tflops, double *packed_tflops, gbm3d_stream_t stream);
+
 /* Measurement hook.  events: NULL (off, the default) or an array of four
  * cudaEvent_t created by the caller on the current device.  While set, each
  * gbm3d_denoise on this host thread records events[0] / events[1] on its

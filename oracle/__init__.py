@@ -71,8 +71,8 @@ def _declare(lib):
     lib.orc_idwt1.argtypes = [_f64p, _f64p, c_int, c_int, _f64p]
     lib.orc_upsilon.argtypes = [c_double, c_double]
     lib.orc_upsilon.restype = c_double
-    lib.orc_dwt3.argtypes = [_f64p, c_int, c_int, c_int, c_int, vp]
-    lib.orc_idwt3.argtypes = [_f64p, c_int, c_int, c_int, c_int]
+    lib.orc_dwt3.argtypes = [_f64p, c_int, c_int, c_int, c_int, vp, c_int]
+    lib.orc_idwt3.argtypes = [_f64p, c_int, c_int, c_int, c_int, c_int]
     lib.orc_filter_ht.argtypes = [_f64p, c_int, c_int, _i32p, c_int, c_int, c_int, c_int, c_double, c_int, c_int,
                                   c_double, c_double, c_double, _f64p, _f64p, c_int]
     lib.orc_dct2.argtypes = [_f64p, c_int, c_int]
@@ -205,7 +205,7 @@ def upsilon(a, lam):
     return float(_get().orc_upsilon(float(a), float(lam)))
 
 
-def dwt3(v, L=3, tau=None):
+def dwt3(v, L=3, tau=None, nthreads=1):
     """Forward 3-D transform of v[y][x][z] (Mallat layout), thresholded if tau given."""
     v = _f64(v).copy()
     Y, X, Z = v.shape
@@ -213,14 +213,14 @@ def dwt3(v, L=3, tau=None):
     if tau is not None:
         t = _f64(tau)
         tp = t.ctypes.data_as(ctypes.c_void_p)
-    _check(_get().orc_dwt3(v, Y, X, Z, L, tp), "orc_dwt3")
+    _check(_get().orc_dwt3(v, Y, X, Z, L, tp, nthreads), "orc_dwt3")
     return v
 
 
-def idwt3(v, L=3):
+def idwt3(v, L=3, nthreads=1):
     v = _f64(v).copy()
     Y, X, Z = v.shape
-    _check(_get().orc_idwt3(v, Y, X, Z, L), "orc_idwt3")
+    _check(_get().orc_idwt3(v, Y, X, Z, L, nthreads), "orc_idwt3")
     return v
 
 

@@ -371,16 +371,16 @@ static int dims_ok(int Y, int X, int Z, int L)
 }
 
 /* Exported: forward (optionally thresholded) and inverse 3-D transforms. */
-int orc_dwt3(double *v, int Y, int X, int Z, int L, const double *tau)
+int orc_dwt3(double *v, int Y, int X, int Z, int L, const double *tau, int nthreads)
 {
     if (!v || !dims_ok(Y, X, Z, L)) return ORC_EINVAL;
-    return dwt3_forward(v, Y, X, Z, L, tau, 1);
+    return dwt3_forward(v, Y, X, Z, L, tau, nthreads > 0 ? nthreads : 1);
 }
 
-int orc_idwt3(double *v, int Y, int X, int Z, int L)
+int orc_idwt3(double *v, int Y, int X, int Z, int L, int nthreads)
 {
     if (!v || !dims_ok(Y, X, Z, L)) return ORC_EINVAL;
-    return dwt3_inverse(v, Y, X, Z, L, 1);
+    return dwt3_inverse(v, Y, X, Z, L, nthreads > 0 ? nthreads : 1);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgbm3d.so")
-SOURCES = ["api.cu", "match.cu", "match_tc.cu", "match_box.cu", "ht.cu", "wiener.cu", "aggregate.cu", "pnp.cu", "pilot.cu"]
+SOURCES = ["api.cu", "match.cu", "match_tc.cu", "match_box.cu", "ht.cu", "wiener.cu", "aggregate.cu", "pnp.cu", "pilot.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
     lib.gbm3d_denoise.argtypes = [vp, ci, ci, ci, cf, P, vp, vp, vp]
     lib.gbm3d_aggregate_noalloc.argtypes = [vp, vp, vp, ci, ci, ci, ci, P, cf, vp, vp]
     lib.gbm3d_set_match_events.argtypes = [vp]
+    lib.gbm3d_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.gbm3d_workspace_bytes_color.argtypes = [ci, ci, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.gbm3d_denoise_color.argtypes = [vp, ci, ci, ci, ctypes.c_longlong, cf, P, vp, vp, vp]
     lib.gbm3d_match_stats.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
@@ -105,7 +106,7 @@ def load(build_if_missing: bool = True):
                  "gbm3d_pnp_plan_create", "gbm3d_pnp_run", "gbm3d_pnp_plan_destroy", "gbm3d_pnp_gemm_config",
                  "gbm3d_pilot_param_count", "gbm3d_pilot_workspace_bytes", "gbm3d_pilot_forward",
                  "gbm3d_pilot_loss_grad", "gbm3d_pilot_train_step", "gbm3d_workspace_bytes_learned",
-                 "gbm3d_denoise_learned"):
+                 "gbm3d_denoise_learned", "gbm3d_measure_fp32_peak"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -219,6 +220,16 @@ def set_match_events(events=None):
     arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
     _match_events_keep = (arr, events)
     _check(load().gbm3d_set_match_events(ctypes.cast(arr, ctypes.c_void_p)))
+
+
+def measure_fp32_peak(device=None):
+    """(scalar, packed) FP32 FMA throughput of the device in TFLOP/s,
+    measured by the library's FMA-chain kernels (synchronous)."""
+    dev = torch.device(device or "cuda")
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().gbm3d_measure_fp32_peak(ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
+    return a.value, b.value
 
 
 def match_stats():
