@@ -75,6 +75,7 @@ def _declare(lib):
     lib.orc_idwt3.argtypes = [_f64p, c_int, c_int, c_int, c_int, c_int]
     lib.orc_filter_ht.argtypes = [_f64p, c_int, c_int, _i32p, c_int, c_int, c_int, c_int, c_double, c_int, c_int,
                                   c_double, c_double, c_double, _f64p, _f64p, c_int]
+    lib.orc_tv_weights.argtypes = [_f64p, c_int, c_int, c_int, c_double, _f64p]
     lib.orc_dct2.argtypes = [_f64p, c_int, c_int]
     lib.orc_haar.argtypes = [_f64p, c_int, c_int]
     lib.orc_filter_wiener.argtypes = [_f64p, _f64p, c_int, c_int, _i32p, c_int, c_int, c_int, c_double, c_double,
@@ -82,7 +83,7 @@ def _declare(lib):
     lib.orc_bessel_i0.argtypes = [c_double]
     lib.orc_bessel_i0.restype = c_double
     lib.orc_kaiser.argtypes = [c_int, c_double, _f64p]
-    lib.orc_aggregate.argtypes = [_f64p, _f64p, _i32p, c_int, c_int, c_int, c_int, c_int, c_double, _f64p]
+    lib.orc_aggregate.argtypes = [_f64p, _f64p, _i32p, c_int, c_int, c_int, c_int, c_int, c_double, _f64p, c_int]
     lib.orc_denoise.argtypes = [_f64p, c_int, c_int, c_double, ctypes.POINTER(_Params), _f64p, vp, c_int]
     lib.orc_max_threads.argtypes = []
     lib.orc_opp.argtypes = [_f64p, ctypes.c_size_t, c_int, _f64p]
@@ -235,6 +236,16 @@ def filter_ht(Z, idx, sigma, By, Bx, N=8, K=16, L=3, C=2, tau_a=3.6, tau_b=0.3, 
     return groups, w
 
 
+def tv_weights(groups, eps_w=1e-8):
+    """w[g] = 1 / max(TV(groups[g]), eps_w) for groups [G, K, N, N] (the
+    stage-1 weight rule of orc_filter_ht)."""
+    groups = _f64(groups)
+    G, K, N = groups.shape[0], groups.shape[1], groups.shape[2]
+    w = np.zeros(G)
+    _check(_get().orc_tv_weights(groups, G, K, N, float(eps_w), w), "orc_tv_weights")
+    return w
+
+
 def dct2(blk, inverse=False):
     b = _f64(blk).copy()
     _check(_get().orc_dct2(b, b.shape[0], int(inverse)), "orc_dct2")
@@ -269,14 +280,17 @@ def kaiser(N, beta):
     return out
 
 
-def aggregate(groups, w, idx, H, W, N=8, beta=0.0):
+def aggregate(groups, w, idx, H, W, N=8, beta=0.0, require_cover=True):
+    """Weighted aggregation; with require_cover=False pixels that no block
+    covers are 0 instead of an error (aggregating a subset of the groups)."""
     groups = _f64(groups)
     w = _f64(w)
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     G = w.size
     K = idx.size // G
     out = np.zeros((H, W))
-    _check(_get().orc_aggregate(groups, w, idx, G, K, H, W, N, float(beta), out), "orc_aggregate")
+    _check(_get().orc_aggregate(groups, w, idx, G, K, H, W, N, float(beta), out, int(require_cover)),
+           "orc_aggregate")
     return out
 
 

@@ -383,6 +383,23 @@ int orc_idwt3(double *v, int Y, int X, int Z, int L, int nthreads)
     return dwt3_inverse(v, Y, X, Z, L, nthreads > 0 ? nthreads : 1);
 }
 
+/* w = 1 / max(TV(u), eps_w) for one filtered group u[r][a][b] (N x N x K):
+ * TV is the sum of |forward differences| along a, b and r inside the
+ * group, without wrap (Sec. 3.1; reading: anisotropic L1). */
+static double tv_weight(const double *o, int N, int K, double eps_w)
+{
+    double tv = 0.0;
+    for (int r = 0; r < K; r++)
+        for (int a = 0; a < N; a++)
+            for (int b = 0; b < N; b++) {
+                double c = o[(r * N + a) * N + b];
+                if (a + 1 < N) tv += fabs(o[(r * N + a + 1) * N + b] - c);
+                if (b + 1 < N) tv += fabs(o[(r * N + a) * N + b + 1] - c);
+                if (r + 1 < K) tv += fabs(o[((r + 1) * N + a) * N + b] - c);
+            }
+    return 1.0 / (tv > eps_w ? tv : eps_w);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Stage 1: global volume hard thresholding (Sec. 3, Sec. 3.1).
  *
@@ -452,19 +469,19 @@ int orc_filter_ht(const double *Z, int H, int W, const int32_t *idx, int By, int
                 for (int a = 0; a < N; a++)
                     for (int b = 0; b < N; b++)
                         o[(r * N + a) * N + b] = U[((size_t)(p * N + a) * Xd + (q * N + b)) * Zd + r];
-            double tv = 0.0;
-            for (int r = 0; r < K; r++)
-                for (int a = 0; a < N; a++)
-                    for (int b = 0; b < N; b++) {
-                        double c = o[(r * N + a) * N + b];
-                        if (a + 1 < N) tv += fabs(o[(r * N + a + 1) * N + b] - c);
-                        if (b + 1 < N) tv += fabs(o[(r * N + a) * N + b + 1] - c);
-                        if (r + 1 < K) tv += fabs(o[((r + 1) * N + a) * N + b] - c);
-                    }
-            w[g] = 1.0 / (tv > eps_w ? tv : eps_w);
+            w[g] = tv_weight(o, N, K, eps_w);
         }
     free(V); free(S); free(U); free(tau);
     return st;
+}
+
+/* Exported: the weights w[g] = 1 / max(TV(u^g), eps_w) of G filtered groups
+ * groups[g][r][a][b] (the rule orc_filter_ht applies). */
+int orc_tv_weights(const double *groups, int G, int K, int N, double eps_w, double *w)
+{
+    if (!groups || !w || G <= 0 || K <= 0 || N <= 0) return ORC_EINVAL;
+    for (int g = 0; g < G; g++) w[g] = tv_weight(groups + (size_t)g * K * N * N, N, K, eps_w);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -643,7 +660,7 @@ int orc_kaiser(int N, double beta, double *out)
  * window (stage 2, beta > 0) every block value and its support are also
  * multiplied by kappa[a] kappa[b]. */
 int orc_aggregate(const double *groups, const double *w, const int32_t *idx, int G, int K,
-                  int H, int W, int N, double beta, double *out)
+                  int H, int W, int N, double beta, double *out, int require_cover)
 {
     if (!groups || !w || !idx || !out || G <= 0 || K <= 0 || H < N || W < N || N <= 0 || N > 64)
         return ORC_EINVAL;
@@ -666,7 +683,7 @@ int orc_aggregate(const double *groups, const double *w, const int32_t *idx, int
     int st = ORC_OK;
     for (size_t e = 0; e < (size_t)H * W; e++) {
         if (den[e] > 0.0) out[e] = num[e] / den[e];
-        else { out[e] = 0.0; st = ORC_EINVAL; } /* a pixel no block covers */
+        else { out[e] = 0.0; if (require_cover) st = ORC_EINVAL; } /* a pixel no block covers */
     }
     free(num); free(den);
     return st;
@@ -730,7 +747,7 @@ static int stage1(const double *Z, int H, int W, double sigma, const orc_params 
         if (st == ORC_OK)
             st = orc_filter_ht(Z, H, W, idx, By, Bx, N, K, sigma, p->levels, p->cycle_spins, p->tau_a,
                                p->tau_b, p->eps_w, gr, w, nt);
-        if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, 0.0, out);
+        if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, 0.0, out, 1);
     }
     free(idx); free(gr); free(w);
     return st;
@@ -748,7 +765,7 @@ static int stage2(const double *Z, const double *Y1, int H, int W, double sigma,
     if (idx && gr && w) {
         st = orc_match(Y1, H, W, N, s, p->search_radius, K, idx, NULL, nt);
         if (st == ORC_OK) st = orc_filter_wiener(Z, Y1, H, W, idx, (int)G, N, K, sigma, p->eps_w, gr, w, nt);
-        if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, p->kaiser_beta, out);
+        if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, p->kaiser_beta, out, 1);
     }
     free(idx); free(gr); free(w);
     return st;
@@ -848,10 +865,10 @@ static int stage_color(const double *Zo, const double *Y1o, int H, int W, double
         if (!Y1o) {
             st = orc_filter_ht(Zo + c * n, H, W, idx, By, Bx, N, K, sc, p->levels, p->cycle_spins, p->tau_a,
                                p->tau_b, p->eps_w, gr, w, nt);
-            if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, 0.0, out + c * n);
+            if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, 0.0, out + c * n, 1);
         } else {
             st = orc_filter_wiener(Zo + c * n, Y1o + c * n, H, W, idx, (int)G, N, K, sc, p->eps_w, gr, w, nt);
-            if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, p->kaiser_beta, out + c * n);
+            if (st == ORC_OK) st = orc_aggregate(gr, w, idx, (int)G, K, H, W, N, p->kaiser_beta, out + c * n, 1);
         }
     }
     free(idx); free(gr); free(w);

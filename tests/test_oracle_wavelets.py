@@ -183,3 +183,16 @@ def test_filter_ht_zero_threshold_is_identity(orc):
         for r in range(16):
             i, j = divmod(int(idx[g, r]), 24)
             np.testing.assert_allclose(groups[g, r], Zimg[i:i + 8, j:j + 8], atol=1e-12)
+
+
+def test_tv_weights_closed_form(orc):
+    """w = 1 / TV with TV the anisotropic L1 forward-difference sum inside the
+    group: an interior unit impulse has six unit differences (TV = 6), an
+    impulse of 2 in a corner three differences of 2 (TV = 6); a constant
+    group has TV = 0 and takes the eps guard."""
+    g = np.zeros((3, 16, 8, 8))
+    g[0, 5, 3, 4] = 1.0
+    g[1, 0, 0, 0] = 2.0
+    g[2] = 0.7
+    w = orc.tv_weights(g, eps_w=1e-8)
+    np.testing.assert_allclose(w, [1 / 6, 1 / 6, 1e8], rtol=1e-12)
