@@ -48,9 +48,14 @@
 // that thresholds tighten early.  Every mbarrier wait is bounded; on a
 // timeout the tile falls back to the direct kernel.  Device counters record
 // timeouts and re-matched references.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <float.h>
 #include <limits.h>
+
+#include <mutex>
+#include <string.h>
 
 #include "internal.cuh"
 
@@ -134,6 +139,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile 
     if (err) *err = 1;
     atomicAdd(&g_tc_timeouts, 1ull);
     return false;
+}
+
+// One tiled TMA load of a 2-D box of the image (coordinates: column x,
+// row y; x * 4 bytes is a multiple of 16) into shared memory at dst,
+// completing on the mbarrier at bar, which expects `bytes`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar,
+                                            uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                 "[%4];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -343,7 +361,8 @@ namespace {
 template <int LP, int LT>
 __global__ void __launch_bounds__(kCta, 2)
 k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
-           TcLayout lay, int32_t *__restrict__ idx, float *__restrict__ dist)
+           TcLayout lay, int32_t *__restrict__ idx, float *__restrict__ dist,
+           const __grid_constant__ CUtensorMap tmap, int use_tma)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -359,7 +378,12 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     const int nch = (UH + kChunkRows - 1) / kChunkRows;
     const int rrows = nch * kChunkRows + kPatch - 1; // region rows read by the chunks (<= lay.reg_rows)
 
-    float *reg = reinterpret_cast<float *>(smem + lay.reg);
+    // region row y, column x (image pixel (uy0 + y, ux0 + x)) at reg[y * kRegStride + x];
+    // a TMA box starts at the 16-byte aligned column xa <= ux0, so the
+    // region begins ux0 - xa floats into the buffer (the host admits TMA only
+    // where the columns read, x <= UW + 6, stay inside the box)
+    const int xa = ux0 & ~3;
+    float *reg = reinterpret_cast<float *>(smem + lay.reg) + (use_tma ? ux0 - xa : 0);
     // per candidate of the last three chunks: centred norm, -8 mean, -(8 mean + sum / 4)
     float *nbs = reinterpret_cast<float *>(smem + lay.nb);  // [3][kNc]
     float *nbm = reinterpret_cast<float *>(smem + lay.nbm); // [3][kNc]
@@ -373,6 +397,7 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     volatile int *s_err = reinterpret_cast<volatile int *>(smem + lay.misc + 36);
     float *s_red = reinterpret_cast<float *>(smem + lay.misc + 64); // [4]
     int *s_order = reinterpret_cast<int *>(smem + lay.misc + 128);  // chunk processing order
+    uint64_t *mb_tma = reinterpret_cast<uint64_t *>(smem + lay.misc + 56); // region loaded
     const uint32_t sbase = smem_u32(smem);
 
     if (warp == 0) tmem_alloc(smem_u32(s_tmem), kTmemCols);
@@ -383,15 +408,20 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
             mbar_init(smem_u32(&mb_used[b]), kThreads / 32);
         }
         mbar_init(smem_u32(mb_built), kThreads);
+        mbar_init(smem_u32(mb_tma), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_err = 0;
+        // the search region: one TMA box of lay.reg_rows x kRegStride pixels
+        // from (xa, uy0), zero outside the image
+        if (use_tma)
+            tma_load_2d(smem_u32(smem + lay.reg), &tmap, xa, uy0, smem_u32(mb_tma),
+                        (uint32_t)(lay.reg_rows * kRegStride * 4));
     }
 
     // ---- search region (raw pixels, zero outside the image) and its mean
     const int vrows = UH + kPatch - 1, vcols = UW + kPatch - 1; // pixels of the union's blocks
     float sum = 0.f;
-    { // eight loads per thread in flight before their stores (the same element
-      // order per thread, so the same sum)
+    if (!use_tma) { // eight loads per thread in flight before their stores
         constexpr int kLd = 8;
         const int total = rrows * kRegStride;
         for (int e0 = tid; selw && e0 < total; e0 += kLd * kThreads) {
@@ -414,12 +444,21 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
             }
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-    if (lane == 0 && selw) s_red[warp] = sum;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    bool tma_ok = true;
+    if (use_tma) { // every thread waits for the box (bounded), then the sum
+        tma_ok = __syncthreads_and(mbar_wait(smem_u32(mb_tma), 0, nullptr));
+        for (int e = tid; tma_ok && selw && e < vrows * vcols; e += kThreads) {
+            const int y = e / vcols, x = e - y * vcols;
+            sum += reg[y * kRegStride + x];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    if (lane == 0 && selw) s_red[warp] = sum;
+    __syncthreads();
     const uint32_t tmem = *s_tmem;
     float mu = 0.f;
     for (int w = 0; w < kThreads / 32; w++) mu += s_red[w];
@@ -442,7 +481,8 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     // so block-centred values stay below 2^14, inside FP16 range
     const float sc = maxabs > 0.f ? ldexpf(1.f, 13 - ex) : 1.f;
     const float vt = maxabs * sc * 1.0001f; // bound on every tile-centred scaled value
-    const bool bad = !isfinite(mu) || !isfinite(maxabs) || ex > 100 || ex < -100 || !(fabsf(mu) * sc < 1e30f);
+    const bool bad = !tma_ok || !isfinite(mu) || !isfinite(maxabs) || ex > 100 || ex < -100 ||
+                     !(fabsf(mu) * sc < 1e30f);
     const float nms = -mu * sc; // fma(x, sc, nms) = (x - mu) sc, rounded once
 
     // ---- this thread's reference (tensor-memory lane tid) and its window
@@ -549,7 +589,9 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
     // and their per-candidate terms into buffer par
     auto build = [&](int ch, int par) {
         const int n = tid;
-        const int rowl = ch * kChunkRows + (n >> 6), col = n & (kChunkCols - 1);
+        // columns past the union (never inside a window) repeat its last
+        // column, so no read leaves the region's columns 0 .. UW + 6
+        const int rowl = ch * kChunkRows + (n >> 6), col = min(n & (kChunkCols - 1), UW - 1);
         float n2, mean, ssum;
         centre(reg + rowl * kRegStride + col, true, lay.b_hi, lay.b_lo, n, n2, mean, ssum);
         nbs[par * kNc + n] = n2;
@@ -830,6 +872,9 @@ k_match_tc(const float *__restrict__ img, int H, int W, int pitch, int By, int B
             }
         }
     }
+    // a region load that never completed may still land: wait for it (again
+    // bounded) before the shared memory is released
+    if (use_tma && !tma_ok && tid == 0) mbar_wait(smem_u32(mb_tma), 0, nullptr);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -889,17 +934,57 @@ bool match_tc_supported(int H, int W, int N, int s, int R, int K)
     return t.bytes <= 227 * 1024;
 }
 
+// cuTensorMapEncodeTiled from the driver (through the runtime, so the
+// library needs no link to libcuda), looked up once.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// Tensor map of the image for the region loads: 2-D FP32 (W columns, H rows,
+// row pitch `pitch` floats), box kRegStride x reg_rows, zero fill outside.
+// False where TMA does not apply: a base address not 16-byte aligned, a row
+// pitch that is not a multiple of 16 bytes, a box past the 256 limit, or a
+// union wider than the box holds after the up-to-3-column alignment shift.
+static bool region_tensor_map(const float *img, int H, int W, int pitch, int s, int R, const TcLayout &lay,
+                              CUtensorMap *map)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || ((uintptr_t)img & 15) || (pitch & 3) || lay.reg_rows > 256) return false;
+    if ((kTileX - 1) * s + 2 * R + 1 + (kPatch - 1) + 3 > kRegStride) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kRegStride, (cuuint32_t)lay.reg_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(img), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_match_tc(const float *img, int H, int W, int pitch, int By, int Bx, int s, int R, int K,
                             int32_t *idx, float *dist, cudaStream_t st)
 {
     const TcLayout lay = tc_layout(H, s, R, K);
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof tmap);
+    const int use_tma = region_tensor_map(img, H, W, pitch, s, R, lay, &tmap) ? 1 : 0;
     // the operand tiles and pending keys alone take over a third of the SM's
     // shared memory: at most two CTAs per SM, 2 x 256 tensor-memory columns
     auto kern = lay.L == 16 ? k_match_tc<16, 16> : k_match_tc<32, 32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.bytes);
     if (e != cudaSuccess) return e;
     dim3 grid((Bx + kTileX - 1) / kTileX, (By + kTileY - 1) / kTileY);
-    kern<<<grid, kCta, lay.bytes, st>>>(img, H, W, pitch, By, Bx, s, R, K, lay, idx, dist);
+    kern<<<grid, kCta, lay.bytes, st>>>(img, H, W, pitch, By, Bx, s, R, K, lay, idx, dist, tmap, use_tma);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_match_fix(img, H, W, pitch, By, Bx, s, R, K, idx, dist, st);
 }
