@@ -265,8 +265,10 @@ int gbm3d_set_match_events(void *events);
  *   u <- u + x - v
  * from v = y, u = 0; the result is v after `iters` iterations.  The x-update
  * is exact up to FP32 rounding: H^T H + rho I is diagonal in the separable
- * discrete Hartley basis, applied as dense FP32 matrix products (any image
- * side that is a multiple of 8).  A plan binds a batch of images of uneven
+ * discrete Hartley basis, applied as dense matrix products on the tensor
+ * cores with FP32-accurate results (each operand split into two tf32 parts,
+ * three products accumulated in FP32; any image side that is a multiple of
+ * 8).  A plan binds a batch of images of uneven
  * sizes, each with its own sigma_n, to caller buffers. */
 typedef struct {
     int iters;     /* ADMM iterations (>= 1)                                   */
@@ -313,7 +315,7 @@ int gbm3d_pnp_run(gbm3d_pnp_plan plan, gbm3d_stream_t stream);
  * is accepted.  Always GBM3D_OK. */
 int gbm3d_pnp_plan_destroy(gbm3d_pnp_plan plan);
 
-/* The tile shapes (0..3: 128x128, 128x64, 64x128, 64x64) the plan uses for
+/* The tile shapes (0: 128x128, 1: 128x64 outputs per CTA) the plan uses for
  * image `image`'s products with contraction length H and W. */
 int gbm3d_pnp_gemm_config(gbm3d_pnp_plan plan, int image, int *cfg_k_h, int *cfg_k_w);
 

@@ -16,10 +16,12 @@
 // separable transform T(X) = C_H X C_W (C_N[k][n] = cas(2 pi k n / N),
 // symmetric, C_N C_N = N I) therefore diagonalises the 2-D blur, and
 //   x = T( T(b) / ((lam_H[k] lam_W[l])^2 + rho) ) / (H W).
-// Each T is two dense FP32 matrix products, so any image size works (sizes
-// with large prime factors included) at 8 H W (H + W) FLOP per x-update.
-// The products run in a register-tiled SIMT kernel; an autotuner times four
-// tile shapes per (M, N, K) on the plan's own buffers and keeps the fastest.
+// Each T is two dense matrix products, so any image size works (sizes with
+// large prime factors included) at 8 H W (H + W) FLOP per x-update.  The
+// products run on the tensor cores (tcgen05.mma kind::tf32, each FP32
+// operand split into two tf32 parts, three products accumulated in FP32 in
+// tensor memory); an autotuner times the two tile shapes per (M, N, K) on
+// the plan's own buffers and keeps the faster.
 //
 // Per iteration and image: 4 products (the eigenvalue division and the
 // "x + u" of the denoiser input fused into their epilogues), one G-BM3D
@@ -43,12 +45,17 @@
 namespace gbm3d {
 namespace {
 
-// ---- dense FP32 products ---------------------------------------------------
-// C = epilogue(A[M][K] B[K][N]), row-major with leading dimensions.  CTA tile
-// BM x BN, 256 threads as 16 x 16, each with a TM x TN micro-tile split in two
-// halves (rows ty*TM/2 + i and BM/2 + ty*TM/2 + i, likewise columns) so that
-// the shared-memory reads of a half-warp are contiguous.  BK = 8, one tile of
-// A and B prefetched into registers while the current one is multiplied.
+// ---- dense products on the tensor cores ------------------------------------
+// C = epilogue(A[M][K] B[K][N]) with FP32 inputs and an FP32-accurate result
+// from the 5th-generation tensor cores: every operand is split as
+// v = hi + lo with hi = tf32(v) and lo = tf32(v - hi) (tf32: 10 stored
+// mantissa bits, round to nearest), and the three products hi.hi + hi.lo +
+// lo.hi accumulate in FP32 in tensor memory (tcgen05.mma kind::tf32); the
+// dropped lo.lo term is below 2^-22 of |a| |b|.  CTA tile 128 x BN (BN = 128
+// or 64), K in stages of 32 with two stages in flight; 8 warps split the
+// operands as they load them (thread = one row of the K-major tile), one
+// thread issues the 12 MMAs of a stage, and after the last stage the warps
+// read the accumulators back (tcgen05.ld) and apply the epilogue.
 struct Epi {
     int mode;              // 0: alpha acc; 1: acc / ((lamM[r] lamN[c])^2 + rho); 2: alpha acc + add[r][c]
     float alpha, rho;
@@ -57,115 +64,280 @@ struct Epi {
     int ldadd;
 };
 
-template <int BM, int BN, int TM, int TN>
-__global__ void __launch_bounds__(256)
-k_sgemm(const float *__restrict__ A, int lda, const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
-        int M, int N, int K, Epi epi)
+constexpr int kGM = 128, kGK = 32, kGThreads = 256;
+constexpr int kGSpin = 1 << 22; // bounded mbarrier polls
+
+__device__ unsigned long long g_gemm_timeouts = 0; // bounded waits of the product kernel that gave up
+
+__device__ __forceinline__ uint32_t g_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool g_mbar_test(uint32_t a, uint32_t parity)
 {
-    constexpr int BK = 8, HM = TM / 2, HN = TN / 2;
-    constexpr int LA = BM * BK / 256, LB = BN * BK / 256; // elements each thread loads per tile
-    __shared__ __align__(16) float As[2][BK][BM];
-    __shared__ __align__(16) float Bs[2][BK][BN];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    // load maps: A as BM rows of BK/LA groups; B as BK rows of BN/LB groups
-    const int ar = tid / (BK / LA), ak = (tid % (BK / LA)) * LA;
-    const int bk = tid / (BN / LB), bn = (tid % (BN / LB)) * LB;
-    float ra[LA], rb[LB];
-    auto load = [&](int k0) {
-#pragma unroll
-        for (int i = 0; i < LA; i++) {
-            const int r = m0 + ar, k = k0 + ak + i;
-            ra[i] = (r < M && k < K) ? __ldg(A + (size_t)r * lda + k) : 0.f;
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` (at most kGSpin polls); false on a timeout.
+__device__ __forceinline__ bool g_mbar_wait(uint32_t a, uint32_t parity)
+{
+    for (int it = 0; it < kGSpin; it++)
+        if (g_mbar_test(a, parity)) return true;
+    return false;
+}
+
+// K-major operand tile of ROWS x kGK tf32 in core matrices of 8 rows x 16
+// bytes: (row r, K chunk c of 4 values) at c * ROWS * 16 + r * 16, i.e.
+// leading (K) byte offset ROWS * 16, stride (8-row) byte offset 128.
+template <int ROWS>
+__device__ __forceinline__ uint64_t g_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((ROWS * 16) >> 4) << 16) | ((uint64_t)(128 >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+
+// Splits 4 values into tf32 high and low parts and stores both 16-byte rows.
+__device__ __forceinline__ void split4(float4 v, unsigned char *hi, unsigned char *lo)
+{
+    const uint32_t h0 = to_tf32(v.x), h1 = to_tf32(v.y), h2 = to_tf32(v.z), h3 = to_tf32(v.w);
+    const uint32_t l0 = to_tf32(v.x - __uint_as_float(h0)), l1 = to_tf32(v.y - __uint_as_float(h1));
+    const uint32_t l2 = to_tf32(v.z - __uint_as_float(h2)), l3 = to_tf32(v.w - __uint_as_float(h3));
+    *reinterpret_cast<uint4 *>(hi) = make_uint4(h0, h1, h2, h3);
+    *reinterpret_cast<uint4 *>(lo) = make_uint4(l0, l1, l2, l3);
+}
+
+// Instruction descriptor of tcgen05.mma kind::tf32: D FP32 (bits 4-5 = 1),
+// A and B TF32 (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+template <int BN>
+__host__ __device__ constexpr uint32_t g_idesc()
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kGM >> 4) << 24);
+}
+
+template <int BN>
+constexpr int g_smem_bytes()
+{
+    return 2 * (2 * kGM * kGK * 4 + 2 * BN * kGK * 4) + 64;
+}
+
+// B is read as B[k][n] (b_kmajor = 0: one scalar load per value, coalesced
+// across the tile's columns) or, for a symmetric B, as B[n][k] (b_kmajor = 1:
+// rows along K, like A).  M, N, K are multiples of 8.  A wait that gives up
+// fills the CTA's output tile with NaN (and counts g_gemm_timeouts), so a
+// failure cannot pass unseen.
+template <int BN>
+__global__ void __launch_bounds__(kGThreads, 1)
+k_gemm_tc(const float *__restrict__ A, int lda, const float *__restrict__ B, int ldb, int b_kmajor,
+          float *__restrict__ C, int ldc, int M, int N, int K, Epi epi)
+{
+    constexpr int kA = kGM * kGK * 4, kB = BN * kGK * 4; // bytes of one split part of a stage
+    constexpr int kStage = 2 * kA + 2 * kB;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *ready = reinterpret_cast<uint64_t *>(smem + 2 * kStage); // [2] operands built (kGThreads arrivals)
+    uint64_t *done = ready + 2;                                         // [2] products of the stage complete
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 2);
+    volatile int *s_err = reinterpret_cast<volatile int *>(s_tmem + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * BN;
+    const int nk = (K + kGK - 1) / kGK;
+    const uint32_t sb = g_smem_u32(smem);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(g_smem_u32(s_tmem)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(g_smem_u32(&ready[b])), "r"(kGThreads)
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(g_smem_u32(&done[b])), "r"(1) : "memory");
         }
-#pragma unroll
-        for (int i = 0; i < LB; i++) {
-            const int k = k0 + bk, c = n0 + bn + i;
-            rb[i] = (k < K && c < N) ? __ldg(B + (size_t)k * ldb + c) : 0.f;
-        }
-    };
-    auto store = [&](int s) {
-#pragma unroll
-        for (int i = 0; i < LA; i++) As[s][ak + i][ar] = ra[i];
-#pragma unroll
-        for (int i = 0; i < LB; i++) Bs[s][bk][bn + i] = rb[i];
-    };
-    float acc[TM][TN];
-#pragma unroll
-    for (int i = 0; i < TM; i++)
-#pragma unroll
-        for (int j = 0; j < TN; j++) acc[i][j] = 0.f;
-    load(0);
-    store(0);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_err = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    const int nk = (K + BK - 1) / BK;
-    for (int t = 0; t < nk; t++) {
-        const int s = t & 1;
-        if (t + 1 < nk) load((t + 1) * BK);
-#pragma unroll
-        for (int k = 0; k < BK; k++) {
-            float a[TM], b[TN];
-#pragma unroll
-            for (int i = 0; i < HM; i++) {
-                a[i] = As[s][k][ty * HM + i];
-                a[HM + i] = As[s][k][BM / 2 + ty * HM + i];
-            }
-#pragma unroll
-            for (int j = 0; j < HN; j++) {
-                b[j] = Bs[s][k][tx * HN + j];
-                b[HN + j] = Bs[s][k][BN / 2 + tx * HN + j];
-            }
-#pragma unroll
-            for (int i = 0; i < TM; i++)
-#pragma unroll
-                for (int j = 0; j < TN; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+    int issued = -1; // thread 0: the last stage whose products were issued
+
+    for (int kt = 0; kt < nk; kt++) {
+        const int st = kt & 1;
+        unsigned char *stg = smem + st * kStage;
+        // this stage's buffers were read by the products of k-tile kt - 2
+        if (kt >= 2 && !*s_err && !g_mbar_wait(g_smem_u32(&done[st]), ((kt - 2) >> 1) & 1)) {
+            *s_err = 1;
+            atomicAdd(&g_gemm_timeouts, 1ull);
         }
-        if (t + 1 < nk) {
-            store(s ^ 1);
-            __syncthreads();
+        if (!*s_err) {
+            const int k0 = kt * kGK;
+            if (tid < kGM) { // A row m0 + tid, 8 chunks of 4 along K
+                const int r = m0 + tid;
+#pragma unroll
+                for (int c = 0; c < kGK / 4; c++) {
+                    const int k = k0 + 4 * c; // K is a multiple of 8: k < K covers all four
+                    const float4 v = (r < M && k < K) ? __ldg(reinterpret_cast<const float4 *>(A + (size_t)r * lda + k))
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                    split4(v, stg + c * kGM * 16 + tid * 16, stg + kA + c * kGM * 16 + tid * 16);
+                }
+            } else if (tid - kGM < BN) { // B column n0 + nn as a K-major row
+                const int nn = tid - kGM, cn = n0 + nn;
+#pragma unroll
+                for (int c = 0; c < kGK / 4; c++) {
+                    const int k = k0 + 4 * c;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (cn < N && k < K) {
+                        if (b_kmajor) {
+                            v = __ldg(reinterpret_cast<const float4 *>(B + (size_t)cn * ldb + k));
+                        } else {
+                            const float *bp = B + (size_t)k * ldb + cn;
+                            v = make_float4(__ldg(bp), __ldg(bp + ldb), __ldg(bp + 2 * (size_t)ldb),
+                                            __ldg(bp + 3 * (size_t)ldb));
+                        }
+                    }
+                    split4(v, stg + 2 * kA + c * BN * 16 + nn * 16, stg + 2 * kA + kB + c * BN * 16 + nn * 16);
+                }
+            }
+        }
+        // the generic-proxy stores become visible to the tensor cores' reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(g_smem_u32(&ready[st])) : "memory");
+        if (tid == 0 && !*s_err) {
+            if (!g_mbar_wait(g_smem_u32(&ready[st]), (kt >> 1) & 1)) {
+                *s_err = 1;
+                atomicAdd(&g_gemm_timeouts, 1ull);
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = sb + st * kStage;
+#pragma unroll
+                for (int j = 0; j < kGK / 8; j++) { // K = 8 per instruction: two chunks
+                    const uint64_t ah = g_desc<kGM>(base + j * 2 * kGM * 16);
+                    const uint64_t al = g_desc<kGM>(base + kA + j * 2 * kGM * 16);
+                    const uint64_t bh = g_desc<BN>(base + 2 * kA + j * 2 * BN * 16);
+                    const uint64_t bl = g_desc<BN>(base + 2 * kA + kB + j * 2 * BN * 16);
+                    const uint32_t first = (kt > 0 || j > 0) ? 1u : 0u;
+#define GEMM_MMA(ad, bd, acc)                                                                               \
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                                          \
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),                \
+                 "l"(ad), "l"(bd), "r"(g_idesc<BN>()), "r"(acc)                                             \
+                 : "memory")
+                    GEMM_MMA(ah, bh, first);
+                    GEMM_MMA(ah, bl, 1u);
+                    GEMM_MMA(al, bh, 1u);
+#undef GEMM_MMA
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 g_smem_u32(&done[st]))
+                             : "memory");
+                issued = kt;
+            }
         }
     }
-#pragma unroll
-    for (int i = 0; i < TM; i++) {
-        const int r = m0 + (i < HM ? ty * HM + i : BM / 2 + ty * HM + (i - HM));
+    // thread 0 waits for the last products it issued (also after an error:
+    // tensor memory and shared memory must not be released under them)
+    if (tid == 0 && issued >= 0 && !g_mbar_wait(g_smem_u32(&done[issued & 1]), (issued >> 1) & 1)) {
+        *s_err = 1;
+        atomicAdd(&g_gemm_timeouts, 1ull);
+    }
+    if (tid == 0 && issued != nk - 1) *s_err = 1; // not every stage was multiplied
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool ok = !*s_err;
+
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (rows of the
+    // tile) and half w / 4 of the columns, 32 at a time
+    const int q = warp & 3, half = warp >> 2;
+    const int r = m0 + 32 * q + lane;
+    for (int cc = half * (BN / 2); cc < (half + 1) * (BN / 2); cc += 32) {
+        uint32_t v[32];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                     "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                     "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+                     "tcgen05.wait::ld.sync.aligned;"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                       "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                       "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                       "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                     : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cc)
+                     : "memory");
         if (r >= M) continue;
+        const int c0 = n0 + cc;
+        float o[32];
 #pragma unroll
-        for (int j = 0; j < TN; j++) {
-            const int c = n0 + (j < HN ? tx * HN + j : BN / 2 + tx * HN + (j - HN));
-            if (c >= N) continue;
-            float v = acc[i][j];
-            if (epi.mode == 1) {
-                const float l = __ldg(epi.lamM + r) * __ldg(epi.lamN + c);
-                v = v / fmaf(l, l, epi.rho);
+        for (int j = 0; j < 32; j++) {
+            float val = __uint_as_float(v[j]);
+            const int c = c0 + j;
+            if (!ok) {
+                val = __int_as_float(0x7fc00000); // NaN: the tile was not computed
+            } else if (epi.mode == 1) {
+                const float l = __ldg(epi.lamM + r) * __ldg(epi.lamN + (c < N ? c : N - 1));
+                val = val / fmaf(l, l, epi.rho);
             } else if (epi.mode == 2) {
-                v = fmaf(epi.alpha, v, __ldg(epi.add + (size_t)r * epi.ldadd + c));
+                val = fmaf(epi.alpha, val, c < N ? __ldg(epi.add + (size_t)r * epi.ldadd + c) : 0.f);
             } else {
-                v *= epi.alpha;
+                val *= epi.alpha;
             }
-            C[(size_t)r * ldc + c] = v;
+            o[j] = val;
         }
+        float *dst = C + (size_t)r * ldc + c0;
+        if (c0 + 32 <= N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4 *>(dst + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                if (c0 + j < N) dst[j] = o[j];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                     : "memory");
     }
 }
 
 struct GemmCfg {
-    int bm, bn;
-    void (*fn)(const float *, int, const float *, int, float *, int, int, int, int, Epi);
+    int bn;
+    void (*fn)(const float *, int, const float *, int, int, float *, int, int, int, int, Epi);
+    int smem;
 };
 
 const GemmCfg kGemmCfgs[] = {
-    {128, 128, k_sgemm<128, 128, 8, 8>},
-    {128, 64, k_sgemm<128, 64, 8, 4>},
-    {64, 128, k_sgemm<64, 128, 4, 8>},
-    {64, 64, k_sgemm<64, 64, 4, 4>},
+    {128, k_gemm_tc<128>, g_smem_bytes<128>()},
+    {64, k_gemm_tc<64>, g_smem_bytes<64>()},
 };
 constexpr int kNumCfgs = sizeof(kGemmCfgs) / sizeof(kGemmCfgs[0]);
 
-cudaError_t gemm(int cfg, const float *A, int lda, const float *B, int ldb, float *C, int ldc, int M, int N, int K,
-                 const Epi &epi, cudaStream_t st)
+// C = epi(A B), A [M][K] row-major (lda), B [K][N] row-major (ldb); b_sym:
+// B is symmetric (so its rows are read as its columns).
+cudaError_t gemm(int cfg, const float *A, int lda, const float *B, int ldb, bool b_sym, float *C, int ldc, int M,
+                 int N, int K, const Epi &epi, cudaStream_t st)
 {
     const GemmCfg &g = kGemmCfgs[cfg];
-    dim3 grid((N + g.bn - 1) / g.bn, (M + g.bm - 1) / g.bm);
-    g.fn<<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, epi);
+    cudaError_t e = cudaFuncSetAttribute(g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + g.bn - 1) / g.bn, (M + kGM - 1) / kGM);
+    g.fn<<<grid, kGThreads, g.smem, st>>>(A, lda, B, ldb, b_sym ? 1 : 0, C, ldc, M, N, K, epi);
     return cudaGetLastError();
 }
 
@@ -295,14 +467,16 @@ size_t tables_bytes(const std::vector<int> &sizes)
     return o;
 }
 
-// Fastest tile shape per (M, N, K), cached for the process (all shapes give
-// the same bits: every output is the same sequential FMA chain over k).
-std::map<std::tuple<int, int, int>, int> g_tuned;
+// Fastest tile shape per (M, N, K, B symmetric), cached for the process (all
+// shapes give the same bits: every output accumulates the same products in
+// the same K order).
+std::map<std::tuple<int, int, int, int>, int> g_tuned;
 
-int autotune(const float *A, const float *B, float *C, int M, int N, int K, cudaStream_t st, bool enabled)
+int autotune(const float *A, const float *B, bool b_sym, float *C, int M, int N, int K, cudaStream_t st,
+             bool enabled)
 {
     if (!enabled) return 0;
-    const auto key = std::make_tuple(M, N, K);
+    const auto key = std::make_tuple(M, N, K, b_sym ? 1 : 0);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) return it->second;
     cudaEvent_t e0, e1;
@@ -315,9 +489,9 @@ int autotune(const float *A, const float *B, float *C, int M, int N, int K, cuda
     int best = 0;
     float best_ms = 1e30f;
     for (int c = 0; c < kNumCfgs; c++) {
-        if (gemm(c, A, K, B, N, C, N, M, N, K, epi, st) != cudaSuccess) continue; // warm-up
+        if (gemm(c, A, K, B, N, b_sym, C, N, M, N, K, epi, st) != cudaSuccess) continue; // warm-up
         cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; r++) gemm(c, A, K, B, N, C, N, M, N, K, epi, st);
+        for (int r = 0; r < 3; r++) gemm(c, A, K, B, N, b_sym, C, N, M, N, K, epi, st);
         cudaEventRecord(e1, st);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
@@ -380,10 +554,15 @@ int pnp_iteration(const gbm3d_pnp_plan_st &P, const PnpImage &m, cudaStream_t st
     const Epi finish{2, 1.f / ((float)H * (float)W), 0.f, nullptr, nullptr, m.u, W};
     cudaError_t e;
     // T(b) = C_H b C_W, divided by the eigenvalues, transformed back (+ u)
-    if ((e = gemm(m.cfg1, m.casH, H, m.b, W, m.t1, W, H, W, H, plain, st)) != cudaSuccess) return pnp_cuda_fail(e, "pnp gemm");
-    if ((e = gemm(m.cfg2, m.t1, W, m.casW, W, m.b, W, H, W, W, divide, st)) != cudaSuccess) return pnp_cuda_fail(e, "pnp gemm");
-    if ((e = gemm(m.cfg1, m.casH, H, m.b, W, m.t1, W, H, W, H, plain, st)) != cudaSuccess) return pnp_cuda_fail(e, "pnp gemm");
-    if ((e = gemm(m.cfg2, m.t1, W, m.casW, W, m.t, W, H, W, W, finish, st)) != cudaSuccess) return pnp_cuda_fail(e, "pnp gemm");
+    // (C_W is symmetric, so the second product reads its rows as columns)
+    if ((e = gemm(m.cfg1, m.casH, H, m.b, W, false, m.t1, W, H, W, H, plain, st)) != cudaSuccess)
+        return pnp_cuda_fail(e, "pnp gemm");
+    if ((e = gemm(m.cfg2, m.t1, W, m.casW, W, true, m.b, W, H, W, W, divide, st)) != cudaSuccess)
+        return pnp_cuda_fail(e, "pnp gemm");
+    if ((e = gemm(m.cfg1, m.casH, H, m.b, W, false, m.t1, W, H, W, H, plain, st)) != cudaSuccess)
+        return pnp_cuda_fail(e, "pnp gemm");
+    if ((e = gemm(m.cfg2, m.t1, W, m.casW, W, true, m.t, W, H, W, W, finish, st)) != cudaSuccess)
+        return pnp_cuda_fail(e, "pnp gemm");
     // v = G-BM3D(x + u)
     int s = gbm3d_denoise(m.t, H, W, W, m.sigma_d, &P.p, m.v, m.dws, (gbm3d_stream_t)st);
     if (s != GBM3D_OK) return s;
@@ -509,8 +688,8 @@ int gbm3d_pnp_plan_create(int n, const int *H, const int *W, const float *const 
     // autotune the two product shapes of every image on its own buffers
     for (PnpImage &m : P->img) {
         if (e != cudaSuccess) break;
-        m.cfg1 = autotune(m.casH, m.b, m.t1, m.H, m.W, m.H, s0, q->autotune != 0);
-        m.cfg2 = autotune(m.t1, m.casW, m.t, m.H, m.W, m.W, s0, q->autotune != 0);
+        m.cfg1 = autotune(m.casH, m.b, false, m.t1, m.H, m.W, m.H, s0, q->autotune != 0);
+        m.cfg2 = autotune(m.t1, m.casW, true, m.t, m.H, m.W, m.W, s0, q->autotune != 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s0);

@@ -122,7 +122,7 @@ def test_rerun_is_deterministic_and_tiles_are_recorded():
         assert torch.equal(x, z)
     for i in range(3):
         a, b = plan.gemm_configs(i)
-        assert 0 <= a < 4 and 0 <= b < 4
+        assert 0 <= a < 2 and 0 <= b < 2
     plan.close()
 
 
