@@ -11,11 +11,12 @@
 // rounded to nearest-even by the layer that writes them); accumulation is
 // FP32 throughout.  The six forward 32 -> 32 layers run on the
 // 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory)
-// as implicit GEMMs over 128-pixel row tiles; their backward-data passes
-// run on mma.sync over 4 x 32 pixel tiles (weights flipped and transposed,
-// masked by the ReLU of the layer below).  The thin first and last layers,
-// the weight gradients (per-CTA partial sums, then a fixed-order reduction:
-// deterministic) and Adam are SIMT.
+// as implicit GEMMs over 128-pixel row tiles, and so do their backward-data
+// passes (the same kernel with the weights flipped and transposed, masked by
+// the ReLU of the layer below) and their weight gradients (k_wgrad_tc:
+// per-CTA partial sums, then a fixed-order reduction: deterministic).  The
+// gradients between the 32-channel layers are stored BF16, like the
+// activations.  The thin first and last layers and Adam are SIMT.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdarg.h>
@@ -119,159 +120,6 @@ __global__ void __launch_bounds__(256) k_conv_first(const float *__restrict__ Z,
     }
 }
 
-// ---- backward data pass of a 32 -> 32 layer (mma.sync tensor cores) ----------
-// out[p][n] = (sum_tap sum_k in[p + off(tap)][k] V[tap][n][k]) * (mask[p][n] > 0),
-// in = the FP32 gradient at the layer's output, V the flipped, transposed
-// weights, mask the layer's BF16 input activation (the ReLU of the layer
-// below).  CTA: 4 warps, a tile of 4 rows x 32 pixels; warp w owns row w (two m-tiles
-// of 16 pixels) and all 32 outputs (four n-tiles of 8).  The input tile with
-// its 1-pixel halo (6 x 34 pixels x 32 channels) and V are staged in shared
-// memory as BF16 with 40-element rows (80 bytes: fragment loads are
-// conflict-free).
-constexpr int kTY = 4, kTX = 32, kRow = 40;
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// Persistent: each CTA stages V once, then walks tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; the next tile's input is loaded into
-// registers while the tensor cores work on the current one (two input
-// buffers in shared memory).
-constexpr int kInPix = (kTY + 2) * (kTX + 2);                 // 204 pixels per input tile
-constexpr int kInLd = (kInPix * 8 + 127) / 128;               // float4 loads per thread per tile (13)
-constexpr int kConvSmem = (9 * kC * kRow + 2 * kInPix * kRow) * 2; // bytes: V + two input tiles
-
-struct ConvTiles {
-    int tx, ty, per_img, total; // tiles along x, y; per image; in the batch
-};
-
-__device__ __forceinline__ void conv_tile(const ConvTiles &T, int t, int &b, int &y0, int &x0)
-{
-    b = t / T.per_img;
-    const int r = t - b * T.per_img, ty = r / T.tx;
-    y0 = ty * kTY;
-    x0 = (r - ty * T.tx) * kTX;
-}
-
-__global__ void __launch_bounds__(128, 4) k_conv_bwd(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ V,
-                                                     const __nv_bfloat16 *__restrict__ mask, float *__restrict__ out,
-                                                     int H, int W, ConvTiles T)
-{
-    extern __shared__ __align__(16) __nv_bfloat16 cs[];
-    __nv_bfloat16 *s_v = cs, *s_in0 = cs + 9 * kC * kRow;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-    // stage V (9 x 32 rows of 32 BF16, as 16-byte chunks) once
-    for (int i = tid; i < 9 * kC * 4; i += 128) {
-        const int row = i >> 2, q = i & 3;
-        *reinterpret_cast<uint4 *>(s_v + row * kRow + q * 8) = *reinterpret_cast<const uint4 *>(V + row * kC + q * 8);
-    }
-    float4 pre[kInLd];
-    auto fetch = [&](int t) { // the input tile of t, with halo, zero outside the image
-        int b, y0, x0;
-        conv_tile(T, t, b, y0, x0);
-        const size_t img = (size_t)b * H * W;
-#pragma unroll
-        for (int j = 0; j < kInLd; j++) {
-            const int i = tid + 128 * j, pix = i >> 3, q = i & 7;
-            const int ty = pix / (kTX + 2), tx = pix - ty * (kTX + 2);
-            const int yy = y0 + ty - 1, xx = x0 + tx - 1;
-            pre[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < kInPix * 8 && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                pre[j] = *reinterpret_cast<const float4 *>(in + (img + (size_t)yy * W + xx) * kC + q * 4);
-        }
-    };
-    auto put = [&](__nv_bfloat16 *dst) { // FP32 -> BF16 into an input buffer
-#pragma unroll
-        for (int j = 0; j < kInLd; j++) {
-            const int i = tid + 128 * j;
-            if (i >= kInPix * 8) continue;
-            const int pix = i >> 3, q = i & 7;
-            __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(dst + pix * kRow + q * 4);
-            d[0] = __floats2bfloat162_rn(pre[j].x, pre[j].y);
-            d[1] = __floats2bfloat162_rn(pre[j].z, pre[j].w);
-        }
-    };
-    int t = blockIdx.x;
-    if (t < T.total) {
-        fetch(t);
-        put(s_in0);
-    }
-    __syncthreads();
-    for (int it = 0; t < T.total; t += gridDim.x, it++) {
-        const __nv_bfloat16 *s_in = s_in0 + (it & 1) * kInPix * kRow;
-        const int tn = t + gridDim.x;
-        if (tn < T.total) fetch(tn); // in flight during the MMAs below
-        float acc[2][4][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-            for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                for (int r = 0; r < 4; r++) acc[mt][nt][r] = 0.f;
-#pragma unroll 1
-        for (int tap = 0; tap < 9; tap++) {
-            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-#pragma unroll
-            for (int h = 0; h < 2; h++) { // channels 16 h .. 16 h + 15
-                uint32_t a[2][4], bb[4][2];
-#pragma unroll
-                for (int mt = 0; mt < 2; mt++) {
-                    const int p0 = (warp + 1 + dy) * (kTX + 2) + mt * 16 + g + 1 + dx; // tile pixel of row g
-                    const __nv_bfloat16 *r0 = s_in + p0 * kRow + 16 * h + 2 * t4;
-                    const __nv_bfloat16 *r1 = r0 + 8 * kRow; // pixel g + 8
-                    a[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
-                    a[mt][1] = *reinterpret_cast<const uint32_t *>(r1);
-                    a[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-                    a[mt][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
-                }
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++) {
-                    const __nv_bfloat16 *v = s_v + (tap * kC + nt * 8 + g) * kRow + 16 * h + 2 * t4;
-                    bb[nt][0] = *reinterpret_cast<const uint32_t *>(v);
-                    bb[nt][1] = *reinterpret_cast<const uint32_t *>(v + 8);
-                }
-#pragma unroll
-                for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                    for (int nt = 0; nt < 4; nt++)
-                        mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bb[nt][0], bb[nt][1]);
-            }
-        }
-        int b, y0, x0;
-        conv_tile(T, t, b, y0, x0);
-        const size_t img = (size_t)b * H * W;
-        const int y = y0 + warp;
-        if (y < H) {
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int half = 0; half < 2; half++) {
-                    const int x = x0 + mt * 16 + g + 8 * half;
-                    if (x >= W) continue;
-                    const size_t pp = img + (size_t)y * W + x;
-#pragma unroll
-                    for (int nt = 0; nt < 4; nt++) {
-                        const int n = nt * 8 + 2 * t4;
-                        float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                        const float2 mk =
-                            __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(mask + pp * kC + n));
-                        v0 = mk.x > 0.f ? v0 : 0.f;
-                        v1 = mk.y > 0.f ? v1 : 0.f;
-                        *reinterpret_cast<float2 *>(out + pp * kC + n) = make_float2(v0, v1);
-                    }
-                }
-        }
-        if (tn < T.total) put(s_in0 + ((it + 1) & 1) * kInPix * kRow);
-        __syncthreads();
-    }
-}
-
 // ---- the forward 32 -> 32 convolution on the 5th-generation tensor cores ------
 // tcgen05.mma kind::f16 (BF16 inputs, FP32 accumulators in tensor memory):
 // per tile of 128 pixels of one image row, M = 128 pixels, N = 32 output
@@ -336,9 +184,16 @@ struct ConvRuns {
     int strips, runs_col, run_len, total;
 };
 
+// BWD = false: the forward layer, out = ReLU(conv(in, V) + bias).  BWD =
+// true: its backward-data pass, out = conv(in, V) * (mask > 0) with in the
+// BF16 gradient at the layer's output, V the flipped, transposed weights and
+// mask the layer's input activation (the ReLU of the layer below); bias is
+// unused.  Both write BF16.
+template <bool BWD>
 __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
                                                             const __nv_bfloat16 *__restrict__ V,
                                                             const float *__restrict__ bias,
+                                                            const __nv_bfloat16 *__restrict__ mask,
                                                             __nv_bfloat16 *__restrict__ out, int B, int H, int W,
                                                             ConvRuns RN)
 {
@@ -367,7 +222,7 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
     }
     float bv[kC];
 #pragma unroll
-    for (int c = 0; c < kC; c++) bv[c] = bias[c];
+    for (int c = 0; c < kC; c++) bv[c] = BWD ? 0.f : bias[c];
     // chunk i of a staged row: channel group i & 3 of pixel i >> 2 (x0 - 1 + i >> 2)
     auto src_of = [&](int b, int yy, int x0, int i, bool &inside) {
         const int xx = x0 + (i >> 2) - 1;
@@ -484,15 +339,27 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
                          : "memory");
             const int x = x0 + warp * 32 + lane;
             if (x < W) {
-                uint4 *o = reinterpret_cast<uint4 *>(out + (((size_t)b * H + y) * W + x) * kC);
+                const size_t pix = ((size_t)b * H + y) * W + x;
+                uint4 *o = reinterpret_cast<uint4 *>(out + pix * kC);
 #pragma unroll
                 for (int q = 0; q < kC / 8; q++) {
                     uint32_t h[4];
+                    uint4 mk = make_uint4(0, 0, 0, 0);
+                    if (BWD) mk = __ldg(reinterpret_cast<const uint4 *>(mask + pix * kC) + q);
+                    const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
 #pragma unroll
                     for (int j = 0; j < 4; j++) {
                         const int c = 8 * q + 2 * j;
-                        __nv_bfloat162 t = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[c]) + bv[c], 0.f),
-                                                                 fmaxf(__uint_as_float(v[c + 1]) + bv[c + 1], 0.f));
+                        float v0, v1;
+                        if (BWD) { // the ReLU's derivative: pass where the input activation is positive
+                            const float2 m2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&mw[j]));
+                            v0 = m2.x > 0.f ? __uint_as_float(v[c]) : 0.f;
+                            v1 = m2.y > 0.f ? __uint_as_float(v[c + 1]) : 0.f;
+                        } else {
+                            v0 = fmaxf(__uint_as_float(v[c]) + bv[c], 0.f);
+                            v1 = fmaxf(__uint_as_float(v[c + 1]) + bv[c + 1], 0.f);
+                        }
+                        __nv_bfloat162 t = __floats2bfloat162_rn(v0, v1);
                         h[j] = *reinterpret_cast<uint32_t *>(&t);
                     }
                     o[q] = make_uint4(h[0], h[1], h[2], h[3]);
@@ -593,8 +460,8 @@ __global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16 *__restri
 // eight lanes per pixel, four channels each (coalesced rows), 16 pixels of
 // kThinRows rows per CTA.
 __global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, const float *__restrict__ w8r,
-                                                  const __nv_bfloat16 *__restrict__ x7, float *__restrict__ g7, int H,
-                                                  int W)
+                                                  const __nv_bfloat16 *__restrict__ x7, __nv_bfloat16 *__restrict__ g7,
+                                                  int H, int W)
 {
     const int cq = threadIdx.x & 7;
     const int x = blockIdx.x * 16 + (threadIdx.x >> 3), b = blockIdx.z;
@@ -620,25 +487,29 @@ __global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, 
             acc[2] = fmaf(gv[tap], w[tap].z, acc[2]);
             acc[3] = fmaf(gv[tap], w[tap].w, acc[3]);
         }
-        reinterpret_cast<float4 *>(g7 + p * kC)[cq] =
-            make_float4(mk.x > 0.f ? acc[0] : 0.f, mk.y > 0.f ? acc[1] : 0.f, mk.z > 0.f ? acc[2] : 0.f,
-                        mk.w > 0.f ? acc[3] : 0.f);
+        // the gradient at x7's pre-activation, stored BF16 (the input of the
+        // tensor-core backward passes)
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(mk.x > 0.f ? acc[0] : 0.f, mk.y > 0.f ? acc[1] : 0.f);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(mk.z > 0.f ? acc[2] : 0.f, mk.w > 0.f ? acc[3] : 0.f);
+        reinterpret_cast<uint2 *>(g7 + p * kC)[cq] =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
     }
 }
 
-// ---- weight gradients ---------------------------------------------------------
+// ---- weight gradients of the thin first and last layers ------------------------
 // dW[tap][ci][co] = sum_p x[p + off(tap)][ci] g[p][co] and db[co] = sum_p g[p][co].
 // One thread per (tap, ci) with CO accumulators (thread 9 CI also sums the
 // bias); each CTA walks rows of 64 pixels (x with halo and g staged in shared
 // memory) over a strided share of the batch and writes its partial sums;
-// k_reduce adds the CTAs' partials in a fixed order.
+// k_reduce adds the CTAs' partials in a fixed order.  (The six 32 -> 32
+// layers use k_wgrad_tc on the tensor cores.)
 constexpr int kGX = 64;
 
 __device__ __forceinline__ float ldf(const float *p) { return *p; }
 __device__ __forceinline__ float ldf(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
-template <int CI, int CO, typename TX>
-__global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, const float *__restrict__ g, int B,
+template <int CI, int CO, typename TX, typename TG>
+__global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, const TG *__restrict__ g, int B,
                                                       int H, int W, float *__restrict__ part)
 {
     __shared__ float sx[3][kGX + 2][CI];
@@ -662,7 +533,7 @@ __global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, 
         }
         for (int i = tid; i < kGX * CO; i += nthr) {
             const int c = i / CO, co = i - c * CO, xx = xb + c;
-            sg[c][co] = xx < W ? g[(((size_t)b * H + y) * W + xx) * CO + co] : 0.f;
+            sg[c][co] = xx < W ? ldf(g + (((size_t)b * H + y) * W + xx) * CO + co) : 0.f;
         }
         __syncthreads();
         for (int c = 0; c < kGX; c++) {
@@ -678,6 +549,185 @@ __global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, 
     } else {
 #pragma unroll
         for (int co = 0; co < CO; co++) o[(tap * CI + ci) * CO + co] = acc[co];
+    }
+}
+
+// ---- weight gradient of a 32 -> 32 layer on the tensor cores ----------------------
+// dW[tap][ci][co] = sum_p x[p + off(tap)][ci] g[p][co] as tcgen05.mma kind::f16
+// (BF16 operands, FP32 accumulators in tensor memory), db[co] = sum_p g[p][co].
+// A unit is one 128-pixel segment of an image row y (pixels x0 .. x0 + 127):
+// the rows y - 1 .. y + 2 of x with a 1-pixel halo (the fourth row only pads
+// the M = 128 operand and is zero) are staged as [row][channel group][pixel]
+// [8 BF16], and the row y of g as [co group][pixel][8].  Both are MN-major
+// operands without swizzle (core matrices of 8 channels x 8 pixels, 16-byte
+// rows): x's 16 row-and-group blocks sit 130 x 16 bytes apart, so one
+// operand of M = 128 rows = (row, ci) spans all three kernel rows; starting
+// it dx + 1 pixels into the staged row applies the column offset.  For each
+// dx the 8 instructions of K = 16 pixels add x[y + dy][x + dx][ci] g[y][x][co]
+// into accumulator dx + 1 (tensor-memory lane 32 (dy + 1) + ci, column co;
+// lane 96, whose operand row is a one, sums g: the bias gradient).  Two stages of units alternate on mbarriers (the
+// next unit is staged while the products of the current one run).  Each CTA
+// takes a strided share of the units, then writes one partial row (the
+// layout of k_wgrad's), which k_reduce sums in a fixed order: deterministic.
+constexpr int kWtPix = kCT + 2;                            // staged pixels of an x row
+constexpr int kWtX = 4 * kCGrp * kWtPix * 16;              // staged x rows (33,280 bytes)
+constexpr int kWtG = kCGrp * kCT * 16;                     // staged g row (8,192 bytes)
+constexpr int kWtStage = kWtX + kWtG;
+constexpr int kWtSmem = 2 * kWtStage + 64;
+constexpr uint32_t kWtIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                              ((uint32_t)(kC >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// D FP32; A, B BF16; both MN-major; N = 32; M = 128
+
+__global__ void __launch_bounds__(128, 2) k_wgrad_tc(const __nv_bfloat16 *__restrict__ x,
+                                                     const __nv_bfloat16 *__restrict__ g, int B, int H, int W,
+                                                     float *__restrict__ part)
+{
+    extern __shared__ __align__(1024) unsigned char wsm[];
+    uint64_t *ready = reinterpret_cast<uint64_t *>(wsm + 2 * kWtStage); // [2] stage staged (128 arrivals)
+    uint64_t *done = ready + 2;                                          // [2] products of the stage complete
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 2);
+    volatile int *s_err = reinterpret_cast<volatile int *>(s_tmem + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = (W + kCT - 1) / kCT;
+    const long long units = (long long)B * H * segs;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)), "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(su32(ready + b)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(done + b)) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_err = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+    int n = 0;         // units of this CTA
+    int issued = -1;   // thread 0: the last unit whose products were issued
+    for (long long u = blockIdx.x; u < units; u += gridDim.x, n++) {
+        const int st = n & 1;
+        unsigned char *sx = wsm + st * kWtStage, *sg = sx + kWtX;
+        if (n >= 2 && !*s_err && !cbar_wait(su32(done + st), ((n - 2) >> 1) & 1)) {
+            *s_err = 1;
+            atomicAdd(&g_conv_timeouts, 1ull);
+        }
+        if (!*s_err) {
+            const int seg = (int)(u % segs), y = (int)((u / segs) % H), b = (int)(u / ((long long)segs * H));
+            const int x0 = seg * kCT;
+            // x: 4 rows x 130 pixels x 4 channel groups of 16 bytes, zero outside;
+            // the padding row holds a one in channel 0 (lane 96 of every
+            // accumulator then sums g over the unit: the bias gradient)
+            for (int i = tid; i < 4 * kWtPix * kCGrp; i += 128) {
+                const int grp = i & 3, pix = (i >> 2) % kWtPix, r = (i >> 2) / kWtPix;
+                const int yy = y + r - 1, xx = x0 + pix - 1;
+                uint4 v = make_uint4(r == 3 && grp == 0 ? 0x3F80u : 0u, 0, 0, 0); // BF16 1.0 in element 0
+                if (r < 3 && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    v = __ldg(reinterpret_cast<const uint4 *>(x + (((size_t)b * H + yy) * W + xx) * kC) + grp);
+                *reinterpret_cast<uint4 *>(sx + ((r * kCGrp + grp) * kWtPix + pix) * 16) = v;
+            }
+            // g: 128 pixels x 4 groups
+            for (int i = tid; i < kCT * kCGrp; i += 128) {
+                const int grp = i & 3, pix = i >> 2, xx = x0 + pix;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (xx < W) v = __ldg(reinterpret_cast<const uint4 *>(g + (((size_t)b * H + y) * W + xx) * kC) + grp);
+                *reinterpret_cast<uint4 *>(sg + (grp * kCT + pix) * 16) = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(ready + st)) : "memory");
+        if (tid == 0 && !*s_err) {
+            if (!cbar_wait(su32(ready + st), (n >> 1) & 1)) {
+                *s_err = 1;
+                atomicAdd(&g_conv_timeouts, 1ull);
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t xb = su32(sx), gb = su32(sg);
+#pragma unroll
+                for (int d = 0; d < 3; d++)
+#pragma unroll
+                    for (int ks = 0; ks < kCT / 16; ks++) {
+                        // A: MN stride (row-and-group blocks) 130 x 16 bytes, K stride (8 pixels) 128
+                        const uint64_t ad = cdesc(xb + d * 16 + ks * 256, 128, kWtPix * 16);
+                        const uint64_t bd = cdesc(gb + ks * 256, 128, kCT * 16);
+                        const uint32_t acc = (n > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                         tmem + (uint32_t)(d * kC)),
+                                     "l"(ad), "l"(bd), "r"(kWtIdesc), "r"(acc)
+                                     : "memory");
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(done + st))
+                             : "memory");
+                issued = n;
+            }
+        }
+    }
+    if (tid == 0 && issued >= 0 && !cbar_wait(su32(done + (issued & 1)), (issued >> 1) & 1)) {
+        *s_err = 1;
+        atomicAdd(&g_conv_timeouts, 1ull);
+    }
+    if (tid == 0 && issued != n - 1) *s_err = 1; // a unit was not multiplied
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool ok = !*s_err;
+    float *o = part + (size_t)blockIdx.x * (9 * kC * kC + kC);
+    if (warp == 3) { // lane 96 (warp 3, lane 0) of accumulator 1: the bias gradient
+        uint32_t v[32];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                     "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                     "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+                     "tcgen05.wait::ld.sync.aligned;"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                       "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                       "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                       "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                     : "r"(tmem + ((uint32_t)96 << 16) + (uint32_t)kC)
+                     : "memory");
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < kC; c++)
+                o[9 * kC * kC + c] = !ok ? __int_as_float(0x7fc00000) : (n == 0 ? 0.f : __uint_as_float(v[c]));
+    }
+    if (warp < 3) { // kernel row dy + 1 = warp, input channel = lane
+#pragma unroll 1
+        for (int d = 0; d < 3; d++) {
+            uint32_t v[32];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+                         "tcgen05.wait::ld.sync.aligned;"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * kC))
+                         : "memory");
+            float *row = o + ((warp * 3 + d) * kC + lane) * kC; // tap 3 (dy + 1) + (dx + 1)
+#pragma unroll
+            for (int c = 0; c < kC; c += 4) {
+                const float nan = __int_as_float(0x7fc00000);
+                float4 w4 = n == 0 ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]),
+                                                 __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
+                if (!ok) w4 = make_float4(nan, nan, nan, nan); // a product failed: visible in the gradient
+                *reinterpret_cast<float4 *>(row + c) = w4;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
     }
 }
 
@@ -756,8 +806,8 @@ PilotLayout pilot_layout(int B, int H, int W, bool train)
     L.act = take(P * kC * 2 * (train ? 7 : 2)); // BF16
     if (train) {
         L.g8 = take(P * 4);
-        L.ga = take(P * kC * 4);
-        L.gb = take(P * kC * 4);
+        L.ga = take(P * kC * 2); // BF16 gradients between the 32-channel layers
+        L.gb = take(P * kC * 2);
         L.part = take((size_t)kWgMax * (kWm + kC) * 4);
         L.grad = take((size_t)kParams * 4);
         L.lpart = take((size_t)L.lparts * 4);
@@ -767,35 +817,10 @@ PilotLayout pilot_layout(int B, int H, int W, bool train)
     return L;
 }
 
-ConvTiles conv_tiles(int B, int H, int W)
-{
-    ConvTiles T;
-    T.tx = (W + kTX - 1) / kTX;
-    T.ty = (H + kTY - 1) / kTY;
-    T.per_img = T.tx * T.ty;
-    T.total = B * T.per_img;
-    return T;
-}
-
-// Persistent grid of the 32 -> 32 convolutions: four CTAs per SM (shared
-// memory allows four), no more than there are tiles.  Sets the kernels'
-// shared-memory limit once.
-int conv_ctas(const ConvTiles &T)
-{
-    static int per_dev = 0;
-    if (!per_dev) {
-        int dev = 0, nsm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            nsm = 148;
-        cudaFuncSetAttribute(k_conv_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
-        per_dev = 4 * nsm;
-    }
-    return T.total < per_dev ? T.total : per_dev;
-}
-
-// Grid of the tensor-core forward convolution: runs of rows of each 128-pixel
-// strip, sized so that the runs fill kCTcPerSm CTAs per SM (shared memory)
-// once, and one CTA per run.
+// Grid of the tensor-core convolutions (forward and backward data): runs of
+// rows of each 128-pixel strip, sized so that the runs fill kCTcPerSm CTAs per
+// SM (shared memory) once, and one CTA per run.  Sets the shared-memory
+// limits of the tensor-core kernels once.
 int conv_tc_ctas(int B, int H, int W, ConvRuns &RN)
 {
     static int per_dev = 0;
@@ -803,7 +828,9 @@ int conv_tc_ctas(int B, int H, int W, ConvRuns &RN)
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             nsm = 148;
-        cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kCTcSmem);
+        cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCTcSmem);
+        cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCTcSmem);
+        cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWtSmem);
         per_dev = kCTcPerSm * nsm;
     }
     RN.strips = (W + kCT - 1) / kCT;
@@ -850,8 +877,8 @@ cudaError_t pilot_forward(const float *Z, int B, int H, int W, int zpitch, long 
     ConvRuns RN;
     const int gtc = conv_tc_ctas(B, H, W, RN);
     for (int m = 0; m < kMid; m++)
-        k_conv_tc<<<gtc, 128, kCTcSmem, st>>>(X(m + 1), wf + (size_t)m * kWm, theta + off_bm(m), X(m + 2), B, H, W,
-                                             RN);
+        k_conv_tc<false><<<gtc, 128, kCTcSmem, st>>>(X(m + 1), wf + (size_t)m * kWm, theta + off_bm(m), nullptr,
+                                                    X(m + 2), B, H, W, RN);
     const float inv_n = 1.f / (float)L.plane;
     k_conv_last<<<dim3((W + kLX - 1) / kLX, (H + kThinRows - 1) / kThinRows, B), 256, 0, st>>>(
         X(7), w8r, theta, Z, zpitch, zbatch, Y1, pilot, ppitch, pbatch, train ? (float *)(ws + L.g8) : nullptr,
@@ -868,28 +895,30 @@ cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, 
     auto X = [&](int l) { return act + (size_t)(l - 1) * L.plane * kC; };
     const __nv_bfloat16 *wb = (const __nv_bfloat16 *)(ws + L.wb);
     const float *w8r = (const float *)(ws + L.w8r);
-    float *g8 = (float *)(ws + L.g8), *ga = (float *)(ws + L.ga), *gb = (float *)(ws + L.gb);
+    float *g8 = (float *)(ws + L.g8);
+    __nv_bfloat16 *ga = (__nv_bfloat16 *)(ws + L.ga), *gb = (__nv_bfloat16 *)(ws + L.gb);
     const int nc = wgrad_ctas();
     // loss = sum of the scaled partials (their rows hold (pilot - Y1)^2 / n)
     k_sum<<<1, 1024, 0, st>>>((const float *)(ws + L.lpart), L.lparts, (float *)(ws + L.loss));
     // last layer
-    k_wgrad<32, 1, __nv_bfloat16><<<nc, 9 * 32 + 1, 0, st>>>(X(7), g8, B, H, W, part);
+    k_wgrad<32, 1, __nv_bfloat16, float><<<nc, 9 * 32 + 1, 0, st>>>(X(7), g8, B, H, W, part);
     k_reduce<<<(kW8 + 1 + 255) / 256, 256, 0, st>>>(part, nc, kW8 + 1, grad + kOffW8);
     const dim3 g128((W + 15) / 16, (H + kThinRows - 1) / kThinRows, B); // 16 x kThinRows pixels per CTA
-    const ConvTiles T = conv_tiles(B, H, W);
-    const int gm = conv_ctas(T);
+    ConvRuns RN;
+    const int gtc = conv_tc_ctas(B, H, W, RN);
     k_last_bwd<<<g128, 128, 0, st>>>(g8, w8r, X(7), ga, H, W);
-    float *gcur = ga, *gnext = gb;
+    __nv_bfloat16 *gcur = ga, *gnext = gb;
     for (int m = kMid - 1; m >= 0; m--) { // layer m + 2: x_{m+1} -> x_{m+2}; gcur = dL/dpre_{m+2}
-        k_wgrad<32, 32, __nv_bfloat16><<<nc, 9 * 32 + 1, 0, st>>>(X(m + 1), gcur, B, H, W, part);
+        k_wgrad_tc<<<nc, 128, kWtSmem, st>>>(X(m + 1), gcur, B, H, W, part);
         k_reduce<<<(kWm + kC + 255) / 256, 256, 0, st>>>(part, nc, kWm + kC, grad + off_wm(m));
-        k_conv_bwd<<<gm, 128, kConvSmem, st>>>(gcur, wb + (size_t)m * kWm, X(m + 1), gnext, H, W, T);
-        float *t = gcur;
+        k_conv_tc<true><<<gtc, 128, kCTcSmem, st>>>(gcur, wb + (size_t)m * kWm, nullptr, X(m + 1), gnext, B, H, W,
+                                                   RN);
+        __nv_bfloat16 *t = gcur;
         gcur = gnext;
         gnext = t;
     }
     // first layer (gcur = dL/dpre_1)
-    k_wgrad<2, 32, float><<<nc, 9 * 2 + 1, 0, st>>>((const float *)(ws + L.x0), gcur, B, H, W, part);
+    k_wgrad<2, 32, float, __nv_bfloat16><<<nc, 9 * 2 + 1, 0, st>>>((const float *)(ws + L.x0), gcur, B, H, W, part);
     k_reduce<<<(kW1 + kC + 255) / 256, 256, 0, st>>>(part, nc, kW1 + kC, grad + kOffW1);
     return cudaGetLastError();
 }
