@@ -498,58 +498,124 @@ __global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, 
 
 // ---- weight gradients of the thin first and last layers ------------------------
 // dW[tap][ci][co] = sum_p x[p + off(tap)][ci] g[p][co] and db[co] = sum_p g[p][co].
-// One thread per (tap, ci) with CO accumulators (thread 9 CI also sums the
-// bias); each CTA walks rows of 64 pixels (x with halo and g staged in shared
-// memory) over a strided share of the batch and writes its partial sums;
-// k_reduce adds the CTAs' partials in a fixed order.  (The six 32 -> 32
+// A CTA of 256 threads splits the 9 CI CO + CO outputs among its threads
+// (each keeps its own few sums in registers) and walks row segments of 128
+// pixels (64 for the 32-channel input, keeping the stage under 48 KB) (x with halo and g staged in shared memory) over a strided share
+// of the batch, then writes its partial sums; k_reduce adds the CTAs'
+// partials in a fixed order.  (The six 32 -> 32
 // layers use k_wgrad_tc on the tensor cores.)
-constexpr int kGX = 64;
+constexpr int kWgThreads = 256; // threads of a thin-layer weight-gradient CTA
 
 __device__ __forceinline__ float ldf(const float *p) { return *p; }
 __device__ __forceinline__ float ldf(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
 template <int CI, int CO, typename TX, typename TG>
-__global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, const TG *__restrict__ g, int B,
+__global__ void __launch_bounds__(kWgThreads) k_wgrad(const TX *__restrict__ x, const TG *__restrict__ g, int B,
                                                       int H, int W, float *__restrict__ part)
 {
+    constexpr int kGX = CI >= 16 ? 64 : 128;                   // pixels of a row segment (one unit)
+    constexpr int NW = 9 * CI * CO, NO = NW + CO;              // weights, then biases
+    constexpr int J = (NO + kWgThreads - 1) / kWgThreads;      // outputs per thread
+    constexpr int NX = 3 * (kGX + 2) * CI, NG = kGX * CO;      // staged values
     __shared__ float sx[3][kGX + 2][CI];
     __shared__ float sg[kGX][CO];
-    const int tid = threadIdx.x, nthr = 9 * CI + 1;
-    const bool isb = tid == 9 * CI; // the bias thread
-    const int tap = isb ? 4 : tid / CI, ci = isb ? 0 : tid % CI, dy = tap / 3 - 1, dx = tap % 3 - 1;
-    float acc[CO];
+    const int tid = threadIdx.x;
+    // output o = tid + kWgThreads j: weight (tap, ci, co) or bias co; for
+    // consecutive threads co (then ci) runs fastest, so their shared reads are
+    // consecutive or broadcast
+    int xo[J], go[J];
+    bool has[J];
 #pragma unroll
-    for (int c = 0; c < CO; c++) acc[c] = 0.f;
+    for (int j = 0; j < J; j++) {
+        const int o = tid + kWgThreads * j;
+        has[j] = o < NO;
+        if (o < NW) {
+            const int tap = o / (CI * CO), rem = o - tap * CI * CO, ci = rem / CO, co = rem - ci * CO;
+            xo[j] = ((tap / 3) * (kGX + 2) + tap % 3) * CI + ci; // + c * CI for pixel c
+            go[j] = co;
+        } else {
+            xo[j] = -1; // bias: x = 1
+            go[j] = has[j] ? o - NW : 0;
+        }
+    }
+    float acc[J];
+#pragma unroll
+    for (int j = 0; j < J; j++) acc[j] = 0.f;
+    const float *sxf = &sx[0][0][0];
     const int segs = (W + kGX - 1) / kGX;
     const long long units = (long long)B * H * segs;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
         const int seg = (int)(u % segs), y = (int)((u / segs) % H), b = (int)(u / ((long long)segs * H));
         const int xb = seg * kGX;
         __syncthreads();
-        for (int i = tid; i < 3 * (kGX + 2) * CI; i += nthr) {
-            const int r = i / ((kGX + 2) * CI), rem = i - r * (kGX + 2) * CI, c = rem / CI, ch = rem - c * CI;
-            const int yy = y + r - 1, xx = xb + c - 1;
-            sx[r][c][ch] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? ldf(x + (((size_t)b * H + yy) * W + xx) * CI + ch) : 0.f;
+        if constexpr (sizeof(TX) == 2 && CI % 8 == 0) {
+            // BF16 activations: 16-byte loads of 8 channels, all of a thread's in flight first
+            constexpr int NV = NX / 8, NL = (NV + kWgThreads - 1) / kWgThreads;
+            uint4 v[NL];
+#pragma unroll
+            for (int q = 0; q < NL; q++) {
+                const int i = tid + q * kWgThreads;
+                const int r = i / ((kGX + 2) * (CI / 8)), rem = i - r * (kGX + 2) * (CI / 8);
+                const int c = rem / (CI / 8), ch8 = rem - c * (CI / 8);
+                const int yy = y + r - 1, xx = xb + c - 1;
+                v[q] = make_uint4(0, 0, 0, 0);
+                if (i < NV && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    v[q] = __ldg(reinterpret_cast<const uint4 *>(x + (((size_t)b * H + yy) * W + xx) * CI) + ch8);
+            }
+#pragma unroll
+            for (int q = 0; q < NL; q++) {
+                const int i = tid + q * kWgThreads;
+                if (i >= NV) continue;
+                const uint32_t w4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+                float *d = &sx[0][0][0] + 8 * i;
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[h]));
+                    d[2 * h] = f.x;
+                    d[2 * h + 1] = f.y;
+                }
+            }
+        } else
+        // eight loads of a thread in flight before their stores
+        for (int i0 = tid; i0 < NX; i0 += 8 * kWgThreads) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int i = i0 + q * kWgThreads;
+                const int r = i / ((kGX + 2) * CI), rem = i - r * (kGX + 2) * CI, c = rem / CI, ch = rem - c * CI;
+                const int yy = y + r - 1, xx = xb + c - 1;
+                v[q] = (i < NX && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                           ? ldf(x + (((size_t)b * H + yy) * W + xx) * CI + ch)
+                           : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (i0 + q * kWgThreads < NX) (&sx[0][0][0])[i0 + q * kWgThreads] = v[q];
         }
-        for (int i = tid; i < kGX * CO; i += nthr) {
-            const int c = i / CO, co = i - c * CO, xx = xb + c;
-            sg[c][co] = xx < W ? ldf(g + (((size_t)b * H + y) * W + xx) * CO + co) : 0.f;
+        for (int i0 = tid; i0 < NG; i0 += 8 * kWgThreads) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int i = i0 + q * kWgThreads, c = i / CO, co = i - c * CO, xx = xb + c;
+                v[q] = (i < NG && xx < W) ? ldf(g + (((size_t)b * H + y) * W + xx) * CO + co) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (i0 + q * kWgThreads < NG) (&sg[0][0])[i0 + q * kWgThreads] = v[q];
         }
         __syncthreads();
         for (int c = 0; c < kGX; c++) {
-            const float xv = isb ? 1.f : sx[1 + dy][c + 1 + dx][ci];
 #pragma unroll
-            for (int co = 0; co < CO; co++) acc[co] = fmaf(xv, sg[c][co], acc[co]);
+            for (int j = 0; j < J; j++) {
+                const float xv = xo[j] >= 0 ? sxf[xo[j] + c * CI] : 1.f;
+                acc[j] = fmaf(xv, sg[c][go[j]], acc[j]);
+            }
         }
     }
-    float *o = part + (size_t)blockIdx.x * (9 * CI * CO + CO);
-    if (isb) {
+    float *o = part + (size_t)blockIdx.x * NO;
 #pragma unroll
-        for (int co = 0; co < CO; co++) o[9 * CI * CO + co] = acc[co];
-    } else {
-#pragma unroll
-        for (int co = 0; co < CO; co++) o[(tap * CI + ci) * CO + co] = acc[co];
-    }
+    for (int j = 0; j < J; j++)
+        if (has[j]) o[tid + kWgThreads * j] = acc[j];
 }
 
 // ---- weight gradient of a 32 -> 32 layer on the tensor cores ----------------------
@@ -557,7 +623,7 @@ __global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, 
 // (BF16 operands, FP32 accumulators in tensor memory), db[co] = sum_p g[p][co].
 // A unit is one 128-pixel segment of an image row y (pixels x0 .. x0 + 127):
 // the rows y - 1 .. y + 2 of x with a 1-pixel halo (the fourth row only pads
-// the M = 128 operand and is zero) are staged as [row][channel group][pixel]
+// the M = 128 operand) are staged as [row][channel group][pixel]
 // [8 BF16], and the row y of g as [co group][pixel][8].  Both are MN-major
 // operands without swizzle (core matrices of 8 channels x 8 pixels, 16-byte
 // rows): x's 16 row-and-group blocks sit 130 x 16 bytes apart, so one
@@ -565,10 +631,11 @@ __global__ void __launch_bounds__(9 * CI + 1) k_wgrad(const TX *__restrict__ x, 
 // it dx + 1 pixels into the staged row applies the column offset.  For each
 // dx the 8 instructions of K = 16 pixels add x[y + dy][x + dx][ci] g[y][x][co]
 // into accumulator dx + 1 (tensor-memory lane 32 (dy + 1) + ci, column co;
-// lane 96, whose operand row is a one, sums g: the bias gradient).  Two stages of units alternate on mbarriers (the
-// next unit is staged while the products of the current one run).  Each CTA
-// takes a strided share of the units, then writes one partial row (the
-// layout of k_wgrad's), which k_reduce sums in a fixed order: deterministic.
+// lane 96, whose operand row is a one, sums g: the bias gradient).  Units
+// are staged by cp.async into two alternating stages: the next unit's copies
+// are in flight while the products of the current one run.  Each CTA takes
+// a strided share of the units, then writes one partial row (the layout of
+// k_wgrad's), which k_reduce sums in a fixed order: deterministic.
 constexpr int kWtPix = kCT + 2;                            // staged pixels of an x row
 constexpr int kWtX = 4 * kCGrp * kWtPix * 16;              // staged x rows (33,280 bytes)
 constexpr int kWtG = kCGrp * kCT * 16;                     // staged g row (8,192 bytes)
@@ -609,34 +676,53 @@ __global__ void __launch_bounds__(128, 2) k_wgrad_tc(const __nv_bfloat16 *__rest
     const uint32_t tmem = *s_tmem;
     int n = 0;         // units of this CTA
     int issued = -1;   // thread 0: the last unit whose products were issued
+    // stages unit u into stage st with cp.async (zero fill outside the image);
+    // the padding row holds a one in channel 0 (lane 96 of every accumulator
+    // then sums g over the unit: the bias gradient)
+    auto stage_unit = [&](long long u, int st) {
+        unsigned char *sx = wsm + st * kWtStage, *sg = sx + kWtX;
+        const int seg = (int)(u % segs), y = (int)((u / segs) % H), b = (int)(u / ((long long)segs * H));
+        const int x0 = seg * kCT;
+        for (int i = tid; i < 4 * kWtPix * kCGrp; i += 128) { // x: 4 rows x 130 pixels x 4 groups of 16 bytes
+            const int grp = i & 3, pix = (i >> 2) % kWtPix, r = (i >> 2) / kWtPix;
+            unsigned char *dst = sx + ((r * kCGrp + grp) * kWtPix + pix) * 16;
+            if (r == 3) {
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(grp == 0 ? 0x3F80u : 0u, 0, 0, 0); // BF16 1.0
+                continue;
+            }
+            const int yy = y + r - 1, xx = x0 + pix - 1;
+            const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const __nv_bfloat16 *src = inside ? x + (((size_t)b * H + yy) * W + xx) * kC + grp * 8 : x;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src),
+                         "r"(inside ? 16 : 0)
+                         : "memory");
+        }
+        for (int i = tid; i < kCT * kCGrp; i += 128) { // g: 128 pixels x 4 groups
+            const int grp = i & 3, pix = i >> 2, xx = x0 + pix;
+            const __nv_bfloat16 *src = xx < W ? g + (((size_t)b * H + y) * W + xx) * kC + grp * 8 : g;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(sg + (grp * kCT + pix) * 16)),
+                         "l"(src), "r"(xx < W ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if ((long long)blockIdx.x < units) stage_unit(blockIdx.x, 0);
     for (long long u = blockIdx.x; u < units; u += gridDim.x, n++) {
         const int st = n & 1;
         unsigned char *sx = wsm + st * kWtStage, *sg = sx + kWtX;
-        if (n >= 2 && !*s_err && !cbar_wait(su32(done + st), ((n - 2) >> 1) & 1)) {
-            *s_err = 1;
-            atomicAdd(&g_conv_timeouts, 1ull);
-        }
-        if (!*s_err) {
-            const int seg = (int)(u % segs), y = (int)((u / segs) % H), b = (int)(u / ((long long)segs * H));
-            const int x0 = seg * kCT;
-            // x: 4 rows x 130 pixels x 4 channel groups of 16 bytes, zero outside;
-            // the padding row holds a one in channel 0 (lane 96 of every
-            // accumulator then sums g over the unit: the bias gradient)
-            for (int i = tid; i < 4 * kWtPix * kCGrp; i += 128) {
-                const int grp = i & 3, pix = (i >> 2) % kWtPix, r = (i >> 2) / kWtPix;
-                const int yy = y + r - 1, xx = x0 + pix - 1;
-                uint4 v = make_uint4(r == 3 && grp == 0 ? 0x3F80u : 0u, 0, 0, 0); // BF16 1.0 in element 0
-                if (r < 3 && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    v = __ldg(reinterpret_cast<const uint4 *>(x + (((size_t)b * H + yy) * W + xx) * kC) + grp);
-                *reinterpret_cast<uint4 *>(sx + ((r * kCGrp + grp) * kWtPix + pix) * 16) = v;
+        // the next unit's copies go out before this one is consumed: into the
+        // other stage, once the products of unit n - 1 have read it
+        const long long un = u + gridDim.x;
+        if (un < units) {
+            if (n >= 1 && !*s_err && !cbar_wait(su32(done + (st ^ 1)), ((n - 1) >> 1) & 1)) {
+                *s_err = 1;
+                atomicAdd(&g_conv_timeouts, 1ull);
             }
-            // g: 128 pixels x 4 groups
-            for (int i = tid; i < kCT * kCGrp; i += 128) {
-                const int grp = i & 3, pix = i >> 2, xx = x0 + pix;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (xx < W) v = __ldg(reinterpret_cast<const uint4 *>(g + (((size_t)b * H + y) * W + xx) * kC) + grp);
-                *reinterpret_cast<uint4 *>(sg + (grp * kCT + pix) * 16) = v;
-            }
+            if (!*s_err) stage_unit(un, st ^ 1);
+            else asm volatile("cp.async.commit_group;" ::: "memory"); // keeps the group count
+            asm volatile("cp.async.wait_group 1;" ::: "memory");         // this unit's copies have landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(ready + st)) : "memory");
@@ -668,6 +754,7 @@ __global__ void __launch_bounds__(128, 2) k_wgrad_tc(const __nv_bfloat16 *__rest
             }
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory"); // no copy may land after the CTA ends
     if (tid == 0 && issued >= 0 && !cbar_wait(su32(done + (issued & 1)), (issued >> 1) & 1)) {
         *s_err = 1;
         atomicAdd(&g_conv_timeouts, 1ull);
@@ -731,14 +818,22 @@ __global__ void __launch_bounds__(128, 2) k_wgrad_tc(const __nv_bfloat16 *__rest
     }
 }
 
-// dst[i] = sum_{c < nparts} src[c][i] in ascending c (deterministic).
-__global__ void k_reduce(const float *__restrict__ src, int nparts, int len, float *__restrict__ dst)
+// dst[i] = sum over c < nparts of src[c][i] in a fixed order (deterministic):
+// four lanes take a quarter of the c range each (ascending c), then the four
+// sums are added in lane order.
+__global__ void __launch_bounds__(128) k_reduce(const float *__restrict__ src, int nparts, int len,
+                                                float *__restrict__ dst)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= len) return;
+    const int i = blockIdx.x * 32 + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    const int per = (nparts + 3) / 4, c0 = q * per, c1 = min(nparts, c0 + per);
     float s = 0.f;
-    for (int c = 0; c < nparts; c++) s += src[(size_t)c * len + i];
-    dst[i] = s;
+    if (i < len) {
+#pragma unroll 8
+        for (int c = c0; c < c1; c++) s += __ldg(src + (size_t)c * len + i);
+    }
+    const float s1 = __shfl_down_sync(0xffffffffu, s, 1), s2 = __shfl_down_sync(0xffffffffu, s, 2),
+                s3 = __shfl_down_sync(0xffffffffu, s, 3);
+    if (q == 0 && i < len) dst[i] = ((s + s1) + s2) + s3;
 }
 
 // Sum of n values in a fixed order by one CTA of 1024 threads: strided
@@ -901,8 +996,8 @@ cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, 
     // loss = sum of the scaled partials (their rows hold (pilot - Y1)^2 / n)
     k_sum<<<1, 1024, 0, st>>>((const float *)(ws + L.lpart), L.lparts, (float *)(ws + L.loss));
     // last layer
-    k_wgrad<32, 1, __nv_bfloat16, float><<<nc, 9 * 32 + 1, 0, st>>>(X(7), g8, B, H, W, part);
-    k_reduce<<<(kW8 + 1 + 255) / 256, 256, 0, st>>>(part, nc, kW8 + 1, grad + kOffW8);
+    k_wgrad<32, 1, __nv_bfloat16, float><<<nc, kWgThreads, 0, st>>>(X(7), g8, B, H, W, part);
+    k_reduce<<<(kW8 + 1 + 31) / 32, 128, 0, st>>>(part, nc, kW8 + 1, grad + kOffW8);
     const dim3 g128((W + 15) / 16, (H + kThinRows - 1) / kThinRows, B); // 16 x kThinRows pixels per CTA
     ConvRuns RN;
     const int gtc = conv_tc_ctas(B, H, W, RN);
@@ -910,7 +1005,7 @@ cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, 
     __nv_bfloat16 *gcur = ga, *gnext = gb;
     for (int m = kMid - 1; m >= 0; m--) { // layer m + 2: x_{m+1} -> x_{m+2}; gcur = dL/dpre_{m+2}
         k_wgrad_tc<<<nc, 128, kWtSmem, st>>>(X(m + 1), gcur, B, H, W, part);
-        k_reduce<<<(kWm + kC + 255) / 256, 256, 0, st>>>(part, nc, kWm + kC, grad + off_wm(m));
+        k_reduce<<<(kWm + kC + 31) / 32, 128, 0, st>>>(part, nc, kWm + kC, grad + off_wm(m));
         k_conv_tc<true><<<gtc, 128, kCTcSmem, st>>>(gcur, wb + (size_t)m * kWm, nullptr, X(m + 1), gnext, B, H, W,
                                                    RN);
         __nv_bfloat16 *t = gcur;
@@ -918,8 +1013,8 @@ cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, 
         gnext = t;
     }
     // first layer (gcur = dL/dpre_1)
-    k_wgrad<2, 32, float, __nv_bfloat16><<<nc, 9 * 2 + 1, 0, st>>>((const float *)(ws + L.x0), gcur, B, H, W, part);
-    k_reduce<<<(kW1 + kC + 255) / 256, 256, 0, st>>>(part, nc, kW1 + kC, grad + kOffW1);
+    k_wgrad<2, 32, float, __nv_bfloat16><<<nc, kWgThreads, 0, st>>>((const float *)(ws + L.x0), gcur, B, H, W, part);
+    k_reduce<<<(kW1 + kC + 31) / 32, 128, 0, st>>>(part, nc, kW1 + kC, grad + kOffW1);
     return cudaGetLastError();
 }
 

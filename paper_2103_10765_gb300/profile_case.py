@@ -10,6 +10,8 @@ estimate for stage-2 ops), then `reps` launches of the chosen entry point:
   denoise           gbm3d_denoise
   match3            gbm3d_match with the box-sum engine (K1)
   pilot             the learned pilot's forward pass (committed parameters)
+  pilotgrad         its loss gradient (forward + backward) on a batch of 8
+                    images of size x size (the training step's kernels)
   pnp               one plug-and-play iteration of a 4-image batch (no graph)
 """
 import argparse
@@ -55,6 +57,15 @@ def main():
         net = gbm3d.PilotNet(theta, z.device)
         zb = z[None].contiguous()
         ops["pilot"] = lambda: net.forward(zb, [a.sigma])
+    if a.op == "pilotgrad":
+        import os
+
+        import numpy as np
+        theta = np.fromfile(os.path.join(os.path.dirname(gbm3d.__file__), "pilot_theta.f32"), dtype="<f4")
+        net = gbm3d.PilotNet(theta, z.device)
+        zb = torch.stack([torch.from_numpy(synth.make_pair(H, W, a.sigma, 20 + i)[1]) for i in range(8)]).cuda()
+        yb = zb.clone()
+        ops["pilotgrad"] = lambda: net.loss_grad(zb, yb, [a.sigma] * 8)
     if a.op == "pnp":
         import numpy as np
         t = np.arange(9) - 4.0
