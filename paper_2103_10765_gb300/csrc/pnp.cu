@@ -53,15 +53,18 @@ namespace {
 // lo.hi accumulate in FP32 in tensor memory (tcgen05.mma kind::tf32); the
 // dropped lo.lo term is below 2^-22 of |a| |b|.  CTA tile 128 x BN (BN = 128
 // or 64), K in stages of 32 with two stages in flight; 8 warps split the
-// operands as they load them (thread = one row of the K-major tile), one
-// thread issues the 12 MMAs of a stage, and after the last stage the warps
-// read the accumulators back (tcgen05.ld) and apply the epilogue.
+// operands as they load them (thread = one row of the K-major tile; the next
+// tile's row is fetched into registers while the current one is split and
+// multiplied), one thread issues the 12 MMAs of a stage, and after the last
+// stage the warps read the accumulators back (tcgen05.ld) and apply the
+// epilogue.
 struct Epi {
     int mode;              // 0: alpha acc; 1: acc / ((lamM[r] lamN[c])^2 + rho); 2: alpha acc + add[r][c]
     float alpha, rho;
     const float *lamM, *lamN;
     const float *add;
     int ldadd;
+    int trans;             // 1: store C transposed (C^T[c][r], leading dimension ldc)
 };
 
 constexpr int kGM = 128, kGK = 32, kGThreads = 256;
@@ -133,15 +136,14 @@ constexpr int g_smem_bytes()
     return 2 * (2 * kGM * kGK * 4 + 2 * BN * kGK * 4) + 64;
 }
 
-// B is read as B[k][n] (b_kmajor = 0: one scalar load per value, coalesced
-// across the tile's columns) or, for a symmetric B, as B[n][k] (b_kmajor = 1:
-// rows along K, like A).  M, N, K are multiples of 8.  A wait that gives up
-// fills the CTA's output tile with NaN (and counts g_gemm_timeouts), so a
-// failure cannot pass unseen.
+// B arrives transposed, as Bt[n][k] = B[k][n] (rows along K, like A), so both
+// operands load as 16-byte rows.  M, N, K are multiples of 8.  A wait that
+// gives up fills the CTA's output tile with NaN (and counts
+// g_gemm_timeouts), so a failure cannot pass unseen.
 template <int BN>
 __global__ void __launch_bounds__(kGThreads, 1)
-k_gemm_tc(const float *__restrict__ A, int lda, const float *__restrict__ B, int ldb, int b_kmajor,
-          float *__restrict__ C, int ldc, int M, int N, int K, Epi epi)
+k_gemm_tc(const float *__restrict__ A, int lda, const float *__restrict__ Bt, int ldb, float *__restrict__ C,
+          int ldc, int M, int N, int K, Epi epi)
 {
     constexpr int kA = kGM * kGK * 4, kB = BN * kGK * 4; // bytes of one split part of a stage
     constexpr int kStage = 2 * kA + 2 * kB;
@@ -176,42 +178,46 @@ k_gemm_tc(const float *__restrict__ A, int lda, const float *__restrict__ B, int
     const uint32_t tmem = *s_tmem;
     int issued = -1; // thread 0: the last stage whose products were issued
 
+    // this thread's operand row of a k-tile (A row, or B column as a K-major
+    // row): 8 chunks of 4 values, zero outside the matrices
+    const bool arow = tid < kGM, brow = !arow && tid - kGM < BN;
+    const int ar = m0 + tid, nn = tid - kGM, cn = n0 + nn;
+    auto fetch = [&](int kt, float4 (&v)[kGK / 4]) {
+        const int k0 = kt * kGK;
+#pragma unroll
+        for (int c = 0; c < kGK / 4; c++) {
+            const int k = k0 + 4 * c; // K is a multiple of 8: k < K covers all four
+            v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (arow && ar < M && k < K) {
+                v[c] = __ldg(reinterpret_cast<const float4 *>(A + (size_t)ar * lda + k));
+            } else if (brow && cn < N && k < K) {
+                v[c] = __ldg(reinterpret_cast<const float4 *>(Bt + (size_t)cn * ldb + k));
+            }
+        }
+    };
+    float4 nxt[kGK / 4];
+    fetch(0, nxt);
     for (int kt = 0; kt < nk; kt++) {
         const int st = kt & 1;
         unsigned char *stg = smem + st * kStage;
+        float4 cur[kGK / 4];
+#pragma unroll
+        for (int c = 0; c < kGK / 4; c++) cur[c] = nxt[c];
+        if (kt + 1 < nk) fetch(kt + 1, nxt); // in flight while this tile is split and multiplied
         // this stage's buffers were read by the products of k-tile kt - 2
         if (kt >= 2 && !*s_err && !g_mbar_wait(g_smem_u32(&done[st]), ((kt - 2) >> 1) & 1)) {
             *s_err = 1;
             atomicAdd(&g_gemm_timeouts, 1ull);
         }
         if (!*s_err) {
-            const int k0 = kt * kGK;
-            if (tid < kGM) { // A row m0 + tid, 8 chunks of 4 along K
-                const int r = m0 + tid;
+            if (arow) {
 #pragma unroll
-                for (int c = 0; c < kGK / 4; c++) {
-                    const int k = k0 + 4 * c; // K is a multiple of 8: k < K covers all four
-                    const float4 v = (r < M && k < K) ? __ldg(reinterpret_cast<const float4 *>(A + (size_t)r * lda + k))
-                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                    split4(v, stg + c * kGM * 16 + tid * 16, stg + kA + c * kGM * 16 + tid * 16);
-                }
-            } else if (tid - kGM < BN) { // B column n0 + nn as a K-major row
-                const int nn = tid - kGM, cn = n0 + nn;
+                for (int c = 0; c < kGK / 4; c++)
+                    split4(cur[c], stg + c * kGM * 16 + tid * 16, stg + kA + c * kGM * 16 + tid * 16);
+            } else if (brow) {
 #pragma unroll
-                for (int c = 0; c < kGK / 4; c++) {
-                    const int k = k0 + 4 * c;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (cn < N && k < K) {
-                        if (b_kmajor) {
-                            v = __ldg(reinterpret_cast<const float4 *>(B + (size_t)cn * ldb + k));
-                        } else {
-                            const float *bp = B + (size_t)k * ldb + cn;
-                            v = make_float4(__ldg(bp), __ldg(bp + ldb), __ldg(bp + 2 * (size_t)ldb),
-                                            __ldg(bp + 3 * (size_t)ldb));
-                        }
-                    }
-                    split4(v, stg + 2 * kA + c * BN * 16 + nn * 16, stg + 2 * kA + kB + c * BN * 16 + nn * 16);
-                }
+                for (int c = 0; c < kGK / 4; c++)
+                    split4(cur[c], stg + 2 * kA + c * BN * 16 + nn * 16, stg + 2 * kA + kB + c * BN * 16 + nn * 16);
             }
         }
         // the generic-proxy stores become visible to the tensor cores' reads
@@ -296,6 +302,12 @@ k_gemm_tc(const float *__restrict__ A, int lda, const float *__restrict__ B, int
             }
             o[j] = val;
         }
+        if (epi.trans) { // lanes hold consecutive rows: each column's 32 stores are coalesced
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                if (c0 + j < N) C[(size_t)(c0 + j) * ldc + r] = o[j];
+            continue;
+        }
         float *dst = C + (size_t)r * ldc + c0;
         if (c0 + 32 <= N) {
 #pragma unroll
@@ -318,7 +330,7 @@ k_gemm_tc(const float *__restrict__ A, int lda, const float *__restrict__ B, int
 
 struct GemmCfg {
     int bn;
-    void (*fn)(const float *, int, const float *, int, int, float *, int, int, int, int, Epi);
+    void (*fn)(const float *, int, const float *, int, float *, int, int, int, int, Epi);
     int smem;
 };
 
@@ -328,16 +340,16 @@ const GemmCfg kGemmCfgs[] = {
 };
 constexpr int kNumCfgs = sizeof(kGemmCfgs) / sizeof(kGemmCfgs[0]);
 
-// C = epi(A B), A [M][K] row-major (lda), B [K][N] row-major (ldb); b_sym:
-// B is symmetric (so its rows are read as its columns).
-cudaError_t gemm(int cfg, const float *A, int lda, const float *B, int ldb, bool b_sym, float *C, int ldc, int M,
-                 int N, int K, const Epi &epi, cudaStream_t st)
+// C = epi(A B), A [M][K] row-major (lda), B given as Bt [N][K] row-major (ldb)
+// (for a symmetric B, B itself).
+cudaError_t gemm(int cfg, const float *A, int lda, const float *Bt, int ldb, float *C, int ldc, int M, int N, int K,
+                 const Epi &epi, cudaStream_t st)
 {
     const GemmCfg &g = kGemmCfgs[cfg];
     cudaError_t e = cudaFuncSetAttribute(g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
     if (e != cudaSuccess) return e;
     dim3 grid((N + g.bn - 1) / g.bn, (M + kGM - 1) / kGM);
-    g.fn<<<grid, kGThreads, g.smem, st>>>(A, lda, B, ldb, b_sym ? 1 : 0, C, ldc, M, N, K, epi);
+    g.fn<<<grid, kGThreads, g.smem, st>>>(A, lda, Bt, ldb, C, ldc, M, N, K, epi);
     return cudaGetLastError();
 }
 
@@ -467,16 +479,15 @@ size_t tables_bytes(const std::vector<int> &sizes)
     return o;
 }
 
-// Fastest tile shape per (M, N, K, B symmetric), cached for the process (all
-// shapes give the same bits: every output accumulates the same products in
-// the same K order).
-std::map<std::tuple<int, int, int, int>, int> g_tuned;
+// Fastest tile shape per (M, N, K), cached for the process (all shapes give
+// the same bits: every output accumulates the same products in the same K
+// order).
+std::map<std::tuple<int, int, int>, int> g_tuned;
 
-int autotune(const float *A, const float *B, bool b_sym, float *C, int M, int N, int K, cudaStream_t st,
-             bool enabled)
+int autotune(const float *A, const float *Bt, float *C, int M, int N, int K, cudaStream_t st, bool enabled)
 {
     if (!enabled) return 0;
-    const auto key = std::make_tuple(M, N, K, b_sym ? 1 : 0);
+    const auto key = std::make_tuple(M, N, K);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) return it->second;
     cudaEvent_t e0, e1;
@@ -485,13 +496,13 @@ int autotune(const float *A, const float *B, bool b_sym, float *C, int M, int N,
         cudaEventDestroy(e0);
         return 0;
     }
-    Epi epi{0, 1.f, 0.f, nullptr, nullptr, nullptr, 0};
+    Epi epi{0, 1.f, 0.f, nullptr, nullptr, nullptr, 0, 0};
     int best = 0;
     float best_ms = 1e30f;
     for (int c = 0; c < kNumCfgs; c++) {
-        if (gemm(c, A, K, B, N, b_sym, C, N, M, N, K, epi, st) != cudaSuccess) continue; // warm-up
+        if (gemm(c, A, K, Bt, K, C, N, M, N, K, epi, st) != cudaSuccess) continue; // warm-up
         cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; r++) gemm(c, A, K, B, N, b_sym, C, N, M, N, K, epi, st);
+        for (int r = 0; r < 3; r++) gemm(c, A, K, Bt, K, C, N, M, N, K, epi, st);
         cudaEventRecord(e1, st);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
@@ -549,19 +560,21 @@ int pnp_iteration(const gbm3d_pnp_plan_st &P, const PnpImage &m, cudaStream_t st
 {
     const int H = m.H, W = m.W;
     const float rho = P.q.rho;
-    const Epi plain{0, 1.f, 0.f, nullptr, nullptr, nullptr, 0};
-    const Epi divide{1, 1.f, rho, m.lamH, m.lamW, nullptr, 0};
-    const Epi finish{2, 1.f / ((float)H * (float)W), 0.f, nullptr, nullptr, m.u, W};
+    const Epi plain_t{0, 1.f, 0.f, nullptr, nullptr, nullptr, 0, 1};
+    const Epi divide{1, 1.f, rho, m.lamH, m.lamW, nullptr, 0, 0};
+    const Epi finish{2, 1.f / ((float)H * (float)W), 0.f, nullptr, nullptr, m.u, W, 0};
     cudaError_t e;
-    // T(b) = C_H b C_W, divided by the eigenvalues, transformed back (+ u)
-    // (C_W is symmetric, so the second product reads its rows as columns)
-    if ((e = gemm(m.cfg1, m.casH, H, m.b, W, false, m.t1, W, H, W, H, plain, st)) != cudaSuccess)
+    // T(b) = C_H (b C_W): the inner product is stored transposed (t1 as
+    // [W][H]), so the outer one reads it, like the symmetric C_W, as rows
+    // along its contraction; then the eigenvalue division, and the same two
+    // products again back to the image domain (+ u)
+    if ((e = gemm(m.cfg2, m.b, W, m.casW, W, m.t1, H, H, W, W, plain_t, st)) != cudaSuccess)
         return pnp_cuda_fail(e, "pnp gemm");
-    if ((e = gemm(m.cfg2, m.t1, W, m.casW, W, true, m.b, W, H, W, W, divide, st)) != cudaSuccess)
+    if ((e = gemm(m.cfg1, m.casH, H, m.t1, H, m.b, W, H, W, H, divide, st)) != cudaSuccess)
         return pnp_cuda_fail(e, "pnp gemm");
-    if ((e = gemm(m.cfg1, m.casH, H, m.b, W, false, m.t1, W, H, W, H, plain, st)) != cudaSuccess)
+    if ((e = gemm(m.cfg2, m.b, W, m.casW, W, m.t1, H, H, W, W, plain_t, st)) != cudaSuccess)
         return pnp_cuda_fail(e, "pnp gemm");
-    if ((e = gemm(m.cfg2, m.t1, W, m.casW, W, true, m.t, W, H, W, W, finish, st)) != cudaSuccess)
+    if ((e = gemm(m.cfg1, m.casH, H, m.t1, H, m.t, W, H, W, H, finish, st)) != cudaSuccess)
         return pnp_cuda_fail(e, "pnp gemm");
     // v = G-BM3D(x + u)
     int s = gbm3d_denoise(m.t, H, W, W, m.sigma_d, &P.p, m.v, m.dws, (gbm3d_stream_t)st);
@@ -688,8 +701,8 @@ int gbm3d_pnp_plan_create(int n, const int *H, const int *W, const float *const 
     // autotune the two product shapes of every image on its own buffers
     for (PnpImage &m : P->img) {
         if (e != cudaSuccess) break;
-        m.cfg1 = autotune(m.casH, m.b, false, m.t1, m.H, m.W, m.H, s0, q->autotune != 0);
-        m.cfg2 = autotune(m.t1, m.casW, true, m.t, m.H, m.W, m.W, s0, q->autotune != 0);
+        m.cfg1 = autotune(m.casH, m.t1, m.t, m.H, m.W, m.H, s0, q->autotune != 0);
+        m.cfg2 = autotune(m.b, m.casW, m.t1, m.H, m.W, m.W, s0, q->autotune != 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
