@@ -500,8 +500,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling runs: only the timed workload (no other matching form, no FP32 peak measurement, "
+                         "no oracle, no e2e)")
     ap.add_argument("--workload", default="gray1024", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    if args.profile:
+        args.no_cpu_baseline = args.no_e2e = True
     set_workload(args.workload)
     args.warmup = max(args.warmup, 1)
     rank, world, local = dist_env()
@@ -648,7 +653,7 @@ def main():
     # the other matching engine on the same images (the direct FP32 form of
     # Sec. 2's distance next to the tensor-core form, or the reverse)
     other = None
-    if not LEARNED and C == 1 and PRESET == 0:
+    if not LEARNED and C == 1 and PRESET == 0 and not args.profile:
         q = p.replace(match_engine=1 if ENGINE != 1 else 0)
         outq = torch.empty_like(out)
         gbm3d.denoise(noisy[0], SIGMA, q, ws, outq)
@@ -677,7 +682,7 @@ def main():
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     derived_tflops = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    fma_scalar, fma_packed = gbm3d.measure_fp32_peak(dev)
+    fma_scalar, fma_packed = gbm3d.measure_fp32_peak(dev) if not args.profile else (derived_tflops, 0.0)
     peak_tflops = max(fma_scalar, fma_packed)
     geo = [gbm3d.params_stage(p, 1), gbm3d.params_stage(p, 2)]
     Ks = (p.k1, p.k2)
