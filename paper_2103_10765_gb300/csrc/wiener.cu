@@ -5,7 +5,8 @@
 // One CTA per group, K*8 threads.  Thread (r, c) reads column c of block r of
 // both groups (noisy and pilot) straight from the images -- 8 lanes cover one
 // 32-byte block row per load -- and runs the column DCT in registers (even/odd
-// butterfly of the orthonormal DCT-II); the row DCTs go through a
+// butterfly of the orthonormal DCT-II; the noisy and pilot columns as packed
+// f32x2 pairs, and likewise the row DCTs); the row DCTs go through a
 // bank-conflict-free shared layout, one thread per coefficient position runs
 // the full-depth Haar along the K blocks in registers, and the inverse ends
 // with the column pass writing the filtered group straight out, again 8 lanes
@@ -21,20 +22,64 @@ constexpr float kR8 = 0.35355339059327376f; // 1/sqrt(8)
 constexpr float c1 = 0.98078528040323043f, c2 = 0.92387953251128674f, c3 = 0.83146961230254524f;
 constexpr float c5 = 0.55557023301960218f, c6 = 0.38268343236508977f, c7 = 0.19509032201612825f;
 
-// Orthonormal 8-point DCT-II, even/odd split.
-__device__ __forceinline__ void dct8(float *x)
+// Orthonormal 8-point DCT-II, even/odd split (dct8x2 below), and its inverse.
+// Two transforms at once: the noisy and the pilot values of one column (or
+// row) travel as packed pairs, one f32x2 operation per step of dct8.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk2(float lo, float hi)
 {
-    const float s0 = x[0] + x[7], s1 = x[1] + x[6], s2 = x[2] + x[5], s3 = x[3] + x[4];
-    const float d0 = x[0] - x[7], d1 = x[1] - x[6], d2 = x[2] - x[5], d3 = x[3] - x[4];
-    const float e0 = s0 + s3, e1 = s1 + s2, f0 = s0 - s3, f1 = s1 - s2;
-    x[0] = (e0 + e1) * kR8;
-    x[4] = (e0 - e1) * kR8;
-    x[2] = 0.5f * (c2 * f0 + c6 * f1);
-    x[6] = 0.5f * (c6 * f0 - c2 * f1);
-    x[1] = 0.5f * (c1 * d0 + c3 * d1 + c5 * d2 + c7 * d3);
-    x[3] = 0.5f * (c3 * d0 - c7 * d1 - c1 * d2 - c5 * d3);
-    x[5] = 0.5f * (c5 * d0 - c1 * d1 + c7 * d2 + c3 * d3);
-    x[7] = 0.5f * (c7 * d0 - c5 * d1 + c3 * d2 - c1 * d3);
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2 mul2(f2 a, float c)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(pk2(c, c)));
+    return r;
+}
+
+__device__ __forceinline__ f2 fma2(f2 a, float c, f2 b) // a c + b
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(pk2(c, c)), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ void dct8x2(f2 *x)
+{
+    const f2 s0 = add2(x[0], x[7]), s1 = add2(x[1], x[6]), s2 = add2(x[2], x[5]), s3 = add2(x[3], x[4]);
+    const f2 d0 = sub2(x[0], x[7]), d1 = sub2(x[1], x[6]), d2 = sub2(x[2], x[5]), d3 = sub2(x[3], x[4]);
+    const f2 e0 = add2(s0, s3), e1 = add2(s1, s2), f0 = sub2(s0, s3), f1 = sub2(s1, s2);
+    x[0] = mul2(add2(e0, e1), kR8);
+    x[4] = mul2(sub2(e0, e1), kR8);
+    x[2] = mul2(fma2(f0, c2, mul2(f1, c6)), 0.5f);
+    x[6] = mul2(fma2(f0, c6, mul2(f1, -c2)), 0.5f);
+    x[1] = mul2(fma2(d0, c1, fma2(d1, c3, fma2(d2, c5, mul2(d3, c7)))), 0.5f);
+    x[3] = mul2(fma2(d0, c3, fma2(d1, -c7, fma2(d2, -c1, mul2(d3, -c5)))), 0.5f);
+    x[5] = mul2(fma2(d0, c5, fma2(d1, -c1, fma2(d2, c7, mul2(d3, c3)))), 0.5f);
+    x[7] = mul2(fma2(d0, c7, fma2(d1, -c5, fma2(d2, c3, mul2(d3, -c1)))), 0.5f);
 }
 
 // Its inverse (DCT-III, the transpose).
@@ -74,20 +119,6 @@ __device__ __forceinline__ int sidx(int r, int a, int b) { return r * 72 + (r >>
 // the pairings of the full-depth Mallat transform; every coefficient is held
 // once, so the elementwise shrinkage needs no reordering.
 template <int LEN>
-__device__ __forceinline__ void haar_fwd(float *h)
-{
-    float t[LEN];
-#pragma unroll
-    for (int m = 0; m < LEN / 2; m++) {
-        t[m] = (h[2 * m] + h[2 * m + 1]) * kS;
-        t[LEN / 2 + m] = (h[2 * m] - h[2 * m + 1]) * kS;
-    }
-#pragma unroll
-    for (int m = 0; m < LEN; m++) h[m] = t[m];
-    if constexpr (LEN > 2) haar_fwd<LEN / 2>(h);
-}
-
-template <int LEN>
 __device__ __forceinline__ void haar_inv(float *h)
 {
     if constexpr (LEN > 2) haar_inv<LEN / 2>(h);
@@ -101,15 +132,31 @@ __device__ __forceinline__ void haar_inv(float *h)
     for (int m = 0; m < LEN; m++) h[m] = t[m];
 }
 
-template <int Q>
-__device__ __forceinline__ void haar_fwd_lanes(float *v, int q)
+// The forward transform on packed (pilot, noisy) pairs: one f32x2 operation
+// for both groups, the pairings as described above.
+template <int LEN>
+__device__ __forceinline__ void haar_fwd2(f2 *h)
 {
-    haar_fwd<8>(v);
+    f2 t[LEN];
+#pragma unroll
+    for (int m = 0; m < LEN / 2; m++) {
+        t[m] = mul2(add2(h[2 * m], h[2 * m + 1]), kS);
+        t[LEN / 2 + m] = mul2(sub2(h[2 * m], h[2 * m + 1]), kS);
+    }
+#pragma unroll
+    for (int m = 0; m < LEN; m++) h[m] = t[m];
+    if constexpr (LEN > 2) haar_fwd2<LEN / 2>(h);
+}
+
+template <int Q>
+__device__ __forceinline__ void haar_fwd_lanes2(f2 *v, int q)
+{
+    haar_fwd2<8>(v);
 #pragma unroll
     for (int st = 1; st < Q; st <<= 1) {
-        const float o = __shfl_xor_sync(0xffffffffu, v[0], st);
-        if ((q & (2 * st - 1)) == 0) v[0] = (v[0] + o) * kS;       // lower lane: low-pass
-        else if ((q & (2 * st - 1)) == st) v[0] = (o - v[0]) * kS;  // upper lane: high-pass
+        const f2 o = __shfl_xor_sync(0xffffffffu, v[0], st);
+        if ((q & (2 * st - 1)) == 0) v[0] = mul2(add2(v[0], o), kS);       // lower lane: low-pass
+        else if ((q & (2 * st - 1)) == st) v[0] = mul2(sub2(o, v[0]), kS);  // upper lane: high-pass
     }
 }
 
@@ -150,35 +197,21 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
     { // columns first, straight from global: 8 lanes read one 32-byte block row
         // per load; the column DCT runs in registers
         const float *zc = noisy + s_zoff[r] + cb, *pc = pilot + s_poff[r] + cb;
-        float xz[8], xy[8];
+        f2 x[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-            xz[u] = __ldg(zc + (long long)u * npitch);
-            xy[u] = __ldg(pc + (long long)u * ppitch);
-        }
-        dct8(xz);
-        dct8(xy);
+        for (int u = 0; u < 8; u++) x[u] = pk2(__ldg(zc + (long long)u * npitch), __ldg(pc + (long long)u * ppitch));
+        dct8x2(x);
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-            sq[sidx(r, u, cb)] = xz[u];
-            sp[sidx(r, u, cb)] = xy[u];
-        }
+        for (int u = 0; u < 8; u++) upk2(x[u], sq[sidx(r, u, cb)], sp[sidx(r, u, cb)]);
     }
     __syncthreads();
     { // rows: thread (r, a)
-        float xz[8], xy[8];
+        f2 x[8];
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
-            xz[b] = sq[sidx(r, a, b)];
-            xy[b] = sp[sidx(r, a, b)];
-        }
-        dct8(xz);
-        dct8(xy);
+        for (int b = 0; b < 8; b++) x[b] = pk2(sq[sidx(r, a, b)], sp[sidx(r, a, b)]);
+        dct8x2(x);
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
-            sq[sidx(r, a, b)] = xz[b];
-            sp[sidx(r, a, b)] = xy[b];
-        }
+        for (int b = 0; b < 8; b++) upk2(x[b], sq[sidx(r, a, b)], sp[sidx(r, a, b)]);
     }
     __syncthreads();
     float acc = 0.f;
@@ -186,13 +219,12 @@ k_wiener(const float *__restrict__ noisy, int npitch, const float *__restrict__ 
         const int q = t & (Q - 1), e = t / Q;
         const int ea = e >> 3, eb = e & 7;
         float vp[8], vq[8];
+        f2 v2[8];
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-            vp[i] = sp[sidx(8 * q + i, ea, eb)];
-            vq[i] = sq[sidx(8 * q + i, ea, eb)];
-        }
-        haar_fwd_lanes<Q>(vp, q);
-        haar_fwd_lanes<Q>(vq, q);
+        for (int i = 0; i < 8; i++) v2[i] = pk2(sp[sidx(8 * q + i, ea, eb)], sq[sidx(8 * q + i, ea, eb)]);
+        haar_fwd_lanes2<Q>(v2, q);
+#pragma unroll
+        for (int i = 0; i < 8; i++) upk2(v2[i], vp[i], vq[i]);
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const float p2 = vp[i] * vp[i];
