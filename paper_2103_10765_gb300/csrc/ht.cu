@@ -240,11 +240,21 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
         const int xa = pwrap(x0 - 2 + lane, Xc), xb = pwrap(x0 - 2 + 32 + (lane & 3), Xc);
         const float *bsrc = coef + band * E + (size_t)m * Yc * Xc;
         float va[HY], vb[HY];
+        if (y0 >= 2 && y0 - 2 + HY <= Yc) { // no row wraps: rows HY apart by a fixed stride
+            const float *src = bsrc + (size_t)(y0 - 2) * Xc;
 #pragma unroll
-        for (int yy = 0; yy < HY; yy++) {
-            const float *src = bsrc + (size_t)pwrap(y0 - 2 + yy, Yc) * Xc;
-            va[yy] = __ldg(src + xa);
-            vb[yy] = lane < HX - 32 ? __ldg(src + xb) : 0.f;
+            for (int yy = 0; yy < HY; yy++) {
+                va[yy] = __ldg(src + xa);
+                vb[yy] = lane < HX - 32 ? __ldg(src + xb) : 0.f;
+                src += Xc;
+            }
+        } else {
+#pragma unroll
+            for (int yy = 0; yy < HY; yy++) {
+                const float *src = bsrc + (size_t)pwrap(y0 - 2 + yy, Yc) * Xc;
+                va[yy] = __ldg(src + xa);
+                vb[yy] = lane < HX - 32 ? __ldg(src + xb) : 0.f;
+            }
         }
 #pragma unroll
         for (int yy = 0; yy < HY; yy++) {
@@ -308,22 +318,39 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
         // this thread's 8 output rows: every destination and, when averaging
         // spins, every previous value first (16 loads in flight), then the stores
         constexpr int NRO = 2 * TY / 4;
+        constexpr int PER = (1 << LN) / 4; // rows i and i + PER of a thread lie one block row of groups apart
         float *p0[NRO], *p1[NRO];
         float o0[NRO], o1[NRO];
+        // the level-1 output is group-major ([group][block][row][col], strides
+        // N^2 and N: compile-time shifts)
+        auto rowp = [&](int ys) {
+            const int y = pwrap(ys - shift, Yo);
+            const long long g = (long long)(y >> LN) * Bx + gx;
+            return out.base + (g * Zo << (2 * LN)) + ((y & ((1 << LN) - 1)) << LN) + bx;
+        };
+        const long long dz = (long long)(z1 - z0) * (1 << (2 * LN));
+        if (2 * y0 - shift >= 0 && 2 * y0 + 2 * TY - 1 < Yo) {
+            // no row of the tile wraps: the first PER rows in full, the others
+            // one group row (Bx Zo N^2 floats) further per PER rows
+            const long long gstride = ((long long)Bx * Zo) << (2 * LN);
 #pragma unroll
-        for (int i = 0; i < NRO; i++) {
-            const int orow = (tid >> 6) + 4 * i, ys = 2 * y0 + orow;
-            p0[i] = p1[i] = nullptr;
-            if (ys < Yo) {
-                // the level-1 output is group-major ([group][block][row][col],
-                // strides N^2 and N: compile-time shifts)
-                const int y = pwrap(ys - shift, Yo);
-                const long long g = (long long)(y >> LN) * Bx + gx;
-                float *rowp = out.base + (g * Zo << (2 * LN)) + ((y & ((1 << LN) - 1)) << LN) + bx;
-                p0[i] = rowp + ((long long)z0 << (2 * LN));
-                p1[i] = rowp + ((long long)z1 << (2 * LN));
+            for (int i = 0; i < NRO; i++) {
+                p0[i] = i < PER ? rowp(2 * y0 + (tid >> 6) + 4 * i) + ((long long)z0 << (2 * LN))
+                                : p0[i - PER] + gstride;
+                p1[i] = p0[i] + dz;
+                o0[i] = o1[i] = 0.f;
             }
-            o0[i] = o1[i] = 0.f;
+        } else {
+#pragma unroll
+            for (int i = 0; i < NRO; i++) {
+                const int orow = (tid >> 6) + 4 * i, ys = 2 * y0 + orow;
+                p0[i] = p1[i] = nullptr;
+                if (ys < Yo) {
+                    p0[i] = rowp(ys) + ((long long)z0 << (2 * LN));
+                    p1[i] = p0[i] + dz;
+                }
+                o0[i] = o1[i] = 0.f;
+            }
         }
         if (accumulate) {
 #pragma unroll
