@@ -86,6 +86,19 @@ def test_engines_identical_pitched_and_offset(g):
     _assert_same(*_both(g, view, 16))
 
 
+@pytest.mark.parametrize("pitch", [200, 201, 204])
+def test_engines_identical_region_load_paths(g, pitch):
+    """The search region of a tile arrives by one TMA box where the image
+    allows it (16-byte aligned start, row pitch a multiple of 16 bytes: pitch
+    200 and 204 here) and by thread loads otherwise (pitch 201); the lists
+    are the direct engine's either way."""
+    base = torch.zeros((150, pitch), device="cuda")
+    base[:, :176] = _noisy(150, 176, 25 / 255, seed=6)
+    view = base[:, :176]
+    _assert_same(*_both(g, view, 16))
+    _assert_same(*_both(g, view, 32))
+
+
 def test_engines_identical_scaled_and_shifted(g):
     # the power-of-two scaling and centring must not change the ranking
     z = _noisy(128, 128, 25 / 255, seed=5)
