@@ -65,7 +65,7 @@ WORKLOADS = {
                        "graph per iteration"),
     # stage 1 replaced by the trained network (gbm3d_denoise_learned)
     "learned1024": dict(H=1024, W=1024, C=1, cpu_crop=256, ref_crop=128, learned=True,
-                        desc="G-BM3D with the learned pilot: 8-layer 3x3 conv network (32 channels, BF16 weights, "
+                        desc="G-BM3D with the learned pilot: 16-layer 3x3 conv network (32 channels, BF16 weights, "
                              "FP32 accumulation) in place of stage 1, then the stage-2 Wiener filter; 1024x1024 "
                              "grayscale fp32, sigma 25/255, " + _PARAMS),
     # the Sec. 5 parameter list (library preset 1): tiling reference grids

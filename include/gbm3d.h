@@ -321,15 +321,16 @@ int gbm3d_pnp_gemm_config(gbm3d_pnp_plan plan, int image, int *cfg_k_h, int *cfg
 
 /* ---- Learned pilot: an extension (the paper's method has no learned part).
  * A small network imitates the stage-1 estimate (Sec. 3), which stage 2
- * (Sec. 4) then uses as its pilot.  Per pixel: input (Z, sigma); eight
+ * (Sec. 4) then uses as its pilot.  Per pixel: input (Z, sigma); sixteen
  * zero-padded 3 x 3 convolutions 2 -> 32 -> ... -> 32 -> 1 with biases and
- * ReLU after the first seven; pilot = Z - output; training loss
+ * ReLU after the first fifteen (receptive field 33 x 33); pilot = Z - output;
+ * training loss
  * mean (pilot - Y1)^2.  Parameters: one flat FP32 vector theta of
  * gbm3d_pilot_param_count() values, per layer the weights W[tap][ci][co]
  * (tap = 3 (dy + 1) + (dx + 1)) then the biases.  Convolutions use the
  * weights rounded to BF16 and accumulate in FP32; the hidden activations
- * (outputs of the first seven layers) are stored in BF16, rounded to
- * nearest-even, and the six 32 -> 32 layers run on the tensor cores.
+ * (outputs of the first fifteen layers) are stored in BF16, rounded to
+ * nearest-even, and the fourteen 32 -> 32 layers run on the tensor cores.
  * Batches: B images of H x W, contiguous ([B][H][W] float, device);
  * sigma: device array of B noise levels.  EINVAL for an empty or oversized
  * batch, a NULL pointer or a ws not 256-byte aligned; ECUDA if a launch

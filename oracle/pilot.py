@@ -12,8 +12,10 @@ filter, Sec. 4).  Readings:
 
   L1  input: two channels per pixel, the noisy image Z and the noise level
       sigma (a constant plane), so one network serves every sigma.
-  L2  eight 3 x 3 convolutions with zero padding ("same" size): 2 -> 32,
-      six 32 -> 32, 32 -> 1, each with a bias; ReLU after the first seven.
+  L2  sixteen 3 x 3 convolutions with zero padding ("same" size): 2 -> 32,
+      fourteen 32 -> 32, 32 -> 1, each with a bias; ReLU after the first
+      fifteen (a 33 x 33 receptive field, near the 39 x 39 search window the
+      network stands in for).
   L3  the network predicts the residual: pilot = Z - f(Z, sigma).
   L4  loss: mean over pixels of (pilot - Y1)^2, Y1 the method's stage-1
       output for the same noisy image.
@@ -29,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 
 # (input channels, output channels, ReLU after) per layer (reading L2)
-LAYERS = [(2, 32, True)] + [(32, 32, True)] * 6 + [(32, 1, False)]
+LAYERS = [(2, 32, True)] + [(32, 32, True)] * 14 + [(32, 1, False)]
 
 
 def param_count() -> int:

@@ -3,13 +3,13 @@
 // Wiener stage), with its own forward, backward and optimiser kernels.
 //
 // Network (per pixel, zero-padded 3 x 3 convolutions, NHWC activations):
-//   x0 = (Z, sigma)  -> conv 2->32 + ReLU -> six conv 32->32 + ReLU
+//   x0 = (Z, sigma)  -> conv 2->32 + ReLU -> fourteen conv 32->32 + ReLU
 //   -> conv 32->1 = r;  pilot = Z - r;  loss = mean (pilot - Y1)^2
 // Weights W[l][tap][ci][co] (tap = 3 (dy+1) + (dx+1)), biases b[l][co], in
 // one flat FP32 master vector; every convolution uses the weights rounded
-// to BF16.  Activations x1 .. x7 are stored BF16 (NHWC, 64 bytes a pixel,
+// to BF16.  Activations x1 .. x15 are stored BF16 (NHWC, 64 bytes a pixel,
 // rounded to nearest-even by the layer that writes them); accumulation is
-// FP32 throughout.  The six forward 32 -> 32 layers run on the
+// FP32 throughout.  The forward 32 -> 32 layers run on the
 // 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory)
 // as implicit GEMMs over 128-pixel row tiles, and so do their backward-data
 // passes (the same kernel with the weights flipped and transposed, masked by
@@ -28,14 +28,14 @@ namespace gbm3d {
 namespace {
 
 constexpr int kC = 32;      // hidden channels
-constexpr int kMid = 6;     // 32 -> 32 layers
+constexpr int kMid = 14;    // 32 -> 32 layers (receptive field 2 kMid + 5)
 constexpr int kW1 = 9 * 2 * kC, kWm = 9 * kC * kC, kW8 = 9 * kC;
 // offsets of the flat parameter vector (per layer: weights, then biases)
 constexpr int kOffW1 = 0, kOffB1 = kW1;
 __host__ __device__ constexpr int off_wm(int m) { return kW1 + kC + m * (kWm + kC); }
 __host__ __device__ constexpr int off_bm(int m) { return off_wm(m) + kWm; }
 constexpr int kOffW8 = kW1 + kC + kMid * (kWm + kC), kOffB8 = kOffW8 + kW8;
-constexpr int kParams = kOffB8 + 1; // 56385
+constexpr int kParams = kOffB8 + 1; // 130369
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tmem), "r"(64) : "memory");
 }
 
-// Last layer, 32 -> 1: r = b + sum W8 x7; pilot = Z - r.  A CTA of 256
-// threads covers kLX pixels of kThinRows rows: it stages its x7 tile with
+// Last layer, 32 -> 1: r = b + sum W_last x_last; pilot = Z - r.  A CTA of 256
+// threads covers kLX pixels of kThinRows rows: it stages its x_last tile with
 // the 1-pixel halo in shared memory (cp.async 16-byte copies, zero outside
 // the image), then eight lanes per pixel each take four channels of every
 // tap against the 36 weights they hold in registers, and a shuffle sums the
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(128, kCTcPerSm) k_conv_tc(const __nv_bfloat16 
 // and one partial sum of (pilot - Y1)^2 / n per kLX-pixel row segment
 // (reduced later in a fixed order).
 constexpr int kLX = 32;
-constexpr int kLTile = (kThinRows + 2) * (kLX + 2) * kC * 2; // bytes of the staged x7 tile
+constexpr int kLTile = (kThinRows + 2) * (kLX + 2) * kC * 2; // bytes of the staged x_last tile
 
 __global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16 *__restrict__ x7, const float *__restrict__ w8r,
                                                    const float *__restrict__ theta, const float *__restrict__ Z,
@@ -456,7 +456,8 @@ __global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16 *__restri
     }
 }
 
-// Backward of the last layer: g7[p][ci] = (sum_tap g8[p - off(tap)] W8[tap][ci]) * (x7[p][ci] > 0);
+// Backward of the last layer (x7 here names its input x_last, g7 the gradient at
+// that input's pre-activation): g7[p][ci] = (sum_tap g8[p - off(tap)] W8[tap][ci]) * (x7[p][ci] > 0);
 // eight lanes per pixel, four channels each (coalesced rows), 16 pixels of
 // kThinRows rows per CTA.
 __global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, const float *__restrict__ w8r,
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(128) k_last_bwd(const float *__restrict__ g8, 
 // (each keeps its own few sums in registers) and walks row segments of 128
 // pixels (64 for the 32-channel input, keeping the stage under 48 KB) (x with halo and g staged in shared memory) over a strided share
 // of the batch, then writes its partial sums; k_reduce adds the CTAs'
-// partials in a fixed order.  (The six 32 -> 32
+// partials in a fixed order.  (The 32 -> 32
 // layers use k_wgrad_tc on the tensor cores.)
 constexpr int kWgThreads = 256; // threads of a thin-layer weight-gradient CTA
 
@@ -897,8 +898,8 @@ PilotLayout pilot_layout(int B, int H, int W, bool train)
     L.w1r = take(kW1 * 4);
     L.w8r = take(kW8 * 4);
     L.x0 = train ? take(P * 2 * 4) : 0; // (Z, sigma) for the first layer's weight gradient
-    // activations x1..x7 when training (kept for the backward pass), else two ping-pong buffers
-    L.act = take(P * kC * 2 * (train ? 7 : 2)); // BF16
+    // activations x1 .. x_{kMid+1} when training (kept for the backward pass), else two ping-pong buffers
+    L.act = take(P * kC * 2 * (train ? kMid + 1 : 2)); // BF16
     if (train) {
         L.g8 = take(P * 4);
         L.ga = take(P * kC * 2); // BF16 gradients between the 32-channel layers
@@ -964,7 +965,7 @@ cudaError_t pilot_forward(const float *Z, int B, int H, int W, int zpitch, long 
         k_input<<<dim3((W + 31) / 32, (H + 7) / 8, B), 256, 0, st>>>(Z, zpitch, zbatch, sigma, (float2 *)(ws + L.x0),
                                                                     H, W);
     __nv_bfloat16 *act = (__nv_bfloat16 *)(ws + L.act);
-    auto X = [&](int l) { // x_l, l = 1..7
+    auto X = [&](int l) { // x_l, l = 1 .. kMid + 1
         return act + (size_t)(train ? l - 1 : (l - 1) & 1) * L.plane * kC;
     };
     k_conv_first<<<dim3((W + 15) / 16, (H + kThinRows - 1) / kThinRows, B), 256, 0, st>>>(
@@ -976,7 +977,7 @@ cudaError_t pilot_forward(const float *Z, int B, int H, int W, int zpitch, long 
                                                     X(m + 2), B, H, W, RN);
     const float inv_n = 1.f / (float)L.plane;
     k_conv_last<<<dim3((W + kLX - 1) / kLX, (H + kThinRows - 1) / kThinRows, B), 256, 0, st>>>(
-        X(7), w8r, theta, Z, zpitch, zbatch, Y1, pilot, ppitch, pbatch, train ? (float *)(ws + L.g8) : nullptr,
+        X(kMid + 1), w8r, theta, Z, zpitch, zbatch, Y1, pilot, ppitch, pbatch, train ? (float *)(ws + L.g8) : nullptr,
         train ? (float *)(ws + L.lpart) : nullptr, inv_n, H, W);
     return cudaGetLastError();
 }
@@ -996,12 +997,12 @@ cudaError_t pilot_backward(int B, int H, int W, char *ws, const PilotLayout &L, 
     // loss = sum of the scaled partials (their rows hold (pilot - Y1)^2 / n)
     k_sum<<<1, 1024, 0, st>>>((const float *)(ws + L.lpart), L.lparts, (float *)(ws + L.loss));
     // last layer
-    k_wgrad<32, 1, __nv_bfloat16, float><<<nc, kWgThreads, 0, st>>>(X(7), g8, B, H, W, part);
+    k_wgrad<32, 1, __nv_bfloat16, float><<<nc, kWgThreads, 0, st>>>(X(kMid + 1), g8, B, H, W, part);
     k_reduce<<<(kW8 + 1 + 31) / 32, 128, 0, st>>>(part, nc, kW8 + 1, grad + kOffW8);
     const dim3 g128((W + 15) / 16, (H + kThinRows - 1) / kThinRows, B); // 16 x kThinRows pixels per CTA
     ConvRuns RN;
     const int gtc = conv_tc_ctas(B, H, W, RN);
-    k_last_bwd<<<g128, 128, 0, st>>>(g8, w8r, X(7), ga, H, W);
+    k_last_bwd<<<g128, 128, 0, st>>>(g8, w8r, X(kMid + 1), ga, H, W);
     __nv_bfloat16 *gcur = ga, *gnext = gb;
     for (int m = kMid - 1; m >= 0; m--) { // layer m + 2: x_{m+1} -> x_{m+2}; gcur = dL/dpre_{m+2}
         k_wgrad_tc<<<nc, 128, kWtSmem, st>>>(X(m + 1), gcur, B, H, W, part);

@@ -207,8 +207,9 @@ def he_normal_params(seed: int, shapes) -> np.ndarray:
     return out
 
 
-def pilot_training_specs(n: int = 2000, seed: int = 21, size: int = 256):
-    """(H, W, sigma, scene_seed) of the learned pilot's training images:
-    size x size scenes, sigma uniform in [5, 50] / 255."""
+def pilot_training_specs(n: int = 125, seed: int = 21, size: int = 1024):
+    """(H, W, sigma, scene_seed) of the learned pilot's training scenes:
+    n scenes of size x size (the scale of the images it serves; training cuts
+    them into crops), sigma uniform in [5, 50] / 255."""
     u = uniforms(seed, n)
     return [(size, size, (5.0 + 45.0 * float(u[i])) / 255.0, 10000 + i) for i in range(n)]

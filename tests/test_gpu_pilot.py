@@ -2,9 +2,11 @@
 FP64 oracle (oracle/pilot.py, readings L1-L5).
 
 Tolerances: the oracle runs with the same BF16-rounded weights; the GPU also
-rounds the inputs of its six 32 -> 32 layers to BF16 (relative 2^-9 each),
-so outputs agree to about 1e-2 of the residual's scale and gradients to a
-few per cent in norm (cosine similarity per layer >= 0.995)."""
+stores the outputs of its first fifteen layers in BF16 (relative 2^-9 each,
+one rounding per layer), so over the sixteen layers outputs agree to a few
+1e-2 of the residual's scale at the worst pixel (measured 3.0-3.5 %; the
+bound is 5 %) and gradients to a few per cent in norm (cosine similarity per
+layer >= 0.995)."""
 import os
 import time
 
@@ -67,7 +69,9 @@ def test_forward_matches_oracle(pl, theta, B, H, W):
     out = net.forward(torch.from_numpy(Z).to(DEV), sig).cpu().numpy()
     ref = pl.forward(bf16_weights(pl, theta.astype(np.float32)), Z, sig)
     scale = np.abs(Z - ref).max()
-    assert np.abs(out - ref).max() <= 2e-2 * scale, (np.abs(out - ref).max(), scale)
+    assert np.abs(out - ref).max() <= 5e-2 * scale, (np.abs(out - ref).max(), scale)
+    # the typical pixel is far closer than the worst one
+    assert np.sqrt(np.mean((out - ref) ** 2)) <= 1e-2 * scale
 
 
 def test_zero_last_layer_returns_the_noisy_image(pl, theta):
@@ -100,8 +104,9 @@ def test_gradient_matches_oracle(pl, theta):
 
 
 def test_training_reduces_the_loss():
-    Z, Y1, sig = pilot_train.training_set(48, size=64, seed=3, device=DEV)
-    net, losses = pilot_train.train(Z, Y1, sig, epochs=12, batch=8, lr=2e-3)
+    Z, Y1, sig = pilot_train.training_set(48, size=64, seed=3, device=DEV, full=128)
+    assert Z.shape == (48, 64, 64) and len(sig) == 48
+    net, losses = pilot_train.train(Z, Y1, sig, epochs=12, batch=8, lr=1e-3)
     assert losses[-1] < 0.5 * losses[0], losses
 
 
@@ -156,8 +161,8 @@ def test_trained_pilot_is_faster_than_plain_method(orc, sigma):
 
 
 @pytest.mark.skipif(not os.path.exists(THETA_FILE), reason="trained parameters not present")
-@pytest.mark.xfail(reason="the committed network gives up 0.1-1.1 dB against the plain method (mean 0.7 dB over "
-                          "sigma 15/25/50), above the 0.05 dB bar", strict=False)
+@pytest.mark.xfail(reason="on this scene (high-frequency texture) the committed network gives up 0.57-0.71 dB "
+                          "against the plain method at sigma 15/25/50, above the 0.05 dB bar", strict=False)
 @pytest.mark.parametrize("sigma", [15, 25, 50])
 def test_trained_pilot_psnr_gap(orc, sigma):
     """The configuration's quality bar: at 1024^2 the learned form's PSNR

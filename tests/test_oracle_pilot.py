@@ -15,7 +15,7 @@ def pl():
 
 
 def test_param_count(pl):
-    assert pl.param_count() == (9 * 2 * 32 + 32) + 6 * (9 * 32 * 32 + 32) + (9 * 32 + 1) == 56385
+    assert pl.param_count() == (9 * 2 * 32 + 32) + 14 * (9 * 32 * 32 + 32) + (9 * 32 + 1) == 130369
 
 
 def test_conv_is_zero_padded_correlation(pl, rng):
