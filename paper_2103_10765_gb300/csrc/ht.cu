@@ -6,14 +6,15 @@
 // image through the match list (the image and list stay in L2), with the
 // cycle-spin shift folded into the index arithmetic.  Each level of the
 // periodic 3-D transform (bior1.5 x bior1.5 x Haar, Mallat) is one kernel
-// over tiles of 16 x 32 output positions and one pair of slices along the
-// group axis; rows and columns use the lifting form of bior1.5
+// over tiles of output positions (analysis 8 x 64, synthesis 16 x 32) and one
+// pair of slices along the group axis; rows and columns use the lifting form
+// of bior1.5
 //   d[n]  = (x[2n] - x[2n+1]) / sqrt2,  a0[n] = (x[2n] + x[2n+1]) / sqrt2,
 //   a[n]  = a0[n] + (3 d[n-2] - 22 d[n-1] + 22 d[n+1] - 3 d[n+2]) / 128,
 // and its exact inverse.  Each thread of a lifting pass slides along one line
 // in registers (every pair's d and a0 computed once); shared-memory row
-// strides are odd so the column passes are conflict-free.  Detail bands are
-// hard-thresholded as they are written.
+// strides are chosen so that the passes that read across rows are
+// conflict-free.  Detail bands are hard-thresholded as they are written.
 //
 // The level-1 synthesis writes the filtered blocks into a group-major
 // buffer (averaging the spins); one last pass per group stages the group,
@@ -28,8 +29,6 @@ constexpr float kS = 0.70710678118654752f; // 1/sqrt(2)
 constexpr float kU1 = 0.171875f;           // 22/128
 constexpr float kU2 = 0.0234375f;          // 3/128
 constexpr int TY = 16, TX = 32;            // output positions per tile
-constexpr int IY = 2 * TY + 8, IX = 2 * TX + 8; // analysis input tile: 40 x 72
-constexpr int SX = IX + 1;                 // its shared row stride (odd)
 constexpr int HY = TY + 4, HX = TX + 4;    // synthesis band tile with halo 2: 20 x 36
 constexpr int SB = HX + 1;                 // its shared row stride (odd)
 constexpr int SO = 2 * TX + 1;             // synthesis output row stride (odd)
@@ -71,29 +70,41 @@ __device__ __forceinline__ float lift_u(float dm2, float dm1, float dp1, float d
 }
 
 // Level analysis: input (Z, Y, X) -> 8 bands [band][Z/2][Y/2][X/2], band =
-// 4 hz + 2 hy + hx.  GATHER: the input is the cycle-spun mosaic of blocks of
-// side 2^LN read from the image through the pixel offsets of the match list
-// (level 1); otherwise a [Z][Y][X] plane stack.  vec: X/2 is a multiple of 4
-// (float4 stores).
+// 4 hz + 2 hy + hx, for one tile of ATY x ATX output positions and one slice
+// pair.  GATHER: the input is the cycle-spun mosaic of blocks of side 2^LN
+// read from the image through the pixel offsets of the match list (level 1);
+// otherwise a [Z][Y][X] plane stack.  vec: X/2 is a multiple of 4 (float4
+// stores).
+//
+// Thread xx < AIX holds input column xx of both slices in registers (its
+// loads all in flight at once), applies the Haar step along z and the
+// lifting along y there and writes the four (z band, y band) columns to
+// shared memory; then thread (row, chunk of 8 output columns) slides the
+// x lifting along its row (float4 reads, a row stride of 4 mod 8 floats so
+// the eight rows of a quarter warp hit distinct banks), thresholds and
+// stores.
+constexpr int ATY = 8, ATX = 64;                    // analysis output positions per tile
+constexpr int AIY = 2 * ATY + 8, AIX = 2 * ATX + 8; // its input tile: 24 x 136
+constexpr int ASX = AIX + 4;                        // y-pass output row stride (140)
+static_assert(AIX <= 256 && (ASX & 7) == 4, "analysis tile");
+
 template <bool GATHER, int LN>
 __global__ void __launch_bounds__(256)
 k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitch, const int *__restrict__ ofs,
           int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst, float tau, int vec)
 {
-    __shared__ float s_in[2][IY][SX];   // z-low, z-high planes of the input tile
-    __shared__ float s_y[2][2][TY][SX]; // after the y pass: [z band][y band][row][col]
-    const int m = blockIdx.z;            // slice pair
-    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+    __shared__ __align__(16) float s_y[2][2][ATY][ASX]; // [z band][y band][output row][input col]
+    const int m = blockIdx.z;                           // slice pair
+    const int y0 = blockIdx.y * ATY, x0 = blockIdx.x * ATX;
     const int iy0 = 2 * y0 - 4, ix0 = 2 * x0 - 4;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
 
-    // load (one warp per tile row) + Haar along z.  Gather: the tile's input
-    // rows and columns span at most OY x OX blocks of the mosaic (6 x 10 for
-    // N = 8, 4 x 6 for N = 16; an N-aligned block wraps as a whole), whose
-    // pixel offsets for the two slices are staged in shared memory first;
-    // every voxel is then one image load.
+    // Gather: the tile's input rows and columns span at most OY x OX blocks
+    // of the mosaic (4 x 18 for N = 8, 3 x 10 for N = 16; an N-aligned block
+    // wraps as a whole), whose pixel offsets for the two slices are staged in
+    // shared memory first; every voxel is then one image load.
     constexpr int NB = 1 << LN;
-    constexpr int OY = ((NB + IY - 2) >> LN) + 1, OX = ((NB + IX - 2) >> LN) + 1;
+    constexpr int OY = ((NB + AIY - 2) >> LN) + 1, OX = ((NB + AIX - 2) >> LN) + 1;
     __shared__ int s_ofs[OY][OX][2];
     int z0 = 2 * m, z1 = 2 * m + 1;
     const int uy0 = iy0 - shift, ux0 = ix0 - shift;
@@ -108,83 +119,62 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
         }
         __syncthreads();
     }
-    { // one warp per tile row; all of a thread's loads in flight before any store
-        constexpr int NR = IY / 8, NH = (IX + 31) / 32; // 5 rows, 3 column chunks
-        float v0[NR][NH], v1[NR][NH];
+    if (tid < AIX) { // z and y passes on input column xx
+        const int xx = tid;
+        float v0[AIY], v1[AIY];
+        if (GATHER) {
+            const int dx = ux0 + xx - xbase, rx = dx >> LN;
+            const float *colimg = img + (dx & (NB - 1));
 #pragma unroll
-        for (int j = 0; j < NR; j++) {
-            const int yy = warp + 8 * j;
-            if (GATHER) {
+            for (int yy = 0; yy < AIY; yy++) {
                 const int dy = uy0 + yy - ybase, ry = dy >> LN;
-                const float *rowimg = img + (size_t)(dy & (NB - 1)) * pitch;
+                const float *b = colimg + (size_t)(dy & (NB - 1)) * pitch;
+                v0[yy] = __ldg(b + s_ofs[ry][rx][0]);
+                v1[yy] = __ldg(b + s_ofs[ry][rx][1]);
+            }
+        } else {
+            const int x = pwrap(ix0 + xx, X);
+            const float *r0 = src + (size_t)z0 * Y * X + x, *r1 = src + (size_t)z1 * Y * X + x;
 #pragma unroll
-                for (int h = 0; h < NH; h++) {
-                    const int xx = lane + 32 * h;
-                    v0[j][h] = v1[j][h] = 0.f;
-                    if (xx < IX) {
-                        const int dx = ux0 + xx - xbase;
-                        const float *b = rowimg + (dx & (NB - 1));
-                        v0[j][h] = __ldg(b + s_ofs[ry][dx >> LN][0]);
-                        v1[j][h] = __ldg(b + s_ofs[ry][dx >> LN][1]);
-                    }
-                }
-            } else {
-                const int y = pwrap(iy0 + yy, Y);
-                const float *r0 = src + ((size_t)z0 * Y + y) * X, *r1 = src + ((size_t)z1 * Y + y) * X;
-#pragma unroll
-                for (int h = 0; h < NH; h++) {
-                    const int xx = lane + 32 * h;
-                    v0[j][h] = v1[j][h] = 0.f;
-                    if (xx < IX) {
-                        const int x = pwrap(ix0 + xx, X);
-                        v0[j][h] = __ldg(r0 + x);
-                        v1[j][h] = __ldg(r1 + x);
-                    }
-                }
+            for (int yy = 0; yy < AIY; yy++) {
+                const size_t y = (size_t)pwrap(iy0 + yy, Y) * X;
+                v0[yy] = __ldg(r0 + y);
+                v1[yy] = __ldg(r1 + y);
             }
         }
+        // Haar along z (band zb), then along y: output row o uses pairs o .. o+4
 #pragma unroll
-        for (int j = 0; j < NR; j++)
+        for (int zb = 0; zb < 2; zb++) {
+            float d[AIY / 2], a0[AIY / 2];
 #pragma unroll
-            for (int h = 0; h < NH; h++) {
-                const int yy = warp + 8 * j, xx = lane + 32 * h;
-                if (xx < IX) {
-                    s_in[0][yy][xx] = (v0[j][h] + v1[j][h]) * kS;
-                    s_in[1][yy][xx] = (v0[j][h] - v1[j][h]) * kS;
-                }
+            for (int n = 0; n < AIY / 2; n++) {
+                const float u = (zb ? v0[2 * n] - v1[2 * n] : v0[2 * n] + v1[2 * n]) * kS;
+                const float v = (zb ? v0[2 * n + 1] - v1[2 * n + 1] : v0[2 * n + 1] + v1[2 * n + 1]) * kS;
+                d[n] = (u - v) * kS;
+                a0[n] = (u + v) * kS;
             }
-    }
-    __syncthreads();
-
-    // y pass: one thread per (z band, column); output row o uses pairs o .. o+4
-    if (tid < 2 * IX) {
-        const int zb = tid >= IX, xx = tid - zb * IX;
-        float d[IY / 2], a0[IY / 2];
 #pragma unroll
-        for (int n = 0; n < IY / 2; n++) {
-            const float u = s_in[zb][2 * n][xx], v = s_in[zb][2 * n + 1][xx];
-            d[n] = (u - v) * kS;
-            a0[n] = (u + v) * kS;
-        }
-#pragma unroll
-        for (int o = 0; o < TY; o++) {
-            s_y[zb][0][o][xx] = a0[o + 2] + lift_u(d[o], d[o + 1], d[o + 3], d[o + 4]);
-            s_y[zb][1][o][xx] = d[o + 2];
+            for (int o = 0; o < ATY; o++) {
+                s_y[zb][0][o][xx] = a0[o + 2] + lift_u(d[o], d[o + 1], d[o + 3], d[o + 4]);
+                s_y[zb][1][o][xx] = d[o + 2];
+            }
         }
     }
     __syncthreads();
 
-    // x pass: thread (row = tid & 63: z band, y band, output row; chunk of 8
-    // output columns = tid >> 6), sliding over 12 pairs
-    const int row = tid & 63, chunk = tid >> 6;
-    const int zb = row >> 5, yb = (row >> 4) & 1, o = row & 15;
-    const float *sr = &s_y[zb][yb][o][16 * chunk];
+    // x pass: warp = chunk of 8 output columns, lane = (z band, y band, output
+    // row); it slides over 12 pairs
+    const int row = tid & 31, chunk = tid >> 5;
+    const int zb = row >> 4, yb = (row >> 3) & 1, o = row & 7;
+    const float4 *sr = reinterpret_cast<const float4 *>(&s_y[zb][yb][o][16 * chunk]);
     float d[12], a0[12];
 #pragma unroll
-    for (int n = 0; n < 12; n++) {
-        const float u = sr[2 * n], v = sr[2 * n + 1];
-        d[n] = (u - v) * kS;
-        a0[n] = (u + v) * kS;
+    for (int q = 0; q < 6; q++) {
+        const float4 t = sr[q];
+        d[2 * q] = (t.x - t.y) * kS;
+        a0[2 * q] = (t.x + t.y) * kS;
+        d[2 * q + 1] = (t.z - t.w) * kS;
+        a0[2 * q + 1] = (t.z + t.w) * kS;
     }
     const int band = zb * 4 + yb * 2;
     float lo[8], hi[8];
@@ -223,7 +213,7 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
 // N = 2^LN; it is written (or added) scaled into out, which is group-major
 // (out.base[((g K + r) N + row) N + col]).
 template <bool SCATTER, int LN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4) // four CTAs per SM: at most 64 registers a thread
 k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restrict__ dst, GroupOut out, int Bx,
           int shift, float scale, int accumulate)
 {
@@ -461,7 +451,7 @@ void launch_levels(const HtGeom &g, const float *img, int pitch, const int *ofs,
             const int Y = g.Yd >> (l - 1), X = g.Xd >> (l - 1), Z = g.K >> (l - 1);
             const float tau = sigma * (tau_a - tau_b * (float)l);
             const int vec = ((X >> 1) % 4) == 0;
-            dim3 grid((X / 2 + TX - 1) / TX, (Y / 2 + TY - 1) / TY, Z / 2);
+            dim3 grid((X / 2 + ATX - 1) / ATX, (Y / 2 + ATY - 1) / ATY, Z / 2);
             if (l == 1)
                 k_dwt_ana<true, LN><<<grid, 256, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
             else
