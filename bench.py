@@ -63,6 +63,12 @@ WORKLOADS = {
                        "8, seed 7), per-image sigma in [5, 50]/255, 9x9 Gaussian blur std 1.6, 50 ADMM iterations "
                        "(rho 0.1), each denoising every image with two-stage G-BM3D (" + _PARAMS + "), one CUDA "
                        "graph per iteration"),
+    # the small end of the same batch: where launch overhead weighs most
+    "pnp64_small": dict(H=0, W=0, C=1, cpu_crop=128, ref_crop=128, pnp=True, pnp_hi=256,
+                        desc="batched plug-and-play ADMM deconvolution: 64 images of uneven sizes 128..256 "
+                             "(multiples of 8, seed 7), per-image sigma in [5, 50]/255, 9x9 Gaussian blur std 1.6, "
+                             "50 ADMM iterations (rho 0.1), each denoising every image with two-stage G-BM3D (" +
+                             _PARAMS + "), one CUDA graph per iteration"),
     # stage 1 replaced by the trained network (gbm3d_denoise_learned)
     "learned1024": dict(H=1024, W=1024, C=1, cpu_crop=256, ref_crop=128, learned=True,
                         desc="G-BM3D with the learned pilot: 16-layer 3x3 conv network (32 channels, BF16 weights, "
@@ -80,14 +86,16 @@ PRESET = 0              # library parameter preset of the workload
 ENGINE = 0              # gbm3d_params.match_engine of the workload
 LEARNED = False         # stage 1 replaced by the trained network
 WORKLOAD = WORKLOADS["gray1024"]["desc"]
+PNP_HI = 1024           # largest image side of the plug-and-play batch
 CPU_CROP = None         # cpu_baseline sample: top-left crop of the workload image (None: the whole image)
 REF_CROP = 256          # --impl reference: crop per step
 ST_CROP = 256           # cpu_baseline's single-threaded sample: top-left crop
 
 
 def set_workload(name: str):
-    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP, PRESET, LEARNED, ENGINE
+    global H, W, C, WORKLOAD, CPU_CROP, REF_CROP, PRESET, LEARNED, ENGINE, PNP_HI
     w = WORKLOADS[name]
+    PNP_HI = w.get("pnp_hi", 1024)
     H, W, C, WORKLOAD, CPU_CROP, REF_CROP = w["H"], w["W"], w["C"], w["desc"], w["cpu_crop"], w["ref_crop"]
     PRESET = w.get("preset", 0)
     ENGINE = w.get("engine", 0)
@@ -327,7 +335,7 @@ def run_cpu_pnp(nthreads, iters=2):
     """The FP64 oracle's plug-and-play loop on the top-left CPU_CROP^2 crop of
     the batch's first image: (denoised pixels, seconds)."""
     from oracle import pnp
-    Hh, Ww, sig, seed = synth.pnp_batch_specs()[0]
+    Hh, Ww, sig, seed = synth.pnp_batch_specs(hi=PNP_HI)[0]
     _, y = synth.make_blur_pair(Hh, Ww, sig, seed)
     crop = np.ascontiguousarray(y[:CPU_CROP, :CPU_CROP])
     t0 = time.perf_counter()
@@ -342,7 +350,7 @@ def pnp_main(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    specs = synth.pnp_batch_specs()
+    specs = synth.pnp_batch_specs(hi=PNP_HI)
     # every replica restores its own scenes (same sizes and noise levels)
     pairs = [synth.make_blur_pair(h, w, s, seed + 1000 * rank) for h, w, s, seed in specs]
     sig = [s for _, _, s, _ in specs]
