@@ -111,56 +111,61 @@ __global__ void k_fill(const int32_t *__restrict__ idx, int n, int H, int W, int
 // positions stages their entries (one contiguous range) in shared memory,
 // each thread insertion-sorts its position's bucket there, and the CTA writes
 // the range back; a range larger than kSortCap is sorted in place in global
-// memory instead.
+// memory instead.  With slot_of (the planar layout's tables), each thread
+// then writes, for its position's sorted entries, slot_of[entry] = its index
+// in the sorted list and lpos[index] = the block column of the position; the
+// sorted list itself is then not needed and is written back only without.
 constexpr int kSortCap = 4096;
 
-__global__ void __launch_bounds__(256) k_sort(const int *__restrict__ off, int npos, int *__restrict__ list)
+__device__ __forceinline__ void insertion_sort(int *v, int b0, int b1)
+{
+    for (int i = b0 + 1; i < b1; i++) {
+        const int x = v[i];
+        int j = i - 1;
+        while (j >= b0 && v[j] > x) {
+            v[j + 1] = v[j];
+            j--;
+        }
+        v[j + 1] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sort(const int *__restrict__ off, int npos, int *__restrict__ list, int W,
+                                              int *__restrict__ slot_of, int *__restrict__ lpos)
 {
     __shared__ int sl[kSortCap];
     const int p0 = blockIdx.x * 256, p = p0 + threadIdx.x, pe = min(p0 + 256, npos);
     const int B0 = off[p0], n = off[pe] - B0;
+    const bool tables = slot_of != nullptr;
     if (n <= kSortCap) {
         for (int i = threadIdx.x; i < n; i += 256) sl[i] = list[B0 + i];
         __syncthreads();
         if (p < npos) {
             const int b0 = off[p] - B0, b1 = off[p + 1] - B0;
-            for (int i = b0 + 1; i < b1; i++) {
-                const int v = sl[i];
-                int j = i - 1;
-                while (j >= b0 && sl[j] > v) {
-                    sl[j + 1] = sl[j];
-                    j--;
+            insertion_sort(sl, b0, b1);
+            if (tables) {
+                const int l = p % W;
+                for (int i = b0; i < b1; i++) {
+                    slot_of[sl[i]] = B0 + i;
+                    lpos[B0 + i] = l;
                 }
-                sl[j + 1] = v;
             }
         }
+        if (tables) return;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += 256) list[B0 + i] = sl[i];
         return;
     }
     if (p >= npos) return;
     const int b0 = off[p], b1 = off[p + 1];
-    for (int i = b0 + 1; i < b1; i++) {
-        const int v = list[i];
-        int j = i - 1;
-        while (j >= b0 && list[j] > v) {
-            list[j + 1] = list[j];
-            j--;
+    insertion_sort(list, b0, b1);
+    if (tables) {
+        const int l = p % W;
+        for (int i = b0; i < b1; i++) {
+            slot_of[list[i]] = i;
+            lpos[i] = l;
         }
-        list[j + 1] = v;
     }
-}
-
-// slot_of[entry] = its index in the position-sorted entry list; lpos[slot] =
-// the block column l of that slot's position.
-__global__ void k_slots(const int *__restrict__ list, const int *__restrict__ total, const int32_t *__restrict__ idx,
-                        int W, int *__restrict__ slot_of, int *__restrict__ lpos)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= *total) return;
-    const int e = list[j];
-    slot_of[e] = j;
-    lpos[j] = idx[e] % W;
 }
 
 struct Win {
@@ -383,9 +388,8 @@ cudaError_t build_csr(const int32_t *idx, int G, int K, int H, int W, int N, voi
     k_scan_bsum<<<1, 1024, 0, st>>>(bsum, L.nblk);
     k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(off, nscan, bsum);
     k_fill<<<(n + 255) / 256, 256, 0, st>>>(idx, n, H, W, N, off, cursor, list);
-    k_sort<<<(L.npos + 255) / 256, 256, 0, st>>>(off, L.npos, list);
-    if (with_slots)
-        k_slots<<<(n + 255) / 256, 256, 0, st>>>(list, off + L.npos, idx, W, slot_of, (int *)(base + L.lpos));
+    k_sort<<<(L.npos + 255) / 256, 256, 0, st>>>(off, L.npos, list, W, with_slots ? slot_of : nullptr,
+                                                  with_slots ? (int *)(base + L.lpos) : nullptr);
     return cudaGetLastError();
 }
 
