@@ -32,6 +32,10 @@ constexpr int TY = 16, TX = 32;            // output positions per tile
 constexpr int HY = TY + 4, HX = TX + 4;    // synthesis band tile with halo 2: 20 x 36
 constexpr int SB = HX + 1;                 // its shared row stride (odd)
 constexpr int SO = 2 * TX + 1;             // synthesis output row stride (odd)
+// band tiles of the synthesis lie SBB floats apart: with the 14-float gap the
+// two band rows that the lanes of one x-inverse warp read fall on distinct banks
+constexpr int SBB = HY * SB + 14;
+static_assert(2 * 2 * TY * SO <= 8 * SBB, "the y-pass output fits over the band tiles");
 
 // Periodic index (eq. (1)).  Tile halos reach at most a few samples past
 // either end, so one conditional add or subtract suffices unless the axis is
@@ -79,17 +83,21 @@ __device__ __forceinline__ float lift_u(float dm2, float dm1, float dp1, float d
 // Thread xx < AIX holds input column xx of both slices in registers (its
 // loads all in flight at once), applies the Haar step along z and the
 // lifting along y there and writes the four (z band, y band) columns to
-// shared memory; then thread (row, chunk of 8 output columns) slides the
-// x lifting along its row (float4 reads, a row stride of 4 mod 8 floats so
-// the eight rows of a quarter warp hit distinct banks), thresholds and
-// stores.
+// shared memory; then the CTA's 256 x-pass jobs (row, chunk of 8 output
+// columns) slide the x lifting along their rows (float4 reads, a row stride
+// of 4 mod 8 floats so the eight rows of a quarter warp hit distinct banks),
+// threshold and store.  A CTA has kAnaThreads = 160 threads: AIX = 136 of
+// them gather, so few wait at the barrier while the gathers are in flight,
+// and the small CTAs fit seven to an SM (each thread takes one or two x-pass
+// jobs).
 constexpr int ATY = 8, ATX = 64;                    // analysis output positions per tile
 constexpr int AIY = 2 * ATY + 8, AIX = 2 * ATX + 8; // its input tile: 24 x 136
 constexpr int ASX = AIX + 4;                        // y-pass output row stride (140)
-static_assert(AIX <= 256 && (ASX & 7) == 4, "analysis tile");
+constexpr int kAnaThreads = 160;                    // threads of an analysis CTA (AIX gather, all the x pass)
+static_assert(AIX <= kAnaThreads && kAnaThreads <= 256 && (ASX & 7) == 4, "analysis tile");
 
 template <bool GATHER, int LN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kAnaThreads)
 k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitch, const int *__restrict__ ofs,
           int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst, float tau, int vec)
 {
@@ -162,47 +170,49 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
     }
     __syncthreads();
 
-    // x pass: warp = chunk of 8 output columns, lane = (z band, y band, output
-    // row); it slides over 12 pairs
-    const int row = tid & 31, chunk = tid >> 5;
-    const int zb = row >> 4, yb = (row >> 3) & 1, o = row & 7;
-    const float4 *sr = reinterpret_cast<const float4 *>(&s_y[zb][yb][o][16 * chunk]);
-    float d[12], a0[12];
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-        const float4 t = sr[q];
-        d[2 * q] = (t.x - t.y) * kS;
-        a0[2 * q] = (t.x + t.y) * kS;
-        d[2 * q + 1] = (t.z - t.w) * kS;
-        a0[2 * q + 1] = (t.z + t.w) * kS;
-    }
-    const int band = zb * 4 + yb * 2;
-    float lo[8], hi[8];
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-        const float a = a0[j + 2] + lift_u(d[j], d[j + 1], d[j + 3], d[j + 4]);
-        const float h = d[j + 2];
-        lo[j] = (band == 0 || fabsf(a) >= tau) ? a : 0.f;
-        hi[j] = (fabsf(h) >= tau) ? h : 0.f;
-    }
+    // x pass: 256 jobs, job = 32 chunk + (z band, y band, output row); a job
+    // slides over 12 pairs to make 8 output columns
     const int Zo = Z >> 1, Yo = Y >> 1, Xo = X >> 1;
-    const int yo = y0 + o, xo = x0 + 8 * chunk;
-    if (yo >= Yo || xo >= Xo) return;
     const size_t E = (size_t)Zo * Yo * Xo;
-    float *pl = dst + band * E + ((size_t)m * Yo + yo) * Xo + xo;
-    float *ph = pl + E;
-    if (vec && xo + 8 <= Xo) {
-        reinterpret_cast<float4 *>(pl)[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        reinterpret_cast<float4 *>(pl)[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
-        reinterpret_cast<float4 *>(ph)[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
-        reinterpret_cast<float4 *>(ph)[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
-    } else {
+    for (int job = tid; job < 256; job += kAnaThreads) {
+        const int row = job & 31, chunk = job >> 5;
+        const int zb = row >> 4, yb = (row >> 3) & 1, o = row & 7;
+        const float4 *sr = reinterpret_cast<const float4 *>(&s_y[zb][yb][o][16 * chunk]);
+        float d[12], a0[12];
 #pragma unroll
-        for (int j = 0; j < 8; j++)
-            if (xo + j < Xo) {
-                pl[j] = lo[j];
-                ph[j] = hi[j];
-            }
+        for (int q = 0; q < 6; q++) {
+            const float4 t = sr[q];
+            d[2 * q] = (t.x - t.y) * kS;
+            a0[2 * q] = (t.x + t.y) * kS;
+            d[2 * q + 1] = (t.z - t.w) * kS;
+            a0[2 * q + 1] = (t.z + t.w) * kS;
+        }
+        const int band = zb * 4 + yb * 2;
+        float lo[8], hi[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float a = a0[j + 2] + lift_u(d[j], d[j + 1], d[j + 3], d[j + 4]);
+            const float h = d[j + 2];
+            lo[j] = (band == 0 || fabsf(a) >= tau) ? a : 0.f;
+            hi[j] = (fabsf(h) >= tau) ? h : 0.f;
+        }
+        const int yo = y0 + o, xo = x0 + 8 * chunk;
+        if (yo >= Yo || xo >= Xo) continue;
+        float *pl = dst + band * E + ((size_t)m * Yo + yo) * Xo + xo;
+        float *ph = pl + E;
+        if (vec && xo + 8 <= Xo) {
+            reinterpret_cast<float4 *>(pl)[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            reinterpret_cast<float4 *>(pl)[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
+            reinterpret_cast<float4 *>(ph)[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            reinterpret_cast<float4 *>(ph)[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (xo + j < Xo) {
+                    pl[j] = lo[j];
+                    ph[j] = hi[j];
+                }
+        }
     }
 }
 
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(256, 4) // four CTAs per SM: at most 64 regist
 k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restrict__ dst, GroupOut out, int Bx,
           int shift, float scale, int accumulate)
 {
-    __shared__ float s_b[8][HY][SB];     // band tile with halo; later reused for the y-pass output
+    __shared__ float s_b[8 * SBB];       // band tiles with halo (band stride SBB); later the y-pass output
     __shared__ float s_x[2][2][HY][SO];  // after the x inverse: [z band][y band][coef row][output col]
     const int m = blockIdx.z;
     const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
@@ -248,8 +258,8 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
         }
 #pragma unroll
         for (int yy = 0; yy < HY; yy++) {
-            s_b[band][yy][lane] = va[yy];
-            if (lane < HX - 32) s_b[band][yy][32 + lane] = vb[yy];
+            s_b[band * SBB + yy * SB + lane] = va[yy];
+            if (lane < HX - 32) s_b[band * SBB + yy * SB + 32 + lane] = vb[yy];
         }
     }
     __syncthreads();
@@ -259,8 +269,8 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
     for (int job = tid; job < 4 * HY * 8; job += 256) {
         const int rid = job % (4 * HY), chunk = job / (4 * HY);
         const int zy = rid / HY, rw = rid - zy * HY;
-        const float *lo = &s_b[2 * zy][rw][4 * chunk + 2];
-        const float *hi = &s_b[2 * zy + 1][rw][4 * chunk];
+        const float *lo = &s_b[2 * zy * SBB + rw * SB + 4 * chunk + 2];
+        const float *hi = &s_b[(2 * zy + 1) * SBB + rw * SB + 4 * chunk];
         float h[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) h[i] = hi[i];
@@ -275,7 +285,7 @@ k_dwt_syn(const float *__restrict__ coef, int Yc, int Xc, int Zc, float *__restr
     __syncthreads();
 
     // inverse along y: thread (z band, half of the 16 pairs, output column)
-    float(*s_o)[2 * TY][SO] = reinterpret_cast<float(*)[2 * TY][SO]>(&s_b[0][0][0]); // [z band][row][col]
+    float(*s_o)[2 * TY][SO] = reinterpret_cast<float(*)[2 * TY][SO]>(&s_b[0]); // [z band][row][col]
     {
         const int zb = tid >> 7, half = (tid >> 6) & 1, col = tid & 63;
         float h[12];
@@ -453,9 +463,9 @@ void launch_levels(const HtGeom &g, const float *img, int pitch, const int *ofs,
             const int vec = ((X >> 1) % 4) == 0;
             dim3 grid((X / 2 + ATX - 1) / ATX, (Y / 2 + ATY - 1) / ATY, Z / 2);
             if (l == 1)
-                k_dwt_ana<true, LN><<<grid, 256, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
+                k_dwt_ana<true, LN><<<grid, kAnaThreads, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
             else
-                k_dwt_ana<false, 3><<<grid, 256, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau,
+                k_dwt_ana<false, 3><<<grid, kAnaThreads, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau,
                                                           vec);
         }
         // synthesis, levels L..1; level l writes the approximation of level
