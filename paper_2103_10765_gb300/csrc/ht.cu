@@ -17,9 +17,9 @@
 // conflict-free.  Detail bands are hard-thresholded as they are written.
 //
 // The level-1 synthesis writes the filtered blocks into a group-major
-// buffer (averaging the spins); one last pass per group stages the group,
-// computes its TV weight and, for the aggregation, copies its rows into the
-// position-sorted planar layout.
+// buffer (averaging the spins); one last pass per group (a warp) reads the
+// group, computes its TV weight and, for the aggregation, copies its rows
+// into the position-sorted planar layout.
 #include "internal.cuh"
 
 namespace gbm3d {
@@ -444,11 +444,74 @@ k_tv(const float *__restrict__ gm, int G, float eps, GroupOut out, int permute)
     if (lane < K) out.w[out.slot((long long)g * K + lane)] = wv;
 }
 
+// The same weights for 8 x 8 blocks without shared memory.  Lane l of a
+// group's warp holds the half row (bc = l & 1, row a = (l >> 1) & 7) of the
+// blocks r = (l >> 4) K/2 .. (l >> 4) K/2 + K/2 - 1 as float4 registers (one
+// coalesced 512-byte load per step: two whole block slices).  Differences
+// along the group axis are taken in registers (one shuffle from lane l + 16
+// where the two halves meet), along the row inside the float4 and, across
+// its two halves, by one shuffle from lane l + 1, and between rows by
+// shuffles from lane l + 2.  Each lane sums its terms; the warp adds the
+// lanes.  With permute the rows go to the planar layout straight from the
+// registers (32-byte rows, whole sectors).
+template <int K>
+__global__ void __launch_bounds__(128)
+k_tv8(const float *__restrict__ gm, int G, float eps, GroupOut out, int permute)
+{
+    constexpr int NR = K / 2; // blocks a lane holds
+    constexpr unsigned kFull = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * 4 + warp;
+    if (g >= G) return;
+    const int bc = lane & 1, a = (lane >> 1) & 7, rg = lane >> 4;
+    const float4 *src = reinterpret_cast<const float4 *>(gm + (size_t)g * K * 64) + (rg * NR) * 16 + a * 2 + bc;
+    float4 v[NR];
+#pragma unroll
+    for (int j = 0; j < NR; j++) v[j] = __ldg(src + 16 * j);
+    float tv = 0.f;
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        // along the row: inside the half row, then to the next half
+        tv += fabsf(v[j].y - v[j].x) + fabsf(v[j].z - v[j].y) + fabsf(v[j].w - v[j].z);
+        const float nx = __shfl_down_sync(kFull, v[j].x, 1);
+        if (bc == 0) tv += fabsf(nx - v[j].w);
+        // to the next row of the block (lane l + 2: same half, row a + 1)
+        const float4 d = make_float4(__shfl_down_sync(kFull, v[j].x, 2), __shfl_down_sync(kFull, v[j].y, 2),
+                                     __shfl_down_sync(kFull, v[j].z, 2), __shfl_down_sync(kFull, v[j].w, 2));
+        if (a < 7) tv += fabsf(d.x - v[j].x) + fabsf(d.y - v[j].y) + fabsf(d.z - v[j].z) + fabsf(d.w - v[j].w);
+        // to the next block of the group
+        if (j + 1 < NR)
+            tv += fabsf(v[j + 1].x - v[j].x) + fabsf(v[j + 1].y - v[j].y) + fabsf(v[j + 1].z - v[j].z) +
+                  fabsf(v[j + 1].w - v[j].w);
+    }
+    { // block K/2 - 1 (first half, lanes 0..15) to block K/2 (lane l + 16's first)
+        const float4 n = make_float4(__shfl_down_sync(kFull, v[0].x, 16), __shfl_down_sync(kFull, v[0].y, 16),
+                                     __shfl_down_sync(kFull, v[0].z, 16), __shfl_down_sync(kFull, v[0].w, 16));
+        const float4 &c = v[NR - 1];
+        if (rg == 0) tv += fabsf(n.x - c.x) + fabsf(n.y - c.y) + fabsf(n.z - c.z) + fabsf(n.w - c.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tv += __shfl_xor_sync(kFull, tv, o);
+    const float wv = 1.f / fmaxf(tv, eps);
+    if (!permute) {
+        if (lane == 0) out.w[g] = wv;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < NR; j++)
+        reinterpret_cast<float4 *>(out.row((long long)g * K + rg * NR + j, a))[bc] = v[j];
+    if (lane < K) out.w[out.slot((long long)g * K + lane)] = wv;
+}
+
 template <int K, int NB>
 void launch_tv(const float *gm, int G, float eps, const GroupOut &out, int permute, cudaStream_t st)
 {
-    constexpr int NW = tv_warps<K, NB>();
-    k_tv<K, NB><<<(G + NW - 1) / NW, NW * 32, 0, st>>>(gm, G, eps, out, permute);
+    if constexpr (NB == 8) {
+        k_tv8<K><<<(G + 3) / 4, 128, 0, st>>>(gm, G, eps, out, permute);
+    } else {
+        constexpr int NW = tv_warps<K, NB>();
+        k_tv<K, NB><<<(G + NW - 1) / NW, NW * 32, 0, st>>>(gm, G, eps, out, permute);
+    }
 }
 
 template <int LN>
