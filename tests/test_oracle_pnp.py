@@ -103,3 +103,15 @@ def test_batch_specs():
         assert H % 8 == 0 and W % 8 == 0 and 128 <= H <= 1024 and 128 <= W <= 1024
         assert 5 / 255 <= sigma <= 50 / 255
     assert len({(H, W) for H, W, _, _ in s}) > 50
+
+
+def test_batch_specs_small_end():
+    # the small-image batch of the benchmark (sides 128..256): same noise levels
+    # and scene seeds as the full batch, sides drawn from the narrower range
+    s = synth.pnp_batch_specs(hi=256)
+    full = synth.pnp_batch_specs()
+    assert len(s) == 64
+    for (H, W, sigma, seed), (_, _, sigma_f, seed_f) in zip(s, full):
+        assert H % 8 == 0 and W % 8 == 0 and 128 <= H <= 256 and 128 <= W <= 256
+        assert sigma == sigma_f and seed == seed_f
+    assert len({H for H, _, _, _ in s}) > 10
