@@ -124,7 +124,7 @@ def test_filter_ht_parity(orc, H, W, sigma, C):
 
 def test_filter_ht_levels_and_k8(orc):
     _, X = synth.make_pair(64, 64, 0.1, 1)
-    for levels, k1 in ((1, 16), (2, 16), (3, 8)):
+    for levels, k1 in ((1, 16), (2, 16), (3, 8), (3, 32)):
         p = gbm3d.params_default().replace(levels=levels, k1=k1)
         z = gpu(X)
         idx, _ = gbm3d.match(z, k1, p)
@@ -201,6 +201,18 @@ def test_end_to_end_psnr(orc, H, W, sigma):
     pg, po = orc.psnr(out, clean), orc.psnr(ref, clean)
     assert abs(pg - po) <= 0.01, (pg, po)
     assert pg > orc.psnr(X, clean) + 5
+
+
+@pytest.mark.parametrize("k1,k2", [(8, 16), (32, 32)])
+def test_group_sizes_end_to_end(orc, k1, k2):
+    # stage-1 groups of 8 and 32 blocks through the whole denoise (the TV
+    # weights and the planar permutation for every group size), stage 2 at 16 / 32
+    s = 25 / 255
+    clean, X = synth.make_pair(72, 64, s, 5)
+    p = gbm3d.params_default().replace(k1=k1, k2=k2)
+    out = gbm3d.denoise(gpu(X), s, p).cpu().numpy()
+    ref = orc.denoise(X, s, params=orc.Params(k1=k1, k2=k2), nthreads=NT)
+    assert abs(orc.psnr(out, clean) - orc.psnr(ref, clean)) <= 0.01
 
 
 @pytest.mark.parametrize("T,stages,C", [(2, 2, 2), (3, 1, 1), (1, 1, 2)])
