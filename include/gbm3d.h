@@ -52,7 +52,7 @@ enum {
     GBM3D_ENOMEM = 2,       /* scratch too small for the request */
     GBM3D_ECUDA = 3,        /* a CUDA launch or runtime call failed */
     GBM3D_ETIMEOUT = 4,     /* reserved: a bounded device-side wait gave up */
-    GBM3D_EUNSUPPORTED = 5  /* valid but not implemented for this build */
+    GBM3D_EUNSUPPORTED = 5  /* valid, but not supported by the library */
 };
 
 /* Method parameters (Sec. 5 parameter list; see gbm3d_params_default). */
