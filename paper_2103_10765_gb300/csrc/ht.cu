@@ -96,7 +96,12 @@ constexpr int ASX = AIX + 4;                        // y-pass output row stride 
 constexpr int kAnaThreads = 160;                    // threads of an analysis CTA (AIX gather, all the x pass)
 static_assert(AIX <= kAnaThreads && kAnaThreads <= 256 && (ASX & 7) == 4, "analysis tile");
 
-template <bool GATHER, int LN>
+// SHIFT (GATHER only): the cycle-spin shift.  Tiles start at even multiples
+// of 8 output rows, so the first input row's place inside its mosaic block is
+// (-4 - SHIFT) mod N for every tile: which block each input row falls in is
+// known at compile time, and a thread keeps its column's block offsets in
+// registers instead of looking one up per load.
+template <bool GATHER, int LN, int SHIFT = 0>
 __global__ void __launch_bounds__(kAnaThreads)
 k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitch, const int *__restrict__ ofs,
           int Bx, int shift, int Y, int X, int Z, float *__restrict__ dst, float tau, int vec)
@@ -131,14 +136,21 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
         const int xx = tid;
         float v0[AIY], v1[AIY];
         if (GATHER) {
+            constexpr int kB0 = ((-4 - SHIFT) % NB + NB) % NB; // uy0 - ybase in every tile
             const int dx = ux0 + xx - xbase, rx = dx >> LN;
             const float *colimg = img + (dx & (NB - 1));
+            int o0[OY], o1[OY]; // this column's block offsets, both slices
+#pragma unroll
+            for (int ry = 0; ry < OY; ry++) {
+                o0[ry] = s_ofs[ry][rx][0];
+                o1[ry] = s_ofs[ry][rx][1];
+            }
 #pragma unroll
             for (int yy = 0; yy < AIY; yy++) {
-                const int dy = uy0 + yy - ybase, ry = dy >> LN;
+                const int dy = kB0 + yy, ry = dy >> LN; // both known at compile time
                 const float *b = colimg + (size_t)(dy & (NB - 1)) * pitch;
-                v0[yy] = __ldg(b + s_ofs[ry][rx][0]);
-                v1[yy] = __ldg(b + s_ofs[ry][rx][1]);
+                v0[yy] = __ldg(b + o0[ry]);
+                v1[yy] = __ldg(b + o1[ry]);
             }
         } else {
             const int x = pwrap(ix0 + xx, X);
@@ -525,8 +537,11 @@ void launch_levels(const HtGeom &g, const float *img, int pitch, const int *ofs,
             const float tau = sigma * (tau_a - tau_b * (float)l);
             const int vec = ((X >> 1) % 4) == 0;
             dim3 grid((X / 2 + ATX - 1) / ATX, (Y / 2 + ATY - 1) / ATY, Z / 2);
-            if (l == 1)
-                k_dwt_ana<true, LN><<<grid, kAnaThreads, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
+            if (l == 1) {
+                auto kern = c == 0 ? k_dwt_ana<true, LN, 0>
+                                   : c == 1 ? k_dwt_ana<true, LN, 1> : c == 2 ? k_dwt_ana<true, LN, 2> : k_dwt_ana<true, LN, 3>;
+                kern<<<grid, kAnaThreads, 0, st>>>(nullptr, img, pitch, ofs, g.Bx, c, Y, X, Z, C[1], tau, vec);
+            }
             else
                 k_dwt_ana<false, 3><<<grid, kAnaThreads, 0, st>>>(C[l - 1], nullptr, 0, nullptr, 0, 0, Y, X, Z, C[l], tau,
                                                           vec);
