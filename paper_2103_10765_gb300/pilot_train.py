@@ -66,7 +66,7 @@ def initial_theta(seed: int = 11) -> np.ndarray:
     return synth.he_normal_params(seed, shapes).astype(np.float32)
 
 
-def train(Z, Y1, sigmas, epochs: int = 160, batch: int = 16, lr: float = 5e-4, lr_min: float = 1e-5,
+def train(Z, Y1, sigmas, epochs: int = 240, batch: int = 16, lr: float = 3e-4, lr_min: float = 1e-5,
           seed: int = 5, theta0=None, log=None):
     """Adam over shuffled mini-batches (the order drawn from a SplitMix64
     stream); returns the trained PilotNet and the per-epoch mean losses."""
@@ -96,9 +96,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--n", type=int, default=2000, help="training crops (16 per 1024 x 1024 scene)")
-    ap.add_argument("--epochs", type=int, default=160)
+    ap.add_argument("--epochs", type=int, default=240)
     ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--lr", type=float, default=3e-4)
     a = ap.parse_args()
     t0 = time.perf_counter()
     Z, Y1, sig = training_set(a.n)
