@@ -109,7 +109,7 @@ def test_match_parity_full_size_sampled(orc, H, W, K):
 
 
 @pytest.mark.parametrize("H,W,sigma,C", [(64, 72, 25, 2), (100, 83, 50, 2), (13, 13, 25, 2), (48, 48, 15, 1),
-                                         (56, 40, 25, 3)])
+                                         (56, 40, 25, 3), (64, 56, 25, 4)])
 def test_filter_ht_parity(orc, H, W, sigma, C):
     _, X = synth.make_pair(H, W, sigma / 255, 3)
     p = gbm3d.params_default().replace(cycle_spins=C)
@@ -276,7 +276,7 @@ def test_match_n16_parity(orc, H, W, sigma, K, s):
 
 
 @pytest.mark.parametrize("H,W,sigma,C,K", [(64, 80, 25, 2, 16), (100, 83, 50, 2, 16), (48, 48, 15, 1, 8),
-                                           (32, 32, 25, 2, 32), (16, 40, 25, 3, 16)])
+                                           (32, 32, 25, 2, 32), (16, 40, 25, 3, 16), (48, 64, 25, 4, 16)])
 def test_filter_ht_n16_parity(orc, H, W, sigma, C, K):
     _, X = synth.make_pair(H, W, sigma / 255, 3)
     p = paper_stage(1, cycle_spins=C, k1=K)
