@@ -136,6 +136,7 @@ k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitc
         const int xx = tid;
         float v0[AIY], v1[AIY];
         if (GATHER) {
+            static_assert((2 * ATY) % NB == 0, "tile rows start on a block boundary of the mosaic");
             constexpr int kB0 = ((-4 - SHIFT) % NB + NB) % NB; // uy0 - ybase in every tile
             const int dx = ux0 + xx - xbase, rx = dx >> LN;
             const float *colimg = img + (dx & (NB - 1));
