@@ -130,8 +130,9 @@ def test_validation_errors(g, no_gpu):
     # search window too small for K: 9 x 9 image has 2 x 2 block positions
     assert lib.gbm3d_match(fake, 9, 9, 9, P, 16, fake, None, None, None) == g.EINVAL
     # unsupported parameters
+    # (cycle spins 1..4: the level-1 analysis is instantiated for spin shifts 0..3)
     for bad in (dict(patch=12), dict(patch2=4), dict(step2=-1), dict(k1=64), dict(levels=4), dict(k2=12),
-                dict(translations=4)):
+                dict(translations=4), dict(cycle_spins=0), dict(cycle_spins=5)):
         q = p.replace(**bad)
         st = lib.gbm3d_match(fake, 64, 64, 64, ctypes.byref(q), 16, fake, None, None, None)
         assert st in (g.EINVAL, g.EUNSUPPORTED), bad
