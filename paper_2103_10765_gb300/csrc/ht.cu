@@ -96,11 +96,11 @@ constexpr int ASX = AIX + 4;                        // y-pass output row stride 
 constexpr int kAnaThreads = 160;                    // threads of an analysis CTA (AIX gather, all the x pass)
 static_assert(AIX <= kAnaThreads && kAnaThreads <= 256 && (ASX & 7) == 4, "analysis tile");
 
-// SHIFT (GATHER only): the cycle-spin shift.  Tiles start at even multiples
-// of 8 output rows, so the first input row's place inside its mosaic block is
-// (-4 - SHIFT) mod N for every tile: which block each input row falls in is
-// known at compile time, and a thread keeps its column's block offsets in
-// registers instead of looking one up per load.
+// SHIFT (GATHER only): the cycle-spin shift.  Tiles start at multiples of 8
+// output rows, i.e. of 16 input rows, so the first input row's place inside
+// its mosaic block (N <= 16 rows) is (-4 - SHIFT) mod N for every tile: which
+// block each input row falls in is known at compile time, and a thread keeps
+// its column's block offsets in registers instead of looking one up per load.
 template <bool GATHER, int LN, int SHIFT = 0>
 __global__ void __launch_bounds__(kAnaThreads)
 k_dwt_ana(const float *__restrict__ src, const float *__restrict__ img, int pitch, const int *__restrict__ ofs,
